@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Throughput of the SALS sweep on one GB300, through the library's C ABI.
+
+Metric: nnz*rank updates/s = |Omega| * K * T_in / t_step, where one step is one outer
+iteration of Algorithm 1 (ceil(K/C) splits x N modes: R-hat, Gram/rhs, C x C
+Cholesky, row writes, residual refresh) followed by the loss / training RMSE of
+Eq. (1).  Workload: the 1e5 x 1e5 x 1e3 tensor with 1e8 observed entries, Zipf(1.1)
+slice sizes on modes 1-2, rank-50 ground truth + noise, K = 100, C = 10,
+lambda = 0.1, T_in = 1, FP32, synthetic (seeded), resident in HBM.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded prefix sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nnz*rank updates/s per SALS sweep"
+UNIT = "nnz*rank/s"
+WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=100_000_000,
+                K=100, C=10, T_in=1, lam=0.1, rank_truth=50, zipf=1.1)
+
+# DRAM traffic of one k_mode_pass launch from the ncu capture summarised in
+# profiles/k_mode_pass_skewed_3way.md, and a hash of the kernel source it was taken
+# with; reported as null once the kernel changes.
+NCU_TRAFFIC = None   # bytes per launch, filled from the capture
+NCU_SOURCE_HASH = None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mode_pass.cuh", "sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_1410_5209_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_oracle_sample(m_entries, seed, sweeps=1):
+    """The FP64 oracle as it stands on the first m_entries of the workload (a prefix of
+    the same seeded draw), K = 100, C = 10: seconds per sweep and the update count."""
+    import numpy as np
+    import oracle
+    import synth
+    p = synth.skewed_3way(seed=seed, nnz=m_entries, device="cpu")
+    c, x = p.numpy()
+    t = oracle.Tensor(c, x.astype(np.float64), p.dims)
+    A = [a.numpy() for a in p.init_factors()]
+    r = oracle.residual(t, A)
+    t.groups()
+    times = []
+    for s in range(sweeps):
+        t0 = time.perf_counter()
+        oracle.sals_sweep(t, A, r, WORKLOAD["C"], WORKLOAD["lam"], 1, p.column_order(s, WORKLOAD["C"]))
+        times.append(time.perf_counter() - t0)
+    return times, p.nnz * p.K
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    m = args.ref_sample
+    steps = args.warmup + args.steps
+    times, units = run_oracle_sample(m, args.seed, steps)
+    timed = times[args.warmup:]
+    ms = 1e3 * sum(timed) / len(timed)
+    value = units / (ms / 1e3)
+    sample = (f"first {m} entries (prefix of the seeded 1e8-entry draw) of the workload, "
+              f"one full sweep per step (K=100, C=10), single-threaded C")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {**WORKLOAD, "sample_nnz": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--ref-sample", type=int, default=400_000)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    from paper_1410_5209_gb300 import build as tfbuild
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        tfbuild.build()
+    if world > 1:
+        dist.barrier()
+    tf.load()
+
+    K, C, lam, T_in = WORKLOAD["K"], WORKLOAD["C"], WORKLOAD["lam"], WORKLOAD["T_in"]
+    # each rank factorises its own replica (independent problems: no data-path collective)
+    p = synth.skewed_3way(seed=args.seed + rank, nnz=args.nnz, device="cuda")
+    nnz, N = p.nnz, p.N
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed + rank, dtype=tf.F32,
+                         stream=stream.cuda_stream, device_input=True)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+
+    def step():
+        f.sweep(C, lam, T_in)
+        return f.loss(lam)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    f.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        loss, rmse = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = f.get_profile()
+    cnt = f.counters()
+    f.profile(False)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    units = nnz * K * T_in * world
+    value = units / (ms / 1e3)
+
+    # roofline of the dominant kernel: the fused mode pass
+    hbm, peak_kind = peaks()
+    mp_n, mp_ms = prof["mode_pass"]
+    mp_avg_ms = mp_ms / max(mp_n, 1)
+    bytes_per_launch = nnz * (4 * (N - 1) + 4 + 4.0 / (N * T_in))
+    achieved = bytes_per_launch / (mp_avg_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC if (NCU_SOURCE_HASH and NCU_SOURCE_HASH == kernel_source_hash()) else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_mode_pass",
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": mp_avg_ms}
+    nsplit = math.ceil(K / C)
+    sweep_bytes = nnz * (T_in * N * (4 * (N - 1) + 4) + 4) * nsplit
+    sweep_ms = sum(v[1] for k, v in prof.items() if k in ("pack", "mode_pass", "combine")) / args.steps
+    kernel_breakdown = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+    launches_per_step = cnt["last_sweep_launches"] + cnt["loss_launches"]
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {**WORKLOAD, "nnz": nnz, "l2": "inputs larger than L2 (>= 2.4 GB per sweep)",
+                      "parallelism": f"replicas{world}", "create_s": create_s},
+           "roofline": roofline,
+           "sweep_roofline": {"bound": "hbm", "algorithmic_bytes": sweep_bytes,
+                              "device_ms": sweep_ms,
+                              "achieved": sweep_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms else None,
+                              "peak": hbm, "frac": (sweep_bytes / (sweep_ms / 1e3) / 1e9 / hbm)
+                              if sweep_ms else None},
+           "kernels": kernel_breakdown, "gpu_launches": launches_per_step * args.steps,
+           "clocks": clocks, "loss": loss, "train_rmse": rmse}
+    f.close()
+    del f
+
+    # end to end through the C ABI from pinned host buffers: upload + layout + one sweep
+    # + loss + factors back, per step
+    c_pin = torch.empty((nnz, N), dtype=torch.int32, pin_memory=True)
+    x_pin = torch.empty(nnz, dtype=torch.float32, pin_memory=True)
+    c_pin.copy_(p.coords)
+    x_pin.copy_(p.x)
+    del p
+    torch.cuda.empty_cache()
+    cn, xn = c_pin.numpy(), x_pin.numpy()
+    outs = [np.empty((d, K), np.float32) for d in WORKLOAD["dims"]]
+    e2e_times = []
+    for s in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = tf.Factorization(cn, xn, WORKLOAD["dims"], K, seed=args.seed + rank, dtype=tf.F32,
+                             stream=stream.cuda_stream)
+        g.sweep(C, lam, T_in)
+        g.loss(lam)
+        for n in range(N):
+            g._check(g._lib.tf_get_factors(g.handle, n, outs[n].ctypes.data_as(
+                __import__("ctypes").c_void_p)))
+        g.close()
+        if s > 0:   # the first one is a warm-up
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max(e2e_times) if world == 1 else max(e2e_times)
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    out["e2e"] = {"value": units / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": nnz * (4 * N + 4),
+                  "d2h_bytes_per_step": sum(WORKLOAD["dims"]) * K * 4 + 16,
+                  "what": "tf_create from pinned host COO + 1 sweep + tf_loss + factors to host "
+                          "+ tf_destroy"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, u = run_oracle_sample(args.cpu_sample, args.seed, 1)
+        out["cpu_baseline"] = {"value": u / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"first {args.cpu_sample} entries (prefix of the seeded "
+                                         f"draw) of the same workload, one full sweep, K=100, "
+                                         f"C=10, FP64 single-threaded C"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,230 @@
+/*
+ * tf_sals.h -- C ABI of the GB300 SALS / CDTF library.
+ *
+ * The library factorises a partially observed N-way tensor X (observed set Omega)
+ * into factor matrices A^(1..N) (each I_n x K) by Subset Alternating Least Squares
+ * (SALS) and its C = 1 special case CDTF, after Shin & Kang, "Distributed Methods
+ * for High-dimensional and Large-scale Tensor Factorization" (arXiv 1410.5209):
+ *   loss  L = sum_{Omega} (x - sum_k prod_n a^(n)_{i_n k})^2 + lambda sum_n ||A^(n)||_F^2   (Eq. 1)
+ * One call of tf_sals_sweep is one outer iteration of Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ *   - Indices are 0-based.  Coordinates are int32, row-major [nnz][N].
+ *   - Factor matrices are row-major [I_n][K] in the context's dtype (float or double).
+ *   - Every call returns a tf_status and never aborts, traps or exits.  Errors found
+ *     on the device are recorded in a device status word that the next synchronising
+ *     call (tf_loss, tf_get_*, tf_sync) reads back.  tf_last_error() describes the
+ *     most recent failure in words.
+ *   - Inputs are copied: the caller keeps ownership of every buffer it passes, and
+ *     owns every output buffer.  All device memory belongs to the context and is
+ *     released by tf_destroy.
+ *   - Calls on one context are ordered on the context's CUDA stream.  A context is
+ *     not thread-safe; distinct contexts are independent.
+ *   - Host-only entry points (tf_assign_rows, tf_plan_mode, tf_version) need no GPU.
+ */
+#ifndef TF_SALS_H
+#define TF_SALS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tf_ctx tf_ctx;
+
+typedef enum {
+    TF_OK = 0,
+    TF_EINVAL = 1,   /* an argument is out of its documented range */
+    TF_ERANGE = 2,   /* a coordinate is negative or >= its mode length */
+    TF_EDUP = 3,     /* two observed entries share a coordinate (Omega is a set) */
+    TF_ENOMEM = 4,   /* a device or host allocation failed */
+    TF_ECUDA = 5,    /* a CUDA runtime call failed (no device, launch error, ...) */
+    TF_ETIMEOUT = 6, /* a bounded wait on the device gave up */
+    TF_EBUSY = 7     /* the context is in a state that forbids the call */
+} tf_status;
+
+typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
+
+/* tf_create flags */
+#define TF_INPUT_DEVICE 1u  /* coords and values are device pointers (same device) */
+#define TF_KEEP_DEFAULT_INIT 0u
+
+/* per-sweep flags (tf_sals_sweep_ex) */
+#define TF_WEIGHTED_LAMBDA 1u /* lambda * |Omega_i^(n)| per row (weighted-lambda, Sec. 5.1.3) */
+
+/* row scheduling policies (tf_assign_rows / tf_plan_mode / tf_set_schedule) */
+typedef enum {
+    TF_SCHED_LPT = 0,    /* longest first to the least-loaded bin, no row cap (default) */
+    TF_SCHED_GREEDY = 1, /* Algorithm 3: row cap ceil(I_n/M), tie-breaks on rows, totals */
+    TF_SCHED_SEQ = 2,    /* contiguous row ranges (the paper's SEQ baseline, Sec. 5.5) */
+    TF_SCHED_RAN = 3     /* seeded random bin per row (the paper's RAN baseline) */
+} tf_sched_policy;
+
+/* One unit of device work: entries [begin, begin + len) of a mode's sorted order, all
+ * in row `row`.  slot < 0: the item holds the whole row and solves it; slot >= 0: the
+ * item is one chunk of a row split across bins and writes its partial Gram/rhs to
+ * partial slot `slot` (chunks of a row take consecutive slots in entry order). */
+typedef struct {
+    int64_t begin;
+    int32_t len;
+    int32_t row;
+    int32_t slot;
+    int32_t bin;
+} tf_item;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Creates a context holding the tensor X and the factor matrices.
+ *   coords  [nnz][N] int32, 0-based (host, or device with TF_INPUT_DEVICE)
+ *   values  [nnz] float (dtype TF_F32) or double (TF_F64), same residency as coords
+ *   dims    [N] mode lengths I_n, 1 <= I_n <= 2^31 - 1 (host)
+ *   N       1..8;  nnz 0..2^31 - 1;  K >= 1
+ *   seed    seeds the default initialisation and the default column orders
+ *   stream  cudaStream_t to order all work on (NULL = the legacy default stream)
+ * Builds, on the device, the per-mode sorted layout (Omega_i^(n) of the table of
+ * symbols, entries of a row in lexicographic order of the remaining coordinates taken
+ * cyclically from mode n), with bit-exact row offsets; validates coordinates
+ * (TF_ERANGE) and the set property (TF_EDUP); schedules rows onto bins (LPT).
+ * Initialises the factors as Algorithm 1 does: A^(1) = 0 and A^(n>1) i.i.d. normal
+ * with std K^(-1/(2N)) from `seed`, so that R = X.  *out is NULL on failure. */
+tf_status tf_create(const int32_t *coords, const void *values, tf_dtype dtype,
+                    const int64_t *dims, int N, int64_t nnz, int K, uint64_t seed,
+                    void *stream, uint32_t flags, tf_ctx **out);
+
+/* Releases every resource of ctx (NULL is a no-op). */
+void tf_destroy(tf_ctx *ctx);
+
+/* Text of the last failure on ctx (or of the last failed tf_create when ctx is NULL).
+ * The pointer stays valid until the next call on the same context. */
+const char *tf_last_error(const tf_ctx *ctx);
+
+/* Waits for the context's stream and reports any device-side error. */
+tf_status tf_sync(tf_ctx *ctx);
+
+/* ------------------------------------------------------------------ factors */
+
+/* Copies factor matrix n ([I_n][K], host, context dtype) into the context and marks
+ * the residual for recomputation (R = X - model, Section 3.1) before the next use. */
+tf_status tf_set_factors(tf_ctx *ctx, int n, const void *host_A);
+
+/* Copies factor matrix n to host_A ([I_n][K], context dtype).  Synchronises. */
+tf_status tf_get_factors(tf_ctx *ctx, int n, void *host_A);
+
+/* ------------------------------------------------------------------ the sweep */
+
+/* One outer iteration of Algorithm 1: ceil(K/C) splits; for each, R-hat (Algorithm 1),
+ * then T_in passes over modes 1..N updating every row's C parameters by Eq. (4)
+ * (Cholesky, Section 3.1; C = 1 is CDTF's closed form), then the R update of Eq. (5).
+ * The last split holds K mod C columns when C does not divide K.
+ * Column order: a seeded permutation per sweep for C > 1 (chosen without replacement,
+ * Algorithm 1), the identity for C = 1 (CDTF keeps a fixed order, Section 3.1).
+ *   C in 1..K (C <= 16 on the SIMT path, larger C on the tiled path), lambda >= 0,
+ *   T_in >= 1.  Asynchronous: returns once the work is queued on the stream.
+ * A row whose B + lambda I has a non-positive Cholesky pivot (e.g. an empty row with
+ * lambda = 0) is left unchanged and counted (tf_get_counters). */
+tf_status tf_sals_sweep(tf_ctx *ctx, int C, float lambda, int T_in);
+
+/* As tf_sals_sweep with an explicit column order col_order[K] (a permutation of
+ * 0..K-1, host); split s takes col_order[s*C .. min((s+1)*C, K)).  NULL = default. */
+tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, float lambda, int T_in,
+                              const int32_t *col_order);
+
+/* As tf_sals_sweep_order with flags (TF_WEIGHTED_LAMBDA). */
+tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, float lambda, int T_in,
+                           const int32_t *col_order, uint32_t flags);
+
+/* Writes the default column order of sweep number `sweep` (0-based) for this C. */
+tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_order);
+
+/* ------------------------------------------------------------------ loss */
+
+/* loss = sum_Omega r^2 + lambda * sum_n ||A^(n)||_F^2 (Eq. 1; with TF_WEIGHTED_LAMBDA
+ * each row's squared norm is weighted by |Omega_i^(n)|), train_rmse =
+ * sqrt(sum r^2 / |Omega|).  Accumulated in double on the device, in a fixed order
+ * (bit-reproducible).  Synchronises.  Either output pointer may be NULL. */
+tf_status tf_loss(tf_ctx *ctx, float lambda, uint32_t flags, double *loss,
+                  double *train_rmse);
+
+/* ------------------------------------------------------------------ fold-in */
+
+/* Least-squares row for a new slice of mode `mode` against the frozen factors: the
+ * ALS row solve of Eq. (2), a = (B + lambda I_K)^{-1} c, B = sum h h^T, c = sum x h,
+ * h_k = prod_{l != mode} a^(l)_{i_l k}, over the request's m entries.
+ *   other  [m][N-1] int32 (host): indices of the other modes in increasing mode order
+ *   values [m] context dtype (host);  out_row [K] context dtype (host)
+ * Synchronises.  TF_ERANGE if an index is out of range.  A non-positive pivot gives
+ * TF_EINVAL with out_row untouched. */
+tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values,
+                    int64_t m, float lambda, void *out_row);
+
+/* ------------------------------------------------------------------ inspection */
+
+/* Row offsets off[I_n + 1] (int64) and, if perm != NULL, the canonical entry index of
+ * every position of mode n's sorted order, perm[nnz] (int64).  Synchronises. */
+tf_status tf_get_grouping(tf_ctx *ctx, int n, int64_t *off, int64_t *perm);
+
+/* The residual r_e = x_e - sum_k prod_n a^(n)_{i_n k} (Section 3.1) of every entry in
+ * canonical (input) order, host [nnz], context dtype.  Synchronises. */
+tf_status tf_get_residual(tf_ctx *ctx, void *host_r);
+
+/* counters[0] = rows left unchanged by a non-positive pivot since creation,
+ * counters[1] = sweeps run, counters[2] = kernels launched by the last sweep,
+ * counters[3] = work items of all modes, counters[4] = rows split across bins. */
+tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
+
+/* Re-plans the row schedule of every mode (policy, P bins; P = 0 picks the default
+ * for this GPU).  Results do not depend on the schedule. */
+tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
+
+/* ------------------------------------------------------------------ timing */
+
+/* Kernel kinds reported by tf_get_profile. */
+typedef enum {
+    TF_KIND_PACK = 0,      /* slice packing of a split (Theorem 3's C resident columns) */
+    TF_KIND_MODE_PASS = 1, /* fused Gram/rhs/solve/R-hat pass over one mode (Eq. 4)      */
+    TF_KIND_COMBINE = 2,   /* sum of split rows' partial Gram/rhs + solve               */
+    TF_KIND_LOSS = 3,      /* loss / residual reductions (Eq. 1)                        */
+    TF_KIND_OTHER = 4,     /* residual rebuilds and flushes                             */
+    TF_KIND_COUNT = 5
+} tf_kernel_kind;
+
+/* enable != 0: from now on bracket every kernel launch of this context with CUDA
+ * events on its stream and accumulate the device time per kind; enable == 0 stops
+ * and clears.  Off by default. */
+tf_status tf_profile(tf_ctx *ctx, int enable);
+
+/* Launch counts and summed device milliseconds per kind since profiling was enabled
+ * (arrays of TF_KIND_COUNT).  Synchronises. */
+tf_status tf_get_profile(tf_ctx *ctx, int64_t *launches, double *ms);
+
+/* ------------------------------------------------------------------ host-only */
+
+/* Row-to-bin assignment of every mode (no splitting) for M bins, as the paper's
+ * Algorithm 3 does for machines with TF_SCHED_GREEDY (row cap ceil(I_n/M); ties to
+ * fewer rows, then to the smaller total over earlier modes, then to the lower index;
+ * equal rows in increasing index).  TF_SCHED_LPT drops the cap; SEQ and RAN are the
+ * baselines of Section 5.5.  row_nnz[n][I_n], assign[n][I_n] (host).  No GPU. */
+tf_status tf_assign_rows(tf_sched_policy policy, int N, const int64_t *dims,
+                         const int64_t *const *row_nnz, int M, uint64_t seed,
+                         int32_t *const *assign);
+
+/* Work items of one mode for P bins: rows longer than cap entries are split into
+ * ceil(len / cap) near-equal chunks (cap = 0: ceil(nnz / P)); rows and chunks are
+ * placed longest first on the least-loaded bin (TF_SCHED_LPT) or by another policy.
+ * off[I + 1] are the row offsets (host).  items (capacity max_items) come out grouped
+ * by bin, bins in increasing order; bin_ptr[P + 1] indexes them.  *n_items and
+ * *n_slots receive the counts.  TF_ENOMEM if max_items is too small.  No GPU. */
+tf_status tf_plan_mode(const int64_t *off, int64_t I, int P, int64_t cap,
+                       tf_sched_policy policy, uint64_t seed, tf_item *items,
+                       int64_t max_items, int64_t *n_items, int64_t *n_slots,
+                       int64_t *bin_ptr);
+
+/* Library version string. */
+const char *tf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TF_SALS_H */

@@ -97,11 +97,17 @@ class Tensor:
         self.nnz = self.coords.shape[0]
         self._groups = None
 
-    def groups(self, lib=None):
-        """(off[n], perm[n]) for every mode, computed by :func:`group`."""
+    def group_of(self, n, lib=None):
+        """(off, perm) of mode n, computed once by :func:`group`."""
         if self._groups is None:
-            self._groups = [group(self, n, lib) for n in range(self.N)]
-        return self._groups
+            self._groups = [None] * self.N
+        if self._groups[n] is None:
+            self._groups[n] = group(self, n, lib)
+        return self._groups[n]
+
+    def groups(self, lib=None):
+        """(off[n], perm[n]) for every mode."""
+        return [self.group_of(n, lib) for n in range(self.N)]
 
     def row_nnz(self, lib=None):
         return [np.diff(off) for off, _ in self.groups(lib)]
@@ -150,7 +156,7 @@ def row_update(t: Tensor, n, i, rhat, A, S, lam, weighted=False, lib=None):
     K = A[0].shape[1]
     S = _c(S, np.int32)
     rhat = _c(rhat, np.float64)
-    off, perm = t.groups(lib)[n]
+    off, perm = t.group_of(n, lib)
     pa = _ptrs(A)
     return lib.orc_row_update(t.N, n, int(i), _p(t.coords), _p(rhat), K, pa, _p(S), len(S),
                               float(lam), WEIGHTED if weighted else 0, _p(off), _p(perm))

@@ -1,0 +1,290 @@
+"""Python binding of the GB300 SALS / CDTF library (C ABI in include/tf_sals.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libtfsals.so``.  There is no CPU fallback; if the shared library is missing or was
+built for another machine, importing works but the first call raises
+:class:`LibraryMissing` (build it with ``python -m paper_1410_5209_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtfsals.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "tf_sals.h")
+
+OK, EINVAL, ERANGE, EDUP, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(8)
+STATUS_NAMES = ["TF_OK", "TF_EINVAL", "TF_ERANGE", "TF_EDUP", "TF_ENOMEM", "TF_ECUDA",
+                "TF_ETIMEOUT", "TF_EBUSY"]
+F32, F64 = 0, 1
+INPUT_DEVICE = 1
+WEIGHTED_LAMBDA = 1
+SCHED_LPT, SCHED_GREEDY, SCHED_SEQ, SCHED_RAN = 0, 1, 2, 3
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class TFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Item(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int64), ("len", ctypes.c_int32), ("row", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("bin", ctypes.c_int32)]
+
+
+ITEM_DTYPE = np.dtype([("begin", np.int64), ("len", np.int32), ("row", np.int32),
+                       ("slot", np.int32), ("bin", np.int32)])
+
+_lib = None
+
+
+def load():
+    """Load libtfsals.so (no automatic build: build() is explicit)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LibraryMissing(f"{LIB_PATH} not built; run python -m paper_1410_5209_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u32, u64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
+                             ctypes.c_uint64)
+    f32 = ctypes.c_float
+    sig = {
+        "tf_create": [P, P, i32, P, i32, i64, i32, u64, P, u32, P],
+        "tf_destroy": [P],
+        "tf_last_error": [P],
+        "tf_sync": [P],
+        "tf_set_factors": [P, i32, P],
+        "tf_get_factors": [P, i32, P],
+        "tf_sals_sweep": [P, i32, f32, i32],
+        "tf_sals_sweep_order": [P, i32, f32, i32, P],
+        "tf_sals_sweep_ex": [P, i32, f32, i32, P, u32],
+        "tf_default_order": [P, i32, i32, P],
+        "tf_loss": [P, f32, u32, P, P],
+        "tf_foldin": [P, i32, P, P, i64, f32, P],
+        "tf_get_grouping": [P, i32, P, P],
+        "tf_get_residual": [P, P],
+        "tf_get_counters": [P, P],
+        "tf_set_schedule": [P, i32, i32],
+        "tf_profile": [P, i32],
+        "tf_get_profile": [P, P, P],
+        "tf_assign_rows": [i32, i32, P, P, i32, u64, P],
+        "tf_plan_mode": [P, i64, i32, i64, i32, u64, P, i64, P, P, P],
+        "tf_version": [],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tf_destroy.restype = None
+    lib.tf_last_error.restype = ctypes.c_char_p
+    lib.tf_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions declared in the public header."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tf_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _tensor_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_dtype(dtype):
+    return np.float32 if dtype == F32 else np.float64
+
+
+class Factorization:
+    """A tensor resident on the GPU together with its factor matrices.
+
+    coords [nnz, N] int32 and values [nnz] as numpy arrays (host) or, with
+    device_input=True, as CUDA torch tensors.  dtype F32 or F64 selects the device
+    arithmetic.  stream: a cudaStream_t handle as int (None = default stream)."""
+
+    def __init__(self, coords, values, dims, K, seed=0, dtype=F32, stream=None,
+                 device_input=False):
+        self._lib = load()
+        self.dims = [int(d) for d in dims]
+        self.N = len(self.dims)
+        self.K = int(K)
+        self.dtype = dtype
+        self.npdt = _np_dtype(dtype)
+        dims_a = np.asarray(self.dims, np.int64)
+        ctx = ctypes.c_void_p()
+        if device_input:
+            import torch
+            coords = coords.to(torch.int32).contiguous()
+            values = values.to(torch.float32 if dtype == F32 else torch.float64).contiguous()
+            nnz = int(coords.shape[0])
+            cp, vp = _tensor_ptr(coords), _tensor_ptr(values)
+            flags = INPUT_DEVICE
+            keep = (coords, values)
+        else:
+            coords = np.ascontiguousarray(coords, np.int32).reshape(-1, self.N)
+            values = np.ascontiguousarray(values, self.npdt)
+            nnz = int(coords.shape[0])
+            cp, vp = _ptr(coords), _ptr(values)
+            flags = 0
+            keep = (coords, values)
+        self.nnz = nnz
+        st = self._lib.tf_create(cp, vp, int(dtype), _ptr(dims_a), self.N, nnz, self.K,
+                                 ctypes.c_uint64(seed), ctypes.c_void_p(stream or 0), flags,
+                                 ctypes.byref(ctx))
+        del keep
+        if st != OK:
+            raise TFError(st, self._lib.tf_last_error(None).decode())
+        self._ctx = ctx
+
+    # -- plumbing
+    def _check(self, st):
+        if st != OK:
+            raise TFError(st, self._lib.tf_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.tf_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    # -- the method
+    def sweep(self, C, lam, T_in=1, order=None, weighted=False):
+        o = None if order is None else np.ascontiguousarray(order, np.int32)
+        self._check(self._lib.tf_sals_sweep_ex(self._ctx, int(C), float(lam), int(T_in),
+                                               _ptr(o), WEIGHTED_LAMBDA if weighted else 0))
+
+    def loss(self, lam, weighted=False):
+        l, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.tf_loss(self._ctx, float(lam), WEIGHTED_LAMBDA if weighted else 0,
+                                      ctypes.byref(l), ctypes.byref(r)))
+        return l.value, r.value
+
+    def foldin(self, mode, other, values, lam):
+        other = np.ascontiguousarray(other, np.int32).reshape(-1, self.N - 1)
+        values = np.ascontiguousarray(values, self.npdt)
+        out = np.zeros(self.K, self.npdt)
+        self._check(self._lib.tf_foldin(self._ctx, int(mode), _ptr(other), _ptr(values),
+                                        int(other.shape[0]), float(lam), _ptr(out)))
+        return out
+
+    # -- state
+    def factors(self, n):
+        out = np.empty((self.dims[n], self.K), self.npdt)
+        self._check(self._lib.tf_get_factors(self._ctx, int(n), _ptr(out)))
+        return out
+
+    def set_factors(self, n, A):
+        A = np.ascontiguousarray(A, self.npdt).reshape(self.dims[n], self.K)
+        self._check(self._lib.tf_set_factors(self._ctx, int(n), _ptr(A)))
+
+    def grouping(self, n, with_perm=True):
+        off = np.empty(self.dims[n] + 1, np.int64)
+        perm = np.empty(max(self.nnz, 1), np.int64) if with_perm else None
+        self._check(self._lib.tf_get_grouping(self._ctx, int(n), _ptr(off), _ptr(perm)))
+        return off, (perm[: self.nnz] if with_perm else None)
+
+    def residual(self):
+        out = np.empty(max(self.nnz, 1), self.npdt)
+        self._check(self._lib.tf_get_residual(self._ctx, _ptr(out)))
+        return out[: self.nnz]
+
+    def counters(self):
+        c = np.zeros(8, np.int64)
+        self._check(self._lib.tf_get_counters(self._ctx, _ptr(c)))
+        keys = ["singular_rows", "sweeps", "last_sweep_launches", "items", "split_rows", "bins",
+                "loss_launches"]
+        return {k: int(v) for k, v in zip(keys, c)}
+
+    def default_order(self, sweep, C):
+        out = np.empty(self.K, np.int32)
+        self._check(self._lib.tf_default_order(self._ctx, int(sweep), int(C), _ptr(out)))
+        return out
+
+    def set_schedule(self, policy=SCHED_LPT, P=0):
+        self._check(self._lib.tf_set_schedule(self._ctx, int(policy), int(P)))
+
+    KINDS = ["pack", "mode_pass", "combine", "loss", "other"]
+
+    def profile(self, enable=True):
+        self._check(self._lib.tf_profile(self._ctx, 1 if enable else 0))
+
+    def get_profile(self):
+        n = np.zeros(5, np.int64)
+        ms = np.zeros(5, np.float64)
+        self._check(self._lib.tf_get_profile(self._ctx, _ptr(n), _ptr(ms)))
+        return {k: (int(a), float(b)) for k, a, b in zip(self.KINDS, n, ms)}
+
+    def sync(self):
+        self._check(self._lib.tf_sync(self._ctx))
+
+
+# ---------------------------------------------------------------- host-only calls
+
+def assign_rows(policy, dims, row_nnz, M, seed=0):
+    """Row -> bin of every mode (Algorithm 3 with SCHED_GREEDY).  No GPU needed."""
+    lib = load()
+    dims_a = np.asarray(dims, np.int64)
+    rn = [np.ascontiguousarray(v, np.int64) for v in row_nnz]
+    out = [np.zeros(max(int(d), 1), np.int32) for d in dims]
+    prn = (ctypes.c_void_p * len(rn))(*[a.ctypes.data for a in rn])
+    pout = (ctypes.c_void_p * len(out))(*[a.ctypes.data for a in out])
+    st = lib.tf_assign_rows(int(policy), len(dims), _ptr(dims_a), prn, int(M),
+                            ctypes.c_uint64(seed), pout)
+    if st != OK:
+        raise TFError(st, "tf_assign_rows failed")
+    return [o[: int(d)] for o, d in zip(out, dims)]
+
+
+def plan_mode(off, P, cap=0, policy=SCHED_LPT, seed=0):
+    """Work items of one mode (numpy structured array), number of partial slots, bin_ptr."""
+    lib = load()
+    off = np.ascontiguousarray(off, np.int64)
+    I = len(off) - 1
+    n_items, n_slots = ctypes.c_int64(), ctypes.c_int64()
+    bin_ptr = np.zeros(P + 1, np.int64)
+    st = lib.tf_plan_mode(_ptr(off), I, int(P), int(cap), int(policy), ctypes.c_uint64(seed),
+                          None, 0, ctypes.byref(n_items), ctypes.byref(n_slots), None)
+    if st not in (OK, ENOMEM):
+        raise TFError(st, "tf_plan_mode failed")
+    items = np.zeros(max(n_items.value, 1), ITEM_DTYPE)
+    st = lib.tf_plan_mode(_ptr(off), I, int(P), int(cap), int(policy), ctypes.c_uint64(seed),
+                          _ptr(items), n_items.value, ctypes.byref(n_items),
+                          ctypes.byref(n_slots), _ptr(bin_ptr))
+    if st != OK:
+        raise TFError(st, "tf_plan_mode failed")
+    return items[: n_items.value], n_slots.value, bin_ptr
+
+
+def version():
+    return load().tf_version().decode()

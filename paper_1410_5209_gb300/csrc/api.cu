@@ -1,0 +1,900 @@
+// C ABI of the SALS / CDTF library: context lifecycle, layout construction and the
+// sweep driver.  Everything the method computes runs in the kernels of this library;
+// the host only validates arguments, plans the row schedule once per tensor, and
+// queues kernels on the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "sweep.cuh"
+
+namespace tfs {
+
+template <class T>
+struct Buf {  // owning device buffer
+    T *p = nullptr;
+    size_t n = 0;
+    Buf() = default;
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    ~Buf() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        reset();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            throw ApiError{TF_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) +
+                                          " bytes failed"};
+        }
+        n = count;
+    }
+    void ensure(size_t count) {
+        if (count > n) alloc(count);
+    }
+};
+
+struct ModeLayout {
+    int64_t I = 0;
+    Buf<int64_t> off;       // [I + 1]
+    Buf<int32_t> perm;      // [nnz] canonical index per sorted position
+    Buf<int32_t> oidx;      // [(N-1) * nnz] other-mode indices, mode order
+    Buf<tf_item> items;
+    Buf<int64_t> bin_ptr;   // [P + 1]
+    Buf<SplitRow> split;
+    int64_t n_items = 0, n_slots = 0;
+    int n_split = 0;
+    int P = 0;
+    int omode[kMaxModes - 1];
+};
+
+struct CtxBase {
+    std::string err;
+    tf_dtype dtype;
+    virtual ~CtxBase() = default;
+};
+
+template <class T>
+struct Impl : CtxBase {
+    int N = 0, K = 0;
+    int64_t nnz = 0;
+    std::vector<int64_t> dims;
+    cudaStream_t st = nullptr;
+    uint64_t seed = 0;
+    int num_sms = 0;
+    tf_sched_policy policy = TF_SCHED_LPT;
+    int P = 0;
+
+    Buf<T> x;                      // canonical values
+    Buf<T> A[kMaxModes];           // factor matrices
+    Buf<T> res[kMaxModes];         // residual copies, mode-n order
+    Buf<T> Z[kMaxModes];           // packed slices
+    ModeLayout mode[kMaxModes];
+    Buf<T> partials;
+    Buf<int32_t> d_order, d_Q;
+    Buf<DeviceStatus> stat;
+    Buf<unsigned long long> ticket;  // bin counter of the mode passes
+    unsigned long long ticket_base = 0;
+    Buf<double> red;               // reduction scratch
+    Buf<int64_t> d_dims;
+    Buf<int32_t> f_other;          // fold-in scratch
+    Buf<T> f_x, f_out;
+    int32_t *h_order = nullptr;    // pinned staging of the column order
+    cudaEvent_t order_ev = nullptr;
+    bool order_pending = false;
+
+    // kernel timing (tf_profile): event pairs per launch, folded in at tf_get_profile
+    bool prof_on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
+    std::vector<int> prof_kind;
+    int64_t prof_launches[TF_KIND_COUNT] = {0};
+    double prof_ms[TF_KIND_COUNT] = {0};
+
+    int Cq = 0, W_last = 0;        // columns Q held by the copies' R-hat, slice stride
+    bool dirty = false;            // residual copies must be rebuilt from the factors
+    bool a0_zero = true;           // A^(1) known to be zero (R = X)
+    int64_t sweeps = 0, last_launches = 0, loss_launches = 0;
+    int64_t launches = 0;
+
+    ~Impl() override {
+        if (h_order) cudaFreeHost(h_order);
+        if (order_ev) cudaEventDestroy(order_ev);
+        for (auto &pr : prof_pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    }
+
+    // Brackets one launch with events when profiling is on.
+    template <class F>
+    void timed(int kind, F &&launch) {
+        if (!prof_on) {
+            launch();
+            return;
+        }
+        cudaEvent_t a, b;
+        TFS_CUDA(cudaEventCreate(&a));
+        TFS_CUDA(cudaEventCreate(&b));
+        TFS_CUDA(cudaEventRecord(a, st));
+        launch();
+        TFS_CUDA(cudaEventRecord(b, st));
+        prof_pending.push_back({a, b});
+        prof_kind.push_back(kind);
+    }
+
+    void profile(int enable) {
+        TFS_CUDA(cudaStreamSynchronize(st));
+        for (auto &pr : prof_pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        prof_pending.clear();
+        prof_kind.clear();
+        for (int k = 0; k < TF_KIND_COUNT; ++k) {
+            prof_launches[k] = 0;
+            prof_ms[k] = 0.0;
+        }
+        prof_on = enable != 0;
+    }
+
+    void get_profile(int64_t *launches_out, double *ms_out) {
+        TFS_CUDA(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < prof_pending.size(); ++i) {
+            float ms = 0.f;
+            TFS_CUDA(cudaEventElapsedTime(&ms, prof_pending[i].first, prof_pending[i].second));
+            prof_launches[prof_kind[i]] += 1;
+            prof_ms[prof_kind[i]] += ms;
+            cudaEventDestroy(prof_pending[i].first);
+            cudaEventDestroy(prof_pending[i].second);
+        }
+        prof_pending.clear();
+        prof_kind.clear();
+        for (int k = 0; k < TF_KIND_COUNT; ++k) {
+            if (launches_out) launches_out[k] = prof_launches[k];
+            if (ms_out) ms_out[k] = prof_ms[k];
+        }
+    }
+
+    // ------------------------------------------------------------ construction
+    void create(const int32_t *coords, const void *values, const int64_t *dims_in, int N_,
+                int64_t nnz_, int K_, uint64_t seed_, cudaStream_t st_, uint32_t flags) {
+        N = N_;
+        K = K_;
+        nnz = nnz_;
+        seed = seed_;
+        st = st_;
+        dims.assign(dims_in, dims_in + N);
+        int dev = 0;
+        TFS_CUDA(cudaGetDevice(&dev));
+        TFS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        P = num_sms * 32;
+        stat.alloc(1);
+        TFS_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(DeviceStatus), st));
+        ticket.alloc(1);
+        TFS_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned long long), st));
+        ticket_base = 0;
+        red.alloc(4096);
+        d_dims.alloc(N);
+        TFS_CUDA(cudaMemcpyAsync(d_dims.p, dims.data(), N * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st));
+        TFS_CUDA(cudaMallocHost(&h_order, sizeof(int32_t) * (size_t)K));
+        TFS_CUDA(cudaEventCreateWithFlags(&order_ev, cudaEventDisableTiming));
+        d_order.alloc(K);
+        d_Q.alloc(K);
+
+        const bool on_dev = flags & TF_INPUT_DEVICE;
+        const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        x.alloc(nnz);
+        if (nnz > 0)
+            TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), kind, st));
+
+        // canonical coordinates -> SoA with range check
+        Buf<int32_t> soa;
+        soa.alloc((size_t)N * nnz);
+        {
+            Buf<int32_t> rowmajor;
+            const int32_t *src = coords;
+            if (!on_dev && nnz > 0) {
+                rowmajor.alloc((size_t)N * nnz);
+                TFS_CUDA(cudaMemcpyAsync(rowmajor.p, coords, (size_t)N * nnz * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, st));
+                src = rowmajor.p;
+            }
+            launch_transpose_check(src, N, nnz, d_dims.p, soa.p, stat.p, st);
+            DeviceStatus s = read_status();
+            if (s.bits & kStatRange)
+                throw ApiError{TF_ERANGE, "a coordinate is negative or not below its mode length"};
+        }
+
+        // per-mode sorted layout
+        SortWorkspace ws;
+        Buf<uint32_t> keys;
+        keys.alloc(nnz);
+        try {
+            for (int n = 0; n < N; ++n) {
+                ModeLayout &L = mode[n];
+                L.I = dims[n];
+                L.perm.alloc(nnz);
+                L.off.alloc(L.I + 1);
+                launch_iota(L.perm.p, nnz, st);
+                for (int t = N - 1; t >= 0; --t) {  // least significant mode first
+                    const int m = (n + t) % N;
+                    launch_gather_keys(soa.p + (size_t)m * nnz, L.perm.p, keys.p, nnz, st);
+                    radix_sort_pairs(keys.p, L.perm.p, nnz, ceil_log2_u64((uint64_t)dims[m]), ws,
+                                     st);
+                }
+                launch_offsets(keys.p, nnz, L.I, L.off.p, st);
+                if (n == 0) {
+                    launch_dup_check(soa.p, N, nnz, L.perm.p, stat.p, st);
+                    DeviceStatus s = read_status();
+                    if (s.bits & kStatDup)
+                        throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
+                }
+                L.oidx.alloc((size_t)std::max(N - 1, 1) * nnz);
+                int t = 0;
+                for (int l = 0; l < N; ++l) {
+                    if (l == n) continue;
+                    L.omode[t] = l;
+                    launch_gather_i32(soa.p + (size_t)l * nnz, L.perm.p, L.oidx.p + (size_t)t * nnz,
+                                      nnz, st);
+                    ++t;
+                }
+            }
+        } catch (...) {
+            ws.release();
+            throw;
+        }
+        ws.release();
+        keys.reset();
+        soa.reset();
+
+        for (int n = 0; n < N; ++n) plan(n);
+
+        // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
+        const double std = pow((double)K, -1.0 / (2.0 * N));
+        for (int n = 0; n < N; ++n) {
+            A[n].alloc((size_t)dims[n] * K);
+            if (n == 0)
+                TFS_CUDA(cudaMemsetAsync(A[n].p, 0, (size_t)dims[n] * K * sizeof(T), st));
+            else
+                launch_init_normal<T>(A[n].p, dims[n] * K, seed, (uint64_t)n, std, st);
+            res[n].alloc(nnz);
+        }
+        a0_zero = true;
+        rebuild_residuals();
+        TFS_CUDA(cudaStreamSynchronize(st));
+    }
+
+    void plan(int n) {
+        ModeLayout &L = mode[n];
+        std::vector<int64_t> off((size_t)L.I + 1);
+        TFS_CUDA(cudaMemcpyAsync(off.data(), L.off.p, off.size() * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        std::vector<tf_item> items;
+        std::vector<int64_t> bin_ptr;
+        int64_t n_slots = 0;
+        tf_status s = plan_mode(off.data(), L.I, P, 0, policy, seed, items, n_slots, bin_ptr);
+        if (s != TF_OK) throw ApiError{s, "row scheduling failed"};
+        // split rows: consecutive slots of one row, in entry order
+        std::vector<tf_item> chunks;
+        for (const auto &it : items)
+            if (it.slot >= 0) chunks.push_back(it);
+        std::sort(chunks.begin(), chunks.end(),
+                  [](const tf_item &a, const tf_item &b) { return a.slot < b.slot; });
+        std::vector<SplitRow> split;
+        for (size_t i = 0; i < chunks.size();) {
+            size_t j = i;
+            while (j < chunks.size() && chunks[j].row == chunks[i].row) ++j;
+            const int64_t r = chunks[i].row;
+            split.push_back({chunks[i].row, chunks[i].slot, (int32_t)(j - i), 0,
+                             off[r + 1] - off[r]});
+            i = j;
+        }
+        L.P = P;
+        L.n_items = (int64_t)items.size();
+        L.n_slots = n_slots;
+        L.n_split = (int)split.size();
+        L.items.alloc(items.size());
+        L.bin_ptr.alloc(bin_ptr.size());
+        L.split.alloc(split.size());
+        if (!items.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.items.p, items.data(), items.size() * sizeof(tf_item),
+                                     cudaMemcpyHostToDevice, st));
+        TFS_CUDA(cudaMemcpyAsync(L.bin_ptr.p, bin_ptr.data(), bin_ptr.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st));
+        if (!split.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.split.p, split.data(), split.size() * sizeof(SplitRow),
+                                     cudaMemcpyHostToDevice, st));
+        TFS_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+    }
+
+    DeviceStatus read_status() {
+        DeviceStatus s;
+        TFS_CUDA(cudaMemcpyAsync(&s, stat.p, sizeof(s), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        return s;
+    }
+
+    // ------------------------------------------------------------ residual copies
+    void rebuild_residuals() {
+        for (int n = 0; n < N; ++n) {
+            InitArgs<T> a{};
+            const ModeLayout &L = mode[n];
+            a.items = L.items.p;
+            a.bin_ptr = L.bin_ptr.p;
+            a.P = L.P;
+            a.N = N;
+            a.n = n;
+            a.K = K;
+            a.model_zero = a0_zero ? 1 : 0;
+            for (int t = 0; t < N - 1; ++t) {
+                a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+                a.Ao[t] = A[L.omode[t]].p;
+            }
+            a.An = A[n].p;
+            a.x = x.p;
+            a.perm = L.perm.p;
+            a.res = res[n].p;
+            timed(TF_KIND_OTHER, [&] { launch_init_res<T>(a, st); });
+        }
+        Cq = 0;
+        dirty = false;
+    }
+
+    template <class Args>
+    void fill_other(Args &a, int n, const ModeLayout &L, int W) {
+        for (int t = 0; t < N - 1; ++t) {
+            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.Zo[t] = Z[L.omode[t]].p;
+        }
+        (void)W;
+    }
+
+    // copies: R-hat of columns Q  ->  true residual (subtract Q's part)
+    void flush_q() {
+        if (Cq == 0) return;
+        for (int n = 0; n < N; ++n) {
+            ResArgs<T> a{};
+            const ModeLayout &L = mode[n];
+            a.items = L.items.p;
+            a.bin_ptr = L.bin_ptr.p;
+            a.P = L.P;
+            a.N = N;
+            a.n = n;
+            a.W = W_last;
+            a.Cq = Cq;
+            a.what = 2;
+            fill_other(a, n, L, W_last);
+            a.Zn = Z[n].p;
+            a.res = res[n].p;
+            timed(TF_KIND_OTHER, [&] { launch_res<T>(a, pass_blocks(L.P), st); });
+        }
+        Cq = 0;
+    }
+
+    // ------------------------------------------------------------ the sweep
+    void sweep(int C, float lambda, int T_in, const int32_t *order, uint32_t flags) {
+        if (C < 1 || C > K) throw ApiError{TF_EINVAL, "C must be in 1..K"};
+        if (T_in < 1) throw ApiError{TF_EINVAL, "T_in must be >= 1"};
+        if (!(lambda >= 0.0f) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
+        const int CM = pick_cm(C);
+        if (CM == 0) throw ApiError{TF_EINVAL, "C > 16 is not supported by this build"};
+        int64_t launches0 = launches;
+        if (dirty) {
+            rebuild_residuals();
+            launches += N;
+        }
+        if (Cq > CM) {
+            flush_q();
+            launches += N;
+        }
+        // column order -> device
+        if (order_pending) {
+            TFS_CUDA(cudaEventSynchronize(order_ev));
+            order_pending = false;
+        }
+        if (order) {
+            std::vector<char> seen(K, 0);
+            for (int k = 0; k < K; ++k) {
+                if (order[k] < 0 || order[k] >= K || seen[order[k]])
+                    throw ApiError{TF_EINVAL, "col_order is not a permutation of 0..K-1"};
+                seen[order[k]] = 1;
+            }
+            memcpy(h_order, order, sizeof(int32_t) * K);
+        } else {
+            default_order((int)sweeps, C, h_order);
+        }
+        TFS_CUDA(cudaMemcpyAsync(d_order.p, h_order, sizeof(int32_t) * K, cudaMemcpyHostToDevice,
+                                 st));
+        TFS_CUDA(cudaEventRecord(order_ev, st));
+        order_pending = true;
+
+        const int W = ((2 * C + std::max(C, Cq)) + 3) / 4 * 4;
+        const int off_old = C, off_prev = 2 * C;
+        int64_t max_slots = 0;
+        for (int n = 0; n < N; ++n) {
+            Z[n].ensure((size_t)dims[n] * W);
+            max_slots = std::max(max_slots, mode[n].n_slots);
+        }
+        partials.ensure((size_t)std::max<int64_t>(max_slots, 1) * partial_stride(CM));
+
+        const int grid = mode_pass_grid<T>(CM, P, num_sms);
+        const int nsplit = (K + C - 1) / C;
+        int cq = Cq;
+        const int32_t *Qp = d_Q.p;
+        for (int s = 0; s < nsplit; ++s) {
+            const int Cs = (s == nsplit - 1) ? K - s * C : C;
+            const int32_t *Sp = d_order.p + (size_t)s * C;
+            PackArgs<T> pk{};
+            pk.N = N;
+            pk.row_base[0] = 0;
+            for (int l = 0; l < N; ++l) {
+                pk.Z[l] = Z[l].p;
+                pk.A[l] = A[l].p;
+                pk.row_base[l + 1] = pk.row_base[l] + dims[l];
+            }
+            pk.K = K;
+            pk.W = W;
+            pk.C = Cs;
+            pk.Cq = cq;
+            pk.off_old = off_old;
+            pk.off_prev = off_prev;
+            pk.S = Sp;
+            pk.Q = Qp;
+            timed(TF_KIND_PACK, [&] { launch_pack<T>(pk, st); });
+            ++launches;
+            for (int t = 0; t < T_in; ++t) {
+                for (int n = 0; n < N; ++n) {
+                    const ModeLayout &L = mode[n];
+                    PassArgs<T> a{};
+                    a.items = L.items.p;
+                    a.bin_ptr = L.bin_ptr.p;
+                    a.P = L.P;
+                    a.N = N;
+                    a.n = n;
+                    a.C = Cs;
+                    a.Cq = cq;
+                    a.W = W;
+                    a.off_old = off_old;
+                    a.off_prev = off_prev;
+                    a.first = (t == 0);
+                    a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
+                    a.lambda = (T)lambda;
+                    for (int u = 0; u < N - 1; ++u) {
+                        a.oidx[u] = L.oidx.p + (size_t)u * nnz;
+                        a.Zo[u] = Z[L.omode[u]].p;
+                    }
+                    a.Zn = Z[n].p;
+                    a.res = res[n].p;
+                    a.A_n = A[n].p;
+                    a.K = K;
+                    a.S = Sp;
+                    a.partials = partials.p;
+                    a.stat = stat.p;
+                    a.ticket = ticket.p;
+                    a.ticket_base = ticket_base;
+                    // every launched warp takes one ticket past the last bin
+                    ticket_base += (unsigned long long)L.P + (unsigned long long)grid * (kPassThreads / kWarp);
+                    timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, grid, st); });
+                    ++launches;
+                    if (L.n_split > 0) {
+                        timed(TF_KIND_COMBINE,
+                              [&] { launch_combine<T>(a, CM, L.split.p, L.n_split, st); });
+                        ++launches;
+                    }
+                }
+            }
+            cq = Cs;
+            Qp = Sp;
+        }
+        // the copies now hold R-hat of the last split's columns
+        TFS_CUDA(cudaMemcpyAsync(d_Q.p, Qp, sizeof(int32_t) * cq, cudaMemcpyDeviceToDevice, st));
+        Cq = cq;
+        W_last = W;
+        ++sweeps;
+        last_launches = launches - launches0;
+    }
+
+    void default_order(int sweep_idx, int C, int32_t *out) const {
+        for (int k = 0; k < K; ++k) out[k] = k;
+        if (C == 1) return;  // CDTF keeps a fixed column order (Section 3.1)
+        // Fisher-Yates driven by splitmix64 of (seed, sweep)
+        uint64_t s = mix64_host(seed ^ mix64_host(0xC01D0000ull + (uint64_t)sweep_idx));
+        for (int k = K - 1; k > 0; --k) {
+            s = mix64_host(s);
+            const int j = (int)(s % (uint64_t)(k + 1));
+            std::swap(out[k], out[j]);
+        }
+    }
+
+    // ------------------------------------------------------------ loss
+    void loss(float lambda, uint32_t flags, double *loss_out, double *rmse_out) {
+        if (dirty) rebuild_residuals();
+        const ModeLayout &L = mode[0];
+        const int blocks = pass_blocks(L.P);
+        const int reg_blocks = 256;
+        red.ensure((size_t)blocks + (size_t)N * reg_blocks + 4);
+        ResArgs<T> a{};
+        a.items = L.items.p;
+        a.bin_ptr = L.bin_ptr.p;
+        a.P = L.P;
+        a.N = N;
+        a.n = 0;
+        a.W = W_last;
+        a.Cq = Cq;
+        a.what = 0;
+        for (int t = 0; t < N - 1; ++t) {
+            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.Zo[t] = Z[L.omode[t]].p;
+        }
+        a.Zn = Z[0].p;
+        a.res = res[0].p;
+        a.block_out = red.p + 2;
+        double *regp = red.p + 2 + blocks;
+        timed(TF_KIND_LOSS, [&] {
+            launch_res<T>(a, blocks, st);
+            launch_sum_blocks(red.p + 2, blocks, red.p + 0, st);
+            for (int n = 0; n < N; ++n)
+                launch_reg<T>(A[n].p, dims[n], K,
+                              (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,
+                              regp + (size_t)n * reg_blocks, reg_blocks, st);
+            launch_sum_blocks(regp, N * reg_blocks, red.p + 1, st);
+        });
+        loss_launches = 3 + N;
+        double h[2];
+        TFS_CUDA(cudaMemcpyAsync(h, red.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+        if (loss_out) *loss_out = h[0] + (double)lambda * h[1];
+        if (rmse_out) *rmse_out = nnz > 0 ? sqrt(h[0] / (double)nnz) : 0.0;
+    }
+
+    void get_residual(T *host_r) {
+        if (dirty) rebuild_residuals();
+        Buf<T> out;
+        out.alloc(nnz);
+        const ModeLayout &L = mode[0];
+        ResArgs<T> a{};
+        a.items = L.items.p;
+        a.bin_ptr = L.bin_ptr.p;
+        a.P = L.P;
+        a.N = N;
+        a.n = 0;
+        a.W = W_last;
+        a.Cq = Cq;
+        a.what = 1;
+        for (int t = 0; t < N - 1; ++t) {
+            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.Zo[t] = Z[L.omode[t]].p;
+        }
+        a.Zn = Z[0].p;
+        a.res = res[0].p;
+        a.perm = L.perm.p;
+        a.out = out.p;
+        launch_res<T>(a, pass_blocks(L.P), st);
+        if (nnz > 0)
+            TFS_CUDA(cudaMemcpyAsync(host_r, out.p, nnz * sizeof(T), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+    }
+
+    void check_errors() {
+        DeviceStatus s = read_status();
+        if (s.bits & (kStatRange | kStatDup)) throw ApiError{TF_ECUDA, "device status corrupt"};
+    }
+
+    // ------------------------------------------------------------ factors
+    void set_factors(int n, const T *host_A) {
+        if (n < 0 || n >= N) throw ApiError{TF_EINVAL, "mode out of range"};
+        const size_t cnt = (size_t)dims[n] * K;
+        TFS_CUDA(cudaMemcpyAsync(A[n].p, host_A, cnt * sizeof(T), cudaMemcpyHostToDevice, st));
+        if (n == 0) {
+            bool zero = true;
+            for (size_t i = 0; i < cnt && zero; ++i) zero = (host_A[i] == T(0));
+            a0_zero = zero;
+        }
+        TFS_CUDA(cudaStreamSynchronize(st));
+        dirty = true;
+        Cq = 0;
+    }
+
+    void get_factors(int n, T *host_A) {
+        if (n < 0 || n >= N) throw ApiError{TF_EINVAL, "mode out of range"};
+        TFS_CUDA(cudaMemcpyAsync(host_A, A[n].p, (size_t)dims[n] * K * sizeof(T),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+    }
+
+    // ------------------------------------------------------------ fold-in
+    void foldin(int md, const int32_t *other, const T *vals, int64_t m, float lambda, T *out) {
+        if (md < 0 || md >= N) throw ApiError{TF_EINVAL, "mode out of range"};
+        if (m < 0) throw ApiError{TF_EINVAL, "m must be >= 0"};
+        if (!(lambda >= 0.0f)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
+        int dev = 0, maxsm = 0;
+        TFS_CUDA(cudaGetDevice(&dev));
+        TFS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (foldin_smem_bytes<T>(K) + 1024 > (size_t)maxsm)
+            throw ApiError{TF_EINVAL, "K too large for the fold-in kernel"};
+        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1));
+        f_x.ensure((size_t)std::max<int64_t>(m, 1));
+        f_out.ensure((size_t)K);
+        if (m > 0) {
+            TFS_CUDA(cudaMemcpyAsync(f_other.p, other, (size_t)m * (N - 1) * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+            TFS_CUDA(cudaMemcpyAsync(f_x.p, vals, (size_t)m * sizeof(T), cudaMemcpyHostToDevice, st));
+        }
+        FoldArgs<T> a{};
+        a.N = N;
+        a.K = K;
+        a.mode = md;
+        for (int l = 0; l < N; ++l) {
+            a.A[l] = A[l].p;
+            a.I[l] = dims[l];
+        }
+        a.m = m;
+        a.other = f_other.p;
+        a.x = f_x.p;
+        a.lambda = (T)lambda;
+        a.out = f_out.p;
+        a.stat = stat.p;
+        launch_foldin<T>(a, st);
+        DeviceStatus s = read_status();
+        const int fb = s.bits & (kStatFoldRange | kStatFoldPivot);
+        if (fb) {
+            TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
+            TFS_CUDA(cudaStreamSynchronize(st));
+            if (fb & kStatFoldRange) throw ApiError{TF_ERANGE, "fold-in index out of range"};
+            throw ApiError{TF_EINVAL, "fold-in system is not positive definite"};
+        }
+        TFS_CUDA(cudaMemcpyAsync(out, f_out.p, K * sizeof(T), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+    }
+
+    void grouping(int n, int64_t *off, int64_t *perm) {
+        if (n < 0 || n >= N) throw ApiError{TF_EINVAL, "mode out of range"};
+        const ModeLayout &L = mode[n];
+        TFS_CUDA(cudaMemcpyAsync(off, L.off.p, (L.I + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                 st));
+        std::vector<int32_t> p32;
+        if (perm && nnz > 0) {
+            p32.resize(nnz);
+            TFS_CUDA(cudaMemcpyAsync(p32.data(), L.perm.p, nnz * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st));
+        }
+        TFS_CUDA(cudaStreamSynchronize(st));
+        if (perm)
+            for (int64_t j = 0; j < nnz; ++j) perm[j] = p32[j];
+    }
+
+    void counters(int64_t *c) {
+        DeviceStatus s = read_status();
+        c[0] = (int64_t)s.singular_rows;
+        c[1] = sweeps;
+        c[2] = last_launches;
+        int64_t items = 0, split = 0;
+        for (int n = 0; n < N; ++n) {
+            items += mode[n].n_items;
+            split += mode[n].n_split;
+        }
+        c[3] = items;
+        c[4] = split;
+        c[5] = P;
+        c[6] = loss_launches;
+        c[7] = 0;
+    }
+
+    void set_schedule(tf_sched_policy pol, int P_) {
+        if (pol < TF_SCHED_LPT || pol > TF_SCHED_RAN) throw ApiError{TF_EINVAL, "bad policy"};
+        if (P_ < 0) throw ApiError{TF_EINVAL, "P must be >= 0"};
+        TFS_CUDA(cudaStreamSynchronize(st));
+        policy = pol;
+        P = P_ > 0 ? P_ : num_sms * 32;
+        for (int n = 0; n < N; ++n) plan(n);
+    }
+};
+
+}  // namespace tfs
+
+struct tf_ctx {
+    std::unique_ptr<tfs::CtxBase> impl;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+template <class F>
+tf_status guarded(tf_ctx *ctx, F &&f) {
+    try {
+        f();
+        return TF_OK;
+    } catch (const tfs::ApiError &e) {
+        if (ctx) ctx->err = e.msg;
+        return e.status;
+    } catch (const tfs::CudaError &e) {
+        if (ctx) ctx->err = std::string(e.what) + ": " + cudaGetErrorString(e.err);
+        cudaGetLastError();
+        return e.err == cudaErrorMemoryAllocation ? TF_ENOMEM : TF_ECUDA;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->err = "host allocation failed";
+        return TF_ENOMEM;
+    } catch (...) {
+        if (ctx) ctx->err = "unexpected error";
+        return TF_ECUDA;
+    }
+}
+
+template <class F>
+tf_status dispatch(tf_ctx *ctx, F &&f) {
+    if (!ctx || !ctx->impl) return TF_EINVAL;
+    return guarded(ctx, [&] {
+        if (ctx->impl->dtype == TF_F32)
+            f(static_cast<tfs::Impl<float> &>(*ctx->impl));
+        else
+            f(static_cast<tfs::Impl<double> &>(*ctx->impl));
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+tf_status tf_create(const int32_t *coords, const void *values, tf_dtype dtype, const int64_t *dims,
+                    int N, int64_t nnz, int K, uint64_t seed, void *stream, uint32_t flags,
+                    tf_ctx **out) {
+    if (!out) return TF_EINVAL;
+    *out = nullptr;
+    g_create_err.clear();
+    if (N < 1 || N > tfs::kMaxModes || nnz < 0 || nnz > INT32_MAX || K < 1 || !dims ||
+        (nnz > 0 && (!coords || !values)) || (dtype != TF_F32 && dtype != TF_F64)) {
+        g_create_err = "invalid argument (N in 1..8, 0 <= nnz < 2^31, K >= 1, buffers non-NULL)";
+        return TF_EINVAL;
+    }
+    for (int n = 0; n < N; ++n)
+        if (dims[n] < 1 || dims[n] > INT32_MAX) {
+            g_create_err = "mode lengths must be in 1..2^31-1";
+            return TF_EINVAL;
+        }
+    tf_ctx *ctx = new (std::nothrow) tf_ctx;
+    if (!ctx) return TF_ENOMEM;
+    tf_status s = guarded(ctx, [&] {
+        if (dtype == TF_F32) {
+            auto *p = new tfs::Impl<float>();
+            p->dtype = dtype;
+            ctx->impl.reset(p);
+            p->create(coords, values, dims, N, nnz, K, seed, (cudaStream_t)stream, flags);
+        } else {
+            auto *p = new tfs::Impl<double>();
+            p->dtype = dtype;
+            ctx->impl.reset(p);
+            p->create(coords, values, dims, N, nnz, K, seed, (cudaStream_t)stream, flags);
+        }
+    });
+    if (s != TF_OK) {
+        g_create_err = ctx->err;
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return TF_OK;
+}
+
+void tf_destroy(tf_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->impl) {
+        cudaStream_t st = ctx->impl->dtype == TF_F32
+                              ? static_cast<tfs::Impl<float> &>(*ctx->impl).st
+                              : static_cast<tfs::Impl<double> &>(*ctx->impl).st;
+        cudaStreamSynchronize(st);
+    }
+    delete ctx;
+}
+
+const char *tf_last_error(const tf_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+tf_status tf_sync(tf_ctx *ctx) {
+    return dispatch(ctx, [&](auto &c) {
+        TFS_CUDA(cudaStreamSynchronize(c.st));
+        c.check_errors();
+    });
+}
+
+tf_status tf_set_factors(tf_ctx *ctx, int n, const void *host_A) {
+    if (!host_A) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.set_factors(n, static_cast<const T *>(host_A));
+    });
+}
+
+tf_status tf_get_factors(tf_ctx *ctx, int n, void *host_A) {
+    if (!host_A) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.get_factors(n, static_cast<T *>(host_A));
+    });
+}
+
+tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, float lambda, int T_in, const int32_t *col_order,
+                           uint32_t flags) {
+    return dispatch(ctx, [&](auto &c) { c.sweep(C, lambda, T_in, col_order, flags); });
+}
+
+tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, float lambda, int T_in,
+                              const int32_t *col_order) {
+    return tf_sals_sweep_ex(ctx, C, lambda, T_in, col_order, 0u);
+}
+
+tf_status tf_sals_sweep(tf_ctx *ctx, int C, float lambda, int T_in) {
+    return tf_sals_sweep_ex(ctx, C, lambda, T_in, nullptr, 0u);
+}
+
+tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_order) {
+    if (!ctx || !ctx->impl || !col_order || sweep < 0 || C < 1) return TF_EINVAL;
+    if (ctx->impl->dtype == TF_F32)
+        static_cast<const tfs::Impl<float> &>(*ctx->impl).default_order(sweep, C, col_order);
+    else
+        static_cast<const tfs::Impl<double> &>(*ctx->impl).default_order(sweep, C, col_order);
+    return TF_OK;
+}
+
+tf_status tf_loss(tf_ctx *ctx, float lambda, uint32_t flags, double *loss, double *train_rmse) {
+    return dispatch(ctx, [&](auto &c) { c.loss(lambda, flags, loss, train_rmse); });
+}
+
+tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values, int64_t m,
+                    float lambda, void *out_row) {
+    if (!out_row || (m > 0 && (!other || !values))) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.foldin(mode, other, static_cast<const T *>(values), m, lambda, static_cast<T *>(out_row));
+    });
+}
+
+tf_status tf_get_grouping(tf_ctx *ctx, int n, int64_t *off, int64_t *perm) {
+    if (!off) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { c.grouping(n, off, perm); });
+}
+
+tf_status tf_get_residual(tf_ctx *ctx, void *host_r) {
+    if (!host_r) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.get_residual(static_cast<T *>(host_r));
+    });
+}
+
+tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]) {
+    if (!counters) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { c.counters(counters); });
+}
+
+tf_status tf_profile(tf_ctx *ctx, int enable) {
+    return dispatch(ctx, [&](auto &c) { c.profile(enable); });
+}
+
+tf_status tf_get_profile(tf_ctx *ctx, int64_t *launches, double *ms) {
+    return dispatch(ctx, [&](auto &c) { c.get_profile(launches, ms); });
+}
+
+tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P) {
+    return dispatch(ctx, [&](auto &c) { c.set_schedule(policy, P); });
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// Per-split and per-sweep helper kernels: slice packing (the C columns of a split,
+// Theorem 3's "only C columns need to be resident"), residual reconstruction and
+// loss reduction (Eq. 1, accumulated in double in a fixed order), residual
+// initialisation (Section 3.1) and the default factor initialisation (Algorithm 1).
+#include <math.h>
+
+#include "sweep.cuh"
+
+namespace tfs {
+
+int pick_cm(int C) {
+    static const int cms[] = {1, 2, 4, 6, 8, 10, 12, 16};
+    for (int cm : cms)
+        if (C <= cm) return cm;
+    return 0;
+}
+
+namespace {
+
+constexpr int kResThreads = 256;
+
+template <class T>
+__global__ void k_pack(const PackArgs<T> a) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.row_base[a.N]) return;
+    int l = 0;
+    while (r >= a.row_base[l + 1]) ++l;
+    const int64_t i = r - a.row_base[l];
+    const T *Ar = a.A[l] + i * a.K;
+    T *z = a.Z[l] + i * a.W;
+    for (int c = 0; c < a.C; ++c) {
+        const T v = Ar[a.S[c]];
+        z[c] = v;
+        z[a.off_old + c] = v;
+    }
+    for (int c = 0; c < a.Cq; ++c) z[a.off_prev + c] = Ar[a.Q[c]];
+}
+
+template <class T>
+__global__ void __launch_bounds__(kResThreads) k_res(const ResArgs<T> a) {
+    __shared__ double wsum[kResThreads / kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bin = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    double acc = 0.0;
+    if (bin < a.P) {
+        for (int64_t it = a.bin_ptr[bin]; it < a.bin_ptr[bin + 1]; ++it) {
+            const tf_item item = a.items[it];
+            const T *zown = a.Zn + (int64_t)item.row * a.W;
+            const int64_t jend = item.begin + item.len;
+            for (int64_t j = item.begin + lane; j < jend; j += kWarp) {
+                T p = T(0);
+                for (int c = 0; c < a.Cq; ++c) {
+                    T q = zown[c];
+                    for (int t = 0; t < a.N - 1; ++t)
+                        q *= a.Zo[t][(int64_t)a.oidx[t][j] * a.W + c];
+                    p += q;
+                }
+                const T r = a.res[j] - p;
+                if (a.what == 0)
+                    acc += (double)r * (double)r;
+                else if (a.what == 1)
+                    a.out[a.perm[j]] = r;
+                else
+                    a.res[j] = r;
+            }
+        }
+    }
+    if (a.what != 0) return;
+    acc = warp_sum_d(acc);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kResThreads / kWarp; ++w) s += wsum[w];
+        a.block_out[blockIdx.x] = s;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kResThreads) k_init_res(const InitArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int bin = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (bin >= a.P) return;
+    for (int64_t it = a.bin_ptr[bin]; it < a.bin_ptr[bin + 1]; ++it) {
+        const tf_item item = a.items[it];
+        const T *An = a.An + (int64_t)item.row * a.K;
+        const int64_t jend = item.begin + item.len;
+        for (int64_t j = item.begin + lane; j < jend; j += kWarp) {
+            T model = T(0);
+            if (!a.model_zero) {
+                for (int k = 0; k < a.K; ++k) {
+                    T q = An[k];
+                    for (int t = 0; t < a.N - 1; ++t)
+                        q *= a.Ao[t][(int64_t)a.oidx[t][j] * a.K + k];
+                    model += q;
+                }
+            }
+            a.res[j] = a.x[a.perm[j]] - model;
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kResThreads) k_reg(const T *A, int64_t I, int K,
+                                                     const int64_t *off, double *block_out) {
+    __shared__ double wsum[kResThreads / kWarp];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double v = (double)A[i * K + k];
+            s += v * v;
+        }
+        acc += off ? s * (double)(off[i + 1] - off[i]) : s;
+    }
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kResThreads / kWarp; ++w) s += wsum[w];
+        block_out[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_blocks(const double *in, int n, double *out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += in[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_init_normal(T *A, int64_t count, uint64_t key, double std) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double u1 = (double)(mix64(key + 2 * (uint64_t)i) >> 11) * 0x1.0p-53;
+    const double u2 = (double)(mix64(key + 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
+    A[i] = (T)(std * sqrt(-2.0 * log1p(-u1)) * cospi(2.0 * u2));
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+    return (unsigned)((n > 0 ? n : 1) + threads - 1) / threads;
+}
+
+}  // namespace
+
+template <class T>
+void launch_pack(const PackArgs<T> &a, cudaStream_t st) {
+    const int64_t rows = a.row_base[a.N];
+    if (rows <= 0) return;
+    k_pack<T><<<blocks_for(rows, 256), 256, 0, st>>>(a);
+    TFS_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void launch_res(const ResArgs<T> &a, int grid_blocks, cudaStream_t st) {
+    k_res<T><<<grid_blocks, kResThreads, 0, st>>>(a);
+    TFS_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void launch_init_res(const InitArgs<T> &a, cudaStream_t st) {
+    k_init_res<T><<<pass_blocks(a.P), kResThreads, 0, st>>>(a);
+    TFS_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void launch_reg(const T *A, int64_t I, int K, const int64_t *off, double *block_out, int blocks,
+                cudaStream_t st) {
+    k_reg<T><<<blocks, kResThreads, 0, st>>>(A, I, K, off, block_out);
+    TFS_CUDA(cudaGetLastError());
+}
+
+void launch_sum_blocks(const double *in, int n, double *out, cudaStream_t st) {
+    k_sum_blocks<<<1, 256, 0, st>>>(in, n, out);
+    TFS_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, double std,
+                        cudaStream_t st) {
+    if (count <= 0) return;
+    const uint64_t key = mix64_host(seed ^ mix64_host(stream_id + 0x51A5ull));
+    k_init_normal<T><<<blocks_for(count, 256), 256, 0, st>>>(A, count, key, std);
+    TFS_CUDA(cudaGetLastError());
+}
+
+#define TFS_INST(T)                                                                        \
+    template void launch_pack<T>(const PackArgs<T> &, cudaStream_t);                       \
+    template void launch_res<T>(const ResArgs<T> &, int, cudaStream_t);                    \
+    template void launch_init_res<T>(const InitArgs<T> &, cudaStream_t);                   \
+    template void launch_reg<T>(const T *, int64_t, int, const int64_t *, double *, int,   \
+                                cudaStream_t);                                             \
+    template void launch_init_normal<T>(T *, int64_t, uint64_t, uint64_t, double, cudaStream_t);
+TFS_INST(float)
+TFS_INST(double)
+#undef TFS_INST
+
+}  // namespace tfs

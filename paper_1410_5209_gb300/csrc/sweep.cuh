@@ -1,0 +1,142 @@
+// Kernel interfaces of one SALS sweep (sweep.cu) and of the fold-in (foldin.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace tfs {
+
+// A row split across bins: its chunks wrote partial Gram/rhs to slots
+// [first_slot, first_slot + n_slots), in entry order.
+struct SplitRow {
+    int32_t row;
+    int32_t first_slot;
+    int32_t n_slots;
+    int32_t pad;
+    int64_t len;  // |Omega_i^(n)| (for weighted lambda)
+};
+
+// Packed slice layout, one row of W elements per factor row i of mode l:
+//   [0, C)                 "cur":  a^(l)_{i,S} as updated in this split
+//   [off_old, off_old + C) "old":  a^(l)_{i,S} at the start of the split
+//   [off_prev, +Cq)        "prev": a^(l)_{i,Q}, the previous split's columns (final)
+// Residual copy n holds, for its entries in mode-n order, R-hat of the split during
+// which it was last refreshed (columns Q); its first pass of a new split turns it into
+// this split's R-hat: r_hat_S = r_hat_Q - sum_{c in Q} prod_l prev + sum_{c in S} prod_l old
+// (Eq. 5 followed by the R-hat step of Algorithm 1, fused and done lazily per copy).
+template <class T>
+struct PassArgs {
+    const tf_item *items;
+    const int64_t *bin_ptr;
+    int P;
+    int N, n;       // number of modes, mode being updated
+    int C, Cq;      // |S| of this split, |Q| of the previous one (Cq <= CM)
+    int W, off_old, off_prev;
+    int first;      // first inner iteration of the split: refresh R-hat
+    int weighted;   // weighted lambda
+    T lambda;
+    const int32_t *oidx[kMaxModes - 1];  // other-mode indices, mode-n order
+    const T *Zo[kMaxModes - 1];          // packed slices of those modes
+    T *Zn;                               // packed slice of mode n
+    T *res;                              // residual copy of mode n
+    T *A_n;                              // factor matrix of mode n [I_n][K]
+    int K;
+    const int32_t *S;                    // the split's columns (device)
+    T *partials;                         // [slots][CM(CM+1)/2 + CM]
+    DeviceStatus *stat;
+    unsigned long long *ticket;          // monotone bin counter shared by all passes
+    unsigned long long ticket_base;      // its value when this launch starts
+};
+
+template <class T>
+struct PackArgs {
+    int N;
+    T *Z[kMaxModes];
+    const T *A[kMaxModes];
+    int64_t row_base[kMaxModes + 1];
+    int K, W, C, Cq, off_old, off_prev;
+    const int32_t *S, *Q;
+};
+
+// Residual of copy n against the columns held in the slices' "cur" region:
+//   r_e = res_e - sum_{c < Cq} prod_l Z_l[i_l, c]
+// what = 0: accumulate sum r^2 (double) per block; 1: out[perm[j]] = r; 2: res_e = r.
+template <class T>
+struct ResArgs {
+    const tf_item *items;
+    const int64_t *bin_ptr;
+    int P;
+    int N, n, W, Cq, what;
+    const int32_t *oidx[kMaxModes - 1];
+    const T *Zo[kMaxModes - 1];
+    const T *Zn;
+    T *res;
+    double *block_out;
+    const int32_t *perm;
+    T *out;
+};
+
+// res_e = x[perm[j]] - sum_k prod_l A_l[i_l, k]  (Section 3.1's residual), per copy.
+template <class T>
+struct InitArgs {
+    const tf_item *items;
+    const int64_t *bin_ptr;
+    int P;
+    int N, n, K, model_zero;
+    const int32_t *oidx[kMaxModes - 1];
+    const T *Ao[kMaxModes - 1];
+    const T *An;
+    const T *x;
+    const int32_t *perm;
+    T *res;
+};
+
+template <class T>
+struct FoldArgs {
+    int N, K, mode;
+    const T *A[kMaxModes];
+    int64_t I[kMaxModes];
+    int64_t m;
+    const int32_t *other;
+    const T *x;
+    T lambda;
+    T *out;
+    DeviceStatus *stat;
+};
+
+constexpr int kPassThreads = 256;
+constexpr int kCombineThreads = 512;
+constexpr int kMaxCSimt = 16;
+
+int pick_cm(int C);  // smallest instantiated register width >= C (0 if none)
+inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
+
+template <class T>
+void launch_mode_pass(const PassArgs<T> &a, int CM, int grid, cudaStream_t st);
+template <class T>
+void launch_combine(const PassArgs<T> &a, int CM, const SplitRow *rows, int n_rows,
+                    cudaStream_t st);
+template <class T>
+void launch_pack(const PackArgs<T> &a, cudaStream_t st);
+template <class T>
+void launch_res(const ResArgs<T> &a, int grid_blocks, cudaStream_t st);
+template <class T>
+void launch_init_res(const InitArgs<T> &a, cudaStream_t st);
+template <class T>
+void launch_reg(const T *A, int64_t I, int K, const int64_t *off, double *block_out, int blocks,
+                cudaStream_t st);
+void launch_sum_blocks(const double *in, int n, double *out, cudaStream_t st);
+template <class T>
+void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, double std,
+                        cudaStream_t st);
+template <class T>
+void launch_foldin(const FoldArgs<T> &a, cudaStream_t st);
+template <class T>
+size_t foldin_smem_bytes(int K);
+
+inline int pass_blocks(int P) { return (P * kWarp + kPassThreads - 1) / kPassThreads; }
+
+// Blocks of a mode-pass launch (at most one resident wave) for register width CM.
+template <class T>
+int mode_pass_grid(int CM, int P, int num_sms);
+
+}  // namespace tfs

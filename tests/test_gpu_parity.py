@@ -1,0 +1,368 @@
+"""GPU <-> oracle parity through the C ABI.
+
+Tolerances (stated by the task for this method): sorting, offsets and permutations
+bit-exact; a row update from identical inputs within 1e-5 relative in FP32; training
+RMSE after a fixed number of sweeps within 1e-3 relative.  The FP64 device path is
+held to 1e-9 (only summation order differs from the oracle)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1410_5209_gb300 as tf
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1410_5209_gb300 import build
+    build.build()
+
+
+def make(p, dtype=tf.F64):
+    """Device context and oracle inputs holding exactly the same numbers (for the FP32
+    path the values and initial factors are rounded to float32 on both sides)."""
+    c, x = p.numpy()
+    A = [a.numpy().astype(np.float64) for a in p.init_factors()]
+    if dtype == tf.F32:
+        x = x.astype(np.float32).astype(np.float64)
+        A = [a.astype(np.float32).astype(np.float64) for a in A]
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=dtype)
+    for n in range(p.N):
+        f.set_factors(n, A[n])
+    return f, oracle.Tensor(c, x, p.dims), A
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def ragged_problem(seed=21):
+    # several tiles of the radix sort (4096 keys), ragged tail, mode lengths that are
+    # not powers of two, a mode with many empty rows
+    return synth.small(seed, (301, 157, 1000), 9_973, 4, 6)
+
+
+# --------------------------------------------------------------------------- layout
+
+
+@pytest.mark.parametrize("prob", ["parity", "ragged", "skew"])
+def test_grouping_bit_exact(prob):
+    if prob == "parity":
+        p = synth.parity_3way()
+    elif prob == "ragged":
+        p = ragged_problem()
+    else:
+        p = synth.small(5, (2000, 3000, 50), 60_000, 3, 4, modes=["zipf", "zipf", "uniform"])
+    f, t, _ = make(p)
+    for n in range(p.N):
+        off, perm = f.grouping(n)
+        ooff, operm = oracle.group(t, n)
+        assert np.array_equal(off, ooff)
+        assert np.array_equal(perm, operm)
+
+
+def test_create_validates_coordinates():
+    c = np.array([[0, 0, 0], [1, 2, 0]], np.int32)
+    with pytest.raises(tf.TFError) as e:
+        tf.Factorization(c, np.ones(2), [2, 2, 1], 2, dtype=tf.F64)
+    assert e.value.status == tf.ERANGE
+    c = np.array([[0, 1, 0], [1, 1, 0], [0, 1, 0]], np.int32)
+    with pytest.raises(tf.TFError) as e:
+        tf.Factorization(c, np.ones(3), [2, 2, 1], 2, dtype=tf.F64)
+    assert e.value.status == tf.EDUP
+
+
+def test_init_residual_is_x():
+    """Algorithm 1 initialisation (A^(1) = 0) gives R = X exactly."""
+    p = synth.parity_3way()
+    c, x = p.numpy()
+    f = tf.Factorization(c, x, p.dims, p.K, seed=3, dtype=tf.F64)
+    assert np.all(f.factors(0) == 0)
+    assert np.array_equal(f.residual(), x)
+    L, rmse = f.loss(1.0)
+    A = [f.factors(n) for n in range(3)]
+    assert np.isclose(L, x @ x + sum((a * a).sum() for a in A), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------- sweeps
+
+
+@pytest.mark.parametrize("C", [1, 5])
+def test_fp64_sweeps_match_oracle(C):
+    """FP64 device path vs FP64 oracle, 5 sweeps of the parity workload."""
+    p = synth.parity_3way()
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(5):
+        order = p.column_order(s, C)
+        f.sweep(C, 1.0, 1, order)
+        oracle.sals_sweep(t, A, r, C, 1.0, 1, order)
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    assert rel(f.residual(), r) < 1e-9
+    L, rmse = f.loss(1.0)
+    Lo, rmseo = oracle.loss(t, r, A, 1.0)
+    assert abs(L - Lo) <= 1e-9 * Lo and abs(rmse - rmseo) <= 1e-9 * rmseo
+
+
+@pytest.mark.parametrize("C", [1, 5])
+def test_fp32_rmse_after_five_sweeps(C):
+    """FP32 device path vs FP64 oracle: training RMSE after 5 sweeps within 1e-3."""
+    p = synth.parity_3way()
+    f, t, A = make(p, tf.F32)
+    r = oracle.residual(t, A)
+    for s in range(5):
+        order = p.column_order(s, C)
+        f.sweep(C, 1.0, 1, order)
+        oracle.sals_sweep(t, A, r, C, 1.0, 1, order)
+    _, rmse = f.loss(1.0)
+    _, rmseo = oracle.loss(t, r, A, 1.0)
+    assert abs(rmse - rmseo) <= 1e-3 * rmseo
+
+
+@pytest.mark.parametrize("C", [1, 5, 10])
+def test_fp32_row_update_from_identical_inputs(C):
+    """The first split's mode-1 rows are computed from identical inputs on both sides
+    (A^(2), A^(3) as given, R-hat = X) and are not touched again during the sweep:
+    per-row relative error <= 1e-5 in FP32."""
+    p = synth.parity_3way()
+    f, t, A = make(p, tf.F32)
+    r = oracle.residual(t, A)
+    order = p.column_order(0, C)
+    f.sweep(C, 1.0, 1, order)
+    oracle.sals_sweep(t, A, r, C, 1.0, 1, order)
+    S = order[:C]
+    g = f.factors(0)[:, S].astype(np.float64)
+    o = A[0][:, S]
+    num = np.linalg.norm(g - o, axis=1)
+    den = np.maximum(np.linalg.norm(o, axis=1), 1e-30)
+    assert np.max(num / den) <= 1e-5
+
+
+def test_ragged_T_in_and_uneven_split():
+    """C not dividing K (last split smaller), T_in = 2, mode with empty rows."""
+    p = ragged_problem()
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, 4)
+        f.sweep(4, 0.3, 2, order)
+        oracle.sals_sweep(t, A, r, 4, 0.3, 2, order)
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    assert rel(f.residual(), r) < 1e-9
+
+
+def test_weighted_lambda_matches_oracle():
+    p = ragged_problem(22)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    order = p.column_order(0, 3)
+    f.sweep(3, 0.05, 1, order, weighted=True)
+    oracle.sals_sweep(t, A, r, 3, 0.05, 1, order, weighted=True)
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    L, _ = f.loss(0.05, weighted=True)
+    Lo, _ = oracle.loss(t, r, A, 0.05, weighted=True)
+    assert abs(L - Lo) <= 1e-9 * Lo
+
+
+def test_residual_invariant_fp32():
+    """The stored residual equals x - model recomputed from the device's own factors."""
+    p = synth.parity_3way()
+    f, t, _ = make(p, tf.F32)
+    for s in range(3):
+        f.sweep(5, 1.0, 1, p.column_order(s, 5))
+    A = [f.factors(n).astype(np.float64) for n in range(3)]
+    model = np.ones((t.nnz, p.K))
+    for n in range(3):
+        model *= A[n][t.coords[:, n]]
+    ref = t.x - model.sum(1)
+    assert np.max(np.abs(f.residual() - ref)) <= 1e-5 * np.max(np.abs(t.x))
+
+
+@pytest.mark.parametrize("C", [1, 4])
+def test_loss_never_increases_fp64(C):
+    """Theorem 1 on the device: every split is an exact block minimisation."""
+    p = synth.small(31, (200, 150, 40), 20_000, 3, 8)
+    f, t, _ = make(p, tf.F64)
+    prev = f.loss(0.5)[0]
+    for s in range(4):
+        f.sweep(C, 0.5, 1, p.column_order(s, C))
+        cur = f.loss(0.5)[0]
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
+def test_singular_rows_left_unchanged():
+    """lambda = 0 with empty rows: pivot 0, row unchanged and counted (both sides)."""
+    p = synth.small(32, (500, 40, 30), 1_500, 2, 3)   # many empty rows in mode 1
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    bad_o = oracle.sals_sweep(t, A, r, 1, 0.0, 1, np.arange(3))
+    f.sweep(1, 0.0, 1, np.arange(3, dtype=np.int32))
+    assert f.counters()["singular_rows"] == bad_o > 0
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-8
+
+
+def test_schedule_does_not_change_results():
+    """Rows are independent (Section 3.3): re-binning without changing the chunking is
+    bit-identical; other chunkings agree to rounding."""
+    p = synth.small(33, (300, 400, 20), 40_000, 3, 6, modes=["zipf", "zipf", "uniform"])
+    outs = []
+    for policy, P in [(tf.SCHED_LPT, 0), (tf.SCHED_LPT, 7), (tf.SCHED_SEQ, 50),
+                      (tf.SCHED_RAN, 50), (tf.SCHED_GREEDY, 64)]:
+        f, t, A = make(p, tf.F64)
+        f.set_schedule(policy, P)
+        if policy == tf.SCHED_LPT and P == 7:
+            assert f.counters()["split_rows"] > 0
+        for s in range(2):
+            f.sweep(3, 0.2, 1, p.column_order(s, 3))
+        outs.append([f.factors(n) for n in range(3)])
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert rel(a, b) < 1e-10
+    # same chunking, different bins -> bit-identical
+    f1, _, _ = make(p, tf.F64)
+    f2, _, _ = make(p, tf.F64)
+    f1.set_schedule(tf.SCHED_SEQ, 50)
+    f2.set_schedule(tf.SCHED_RAN, 50)
+    for f in (f1, f2):
+        f.sweep(3, 0.2, 1, p.column_order(0, 3))
+    for n in range(3):
+        assert np.array_equal(f1.factors(n), f2.factors(n))
+
+
+def test_deterministic_rerun_fp32():
+    p = synth.small(34, (300, 300, 30), 50_000, 3, 10, modes=["zipf", "uniform", "uniform"])
+    res = []
+    for _ in range(2):
+        f, _, _ = make(p, tf.F32)
+        f.sweep(10, 0.1, 1, p.column_order(0, 10))
+        res.append((f.factors(0), f.factors(2), f.loss(0.1)))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
+
+
+def test_default_order_is_permutation_and_identity_for_cdtf():
+    p = synth.small(35, (30, 30, 30), 2_000, 2, 12)
+    f, _, _ = make(p, tf.F32)
+    assert np.array_equal(f.default_order(0, 1), np.arange(12))
+    o0, o1 = f.default_order(0, 4), f.default_order(1, 4)
+    assert sorted(o0) == list(range(12)) and not np.array_equal(o0, o1)
+    f.sweep(4, 0.1, 1)   # default order path runs
+    f.sweep(1, 0.1, 1)
+
+
+def test_change_of_C_between_sweeps():
+    """A sweep with a smaller C after a larger one (the lazily kept R-hat of the larger
+    split must be flushed first)."""
+    p = ragged_problem(23)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s, C in enumerate([6, 2, 5, 1]):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.3, 1, order)
+        oracle.sals_sweep(t, A, r, C, 0.3, 1, order)
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    assert rel(f.residual(), r) < 1e-9
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_other_tensor_orders(N):
+    dims = {2: (400, 300), 4: (40, 30, 20, 25)}[N]
+    p = synth.small(36 + N, dims, 8_000, 2, 5)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, 2)
+        f.sweep(2, 0.4, 1, order)
+        oracle.sals_sweep(t, A, r, 2, 0.4, 1, order)
+    for n in range(N):
+        assert rel(f.factors(n), A[n]) < 1e-9
+
+
+def test_empty_tensor():
+    f = tf.Factorization(np.zeros((0, 3), np.int32), np.zeros(0), [5, 4, 3], 3, dtype=tf.F64)
+    f.sweep(2, 1.0, 1)
+    assert np.all(f.factors(1) == 0)   # empty rows with lambda > 0 go to zero
+    assert f.loss(1.0) == (0.0, 0.0)
+
+
+# --------------------------------------------------------------------------- fold-in
+
+
+@pytest.mark.parametrize("dtype,tol", [(tf.F64, 1e-10), (tf.F32, 1e-4)])
+def test_foldin_matches_oracle(dtype, tol):
+    p = synth.small(40, (50, 300, 200), 30_000, 5, 24)
+    f, t, A = make(p, dtype)
+    rng = np.random.default_rng(1)
+    for m in (0, 1, 7, 33, 500):
+        other = np.stack([rng.integers(0, 300, m), rng.integers(0, 200, m)], 1).astype(np.int32)
+        x = rng.standard_normal(m)
+        got = f.foldin(0, other, x, 0.5)
+        ref, st = oracle.foldin(A, 0, other, x, 0.5)
+        assert st == 0
+        assert rel(got.astype(np.float64), ref) < tol or np.linalg.norm(ref) < 1e-12
+
+
+def test_foldin_rejects_bad_index():
+    p = synth.small(41, (20, 30, 40), 2_000, 2, 4)
+    f, _, _ = make(p, tf.F32)
+    with pytest.raises(tf.TFError) as e:
+        f.foldin(0, np.array([[3, 40]], np.int32), np.ones(1), 0.1)
+    assert e.value.status == tf.ERANGE
+    f.foldin(0, np.array([[3, 39]], np.int32), np.ones(1), 0.1)   # context still usable
+
+
+# --------------------------------------------------------------------------- full size
+
+
+def test_skewed_full_size_sampled_rows():
+    """The 1e5 x 1e5 x 1e3, 1e8-entry Zipf workload at full size, in the schedule the
+    benchmark uses: offsets against a library bincount, sampled first-split mode-1
+    rows against the oracle's row update from the same inputs, and the residual
+    invariant on sampled entries."""
+    dev = "cuda"
+    p = synth.skewed_3way(device=dev)
+    K, C, lam = p.K, 10, 0.1
+    A0 = [a for a in p.init_factors(torch.float32, dev)]
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=p.seed, dtype=tf.F32,
+                         device_input=True)
+    for n in range(3):
+        f.set_factors(n, A0[n].cpu().numpy())
+    for n in range(3):
+        off, _ = f.grouping(n, with_perm=False)
+        cnt = torch.bincount(p.coords[:, n].long(), minlength=p.dims[n]).cpu().numpy()
+        assert np.array_equal(np.diff(off), cnt)
+    order = p.column_order(0, C)
+    f.sweep(C, lam, 1, order)
+    S = order[:C].astype(np.int32)
+    A1 = f.factors(0)
+    # sampled rows: heaviest, a light one, and random ones
+    cnt0 = torch.bincount(p.coords[:, 0].long(), minlength=p.dims[0]).cpu().numpy()
+    rows = [int(np.argmax(cnt0)), int(np.argmin(np.where(cnt0 > 0, cnt0, 1 << 40)))]
+    rows += list(np.random.default_rng(0).choice(np.nonzero(cnt0)[0], 6, replace=False))
+    Ah = [a.double().cpu().numpy() for a in A0]
+    for i in rows:
+        sel = (p.coords[:, 0] == i).nonzero().squeeze(1)
+        c = p.coords[sel].cpu().numpy()
+        x = p.x[sel].double().cpu().numpy()
+        sub = oracle.Tensor(c, x, p.dims)
+        A = [a.copy() for a in Ah]
+        assert oracle.row_update(sub, 0, i, x, A, S, lam) == 0   # R-hat = X (A^(1) = 0)
+        got = A1[i, S].astype(np.float64)
+        assert np.linalg.norm(got - A[0][i, S]) <= 1e-5 * max(np.linalg.norm(A[0][i, S]), 1e-30)
+    # residual invariant on sampled entries, from the device's own factors
+    r = f.residual()
+    idx = np.random.default_rng(1).choice(p.nnz, 20_000, replace=False)
+    c = p.coords[torch.from_numpy(idx).to(dev)].long().cpu().numpy()
+    Af = [f.factors(n).astype(np.float64) for n in range(3)]
+    model = (Af[0][c[:, 0]] * Af[1][c[:, 1]] * Af[2][c[:, 2]]).sum(1)
+    x = p.x[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+    assert np.max(np.abs(r[idx] - (x - model))) <= 1e-4 * np.max(np.abs(x))
