@@ -252,7 +252,8 @@ def main():
                 "avg_launch_ms": mp_avg_ms}
     nsplit = math.ceil(K / C)
     sweep_bytes = nnz * (T_in * N * (4 * (N - 1) + 4) + 4) * nsplit
-    sweep_ms = sum(v[1] for k, v in prof.items() if k in ("pack", "mode_pass", "combine")) / args.steps
+    sweep_ms = sum(v[1] for k, v in prof.items()
+                   if k in ("pack", "mode_pass", "combine", "solve")) / args.steps
     kernel_breakdown = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
     launches_per_step = cnt["last_sweep_launches"] + cnt["loss_launches"]
 

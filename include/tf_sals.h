@@ -62,9 +62,10 @@ typedef enum {
 } tf_sched_policy;
 
 /* One unit of device work: entries [begin, begin + len) of a mode's sorted order, all
- * in row `row`.  slot < 0: the item holds the whole row and solves it; slot >= 0: the
- * item is one chunk of a row split across bins and writes its partial Gram/rhs to
- * partial slot `slot` (chunks of a row take consecutive slots in entry order). */
+ * in row `row`.  The item writes its Gram matrix and right-hand side (Eq. 4) over those
+ * entries to partial slot `slot`; a row is either one item or, when longer than the
+ * cap, several chunks whose slots are consecutive in entry order.  The row's system is
+ * the sum of its slots, in slot order. */
 typedef struct {
     int64_t begin;
     int32_t len;
@@ -119,19 +120,19 @@ tf_status tf_get_factors(tf_ctx *ctx, int n, void *host_A);
  * The last split holds K mod C columns when C does not divide K.
  * Column order: a seeded permutation per sweep for C > 1 (chosen without replacement,
  * Algorithm 1), the identity for C = 1 (CDTF keeps a fixed order, Section 3.1).
- *   C in 1..K (C <= 16 on the SIMT path, larger C on the tiled path), lambda >= 0,
- *   T_in >= 1.  Asynchronous: returns once the work is queued on the stream.
+ *   C in 1..K (C <= 16 on the SIMT path, larger C on the tiled path), lambda >= 0
+ *   (double; converted to the context dtype), T_in >= 1.  Asynchronous: returns once the work is queued on the stream.
  * A row whose B + lambda I has a non-positive Cholesky pivot (e.g. an empty row with
  * lambda = 0) is left unchanged and counted (tf_get_counters). */
-tf_status tf_sals_sweep(tf_ctx *ctx, int C, float lambda, int T_in);
+tf_status tf_sals_sweep(tf_ctx *ctx, int C, double lambda, int T_in);
 
 /* As tf_sals_sweep with an explicit column order col_order[K] (a permutation of
  * 0..K-1, host); split s takes col_order[s*C .. min((s+1)*C, K)).  NULL = default. */
-tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, float lambda, int T_in,
+tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, double lambda, int T_in,
                               const int32_t *col_order);
 
 /* As tf_sals_sweep_order with flags (TF_WEIGHTED_LAMBDA). */
-tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, float lambda, int T_in,
+tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, double lambda, int T_in,
                            const int32_t *col_order, uint32_t flags);
 
 /* Writes the default column order of sweep number `sweep` (0-based) for this C. */
@@ -143,7 +144,7 @@ tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_ord
  * each row's squared norm is weighted by |Omega_i^(n)|), train_rmse =
  * sqrt(sum r^2 / |Omega|).  Accumulated in double on the device, in a fixed order
  * (bit-reproducible).  Synchronises.  Either output pointer may be NULL. */
-tf_status tf_loss(tf_ctx *ctx, float lambda, uint32_t flags, double *loss,
+tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
                   double *train_rmse);
 
 /* ------------------------------------------------------------------ fold-in */
@@ -156,7 +157,7 @@ tf_status tf_loss(tf_ctx *ctx, float lambda, uint32_t flags, double *loss,
  * Synchronises.  TF_ERANGE if an index is out of range.  A non-positive pivot gives
  * TF_EINVAL with out_row untouched. */
 tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values,
-                    int64_t m, float lambda, void *out_row);
+                    int64_t m, double lambda, void *out_row);
 
 /* ------------------------------------------------------------------ inspection */
 
@@ -182,11 +183,12 @@ tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 /* Kernel kinds reported by tf_get_profile. */
 typedef enum {
     TF_KIND_PACK = 0,      /* slice packing of a split (Theorem 3's C resident columns) */
-    TF_KIND_MODE_PASS = 1, /* fused Gram/rhs/solve/R-hat pass over one mode (Eq. 4)      */
-    TF_KIND_COMBINE = 2,   /* sum of split rows' partial Gram/rhs + solve               */
+    TF_KIND_MODE_PASS = 1, /* fused R-hat / Gram / rhs pass over one mode (Eq. 4)        */
+    TF_KIND_COMBINE = 2,   /* sum of split rows' partial Gram/rhs + Cholesky solve      */
     TF_KIND_LOSS = 3,      /* loss / residual reductions (Eq. 1)                        */
     TF_KIND_OTHER = 4,     /* residual rebuilds and flushes                             */
-    TF_KIND_COUNT = 5
+    TF_KIND_SOLVE = 5,     /* Cholesky solves of the rows held by one item (Sec. 3.1)   */
+    TF_KIND_COUNT = 6
 } tf_kernel_kind;
 
 /* enable != 0: from now on bracket every kernel launch of this context with CUDA
@@ -197,6 +199,12 @@ tf_status tf_profile(tf_ctx *ctx, int enable);
 /* Launch counts and summed device milliseconds per kind since profiling was enabled
  * (arrays of TF_KIND_COUNT).  Synchronises. */
 tf_status tf_get_profile(tf_ctx *ctx, int64_t *launches, double *ms);
+
+/* Per-launch trace since profiling was enabled: up to cap records of (kind, mode,
+ * milliseconds) in launch order; *n receives the number available.  mode is the
+ * tensor mode the launch worked on (-1 when it spans all modes).  Synchronises. */
+tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kinds,
+                              int32_t *modes, float *ms);
 
 /* ------------------------------------------------------------------ host-only */
 
@@ -214,7 +222,7 @@ tf_status tf_assign_rows(tf_sched_policy policy, int N, const int64_t *dims,
  * placed longest first on the least-loaded bin (TF_SCHED_LPT) or by another policy.
  * off[I + 1] are the row offsets (host).  items (capacity max_items) come out grouped
  * by bin, bins in increasing order; bin_ptr[P + 1] indexes them.  *n_items and
- * *n_slots receive the counts.  TF_ENOMEM if max_items is too small.  No GPU. */
+ * *n_slots receive the counts (every item has its own slot, so they are equal).  TF_ENOMEM if max_items is too small.  No GPU. */
 tf_status tf_plan_mode(const int64_t *off, int64_t I, int P, int64_t cap,
                        tf_sched_policy policy, uint64_t seed, tf_item *items,
                        int64_t max_items, int64_t *n_items, int64_t *n_slots,

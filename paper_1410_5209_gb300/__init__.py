@@ -57,7 +57,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     P, i32, i64, u32, u64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
                              ctypes.c_uint64)
-    f32 = ctypes.c_float
+    f64 = ctypes.c_double
     sig = {
         "tf_create": [P, P, i32, P, i32, i64, i32, u64, P, u32, P],
         "tf_destroy": [P],
@@ -65,18 +65,19 @@ def load():
         "tf_sync": [P],
         "tf_set_factors": [P, i32, P],
         "tf_get_factors": [P, i32, P],
-        "tf_sals_sweep": [P, i32, f32, i32],
-        "tf_sals_sweep_order": [P, i32, f32, i32, P],
-        "tf_sals_sweep_ex": [P, i32, f32, i32, P, u32],
+        "tf_sals_sweep": [P, i32, f64, i32],
+        "tf_sals_sweep_order": [P, i32, f64, i32, P],
+        "tf_sals_sweep_ex": [P, i32, f64, i32, P, u32],
         "tf_default_order": [P, i32, i32, P],
-        "tf_loss": [P, f32, u32, P, P],
-        "tf_foldin": [P, i32, P, P, i64, f32, P],
+        "tf_loss": [P, f64, u32, P, P],
+        "tf_foldin": [P, i32, P, P, i64, f64, P],
         "tf_get_grouping": [P, i32, P, P],
         "tf_get_residual": [P, P],
         "tf_get_counters": [P, P],
         "tf_set_schedule": [P, i32, i32],
         "tf_profile": [P, i32],
         "tf_get_profile": [P, P, P],
+        "tf_get_launch_trace": [P, i64, P, P, P, P],
         "tf_assign_rows": [i32, i32, P, P, i32, u64, P],
         "tf_plan_mode": [P, i64, i32, i64, i32, u64, P, i64, P, P, P],
         "tf_version": [],
@@ -234,16 +235,29 @@ class Factorization:
     def set_schedule(self, policy=SCHED_LPT, P=0):
         self._check(self._lib.tf_set_schedule(self._ctx, int(policy), int(P)))
 
-    KINDS = ["pack", "mode_pass", "combine", "loss", "other"]
+    KINDS = ["pack", "mode_pass", "combine", "loss", "other", "solve"]
 
     def profile(self, enable=True):
         self._check(self._lib.tf_profile(self._ctx, 1 if enable else 0))
 
     def get_profile(self):
-        n = np.zeros(5, np.int64)
-        ms = np.zeros(5, np.float64)
+        n = np.zeros(len(self.KINDS), np.int64)
+        ms = np.zeros(len(self.KINDS), np.float64)
         self._check(self._lib.tf_get_profile(self._ctx, _ptr(n), _ptr(ms)))
         return {k: (int(a), float(b)) for k, a, b in zip(self.KINDS, n, ms)}
+
+    def launch_trace(self):
+        """[(kind, mode, ms)] of every timed launch since profile(True)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.tf_get_launch_trace(self._ctx, 0, ctypes.byref(n), None, None,
+                                                  None))
+        k = np.zeros(max(n.value, 1), np.int32)
+        m = np.zeros(max(n.value, 1), np.int32)
+        ms = np.zeros(max(n.value, 1), np.float32)
+        self._check(self._lib.tf_get_launch_trace(self._ctx, n.value, ctypes.byref(n), _ptr(k),
+                                                  _ptr(m), _ptr(ms)))
+        return [(self.KINDS[a], int(b), float(c)) for a, b, c in zip(k[:n.value], m[:n.value],
+                                                                    ms[:n.value])]
 
     def sync(self):
         self._check(self._lib.tf_sync(self._ctx))

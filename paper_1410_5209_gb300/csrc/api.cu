@@ -52,9 +52,10 @@ struct ModeLayout {
     Buf<int32_t> oidx;      // [(N-1) * nnz] other-mode indices, mode order
     Buf<tf_item> items;
     Buf<int64_t> bin_ptr;   // [P + 1]
-    Buf<SplitRow> split;
+    Buf<SplitRow> split;    // rows held by several items (chunks)
+    Buf<SplitRow> single;   // rows held by one item
     int64_t n_items = 0, n_slots = 0;
-    int n_split = 0;
+    int n_split = 0, n_single = 0;
     int P = 0;
     int omode[kMaxModes - 1];
 };
@@ -97,11 +98,14 @@ struct Impl : CtxBase {
     // kernel timing (tf_profile): event pairs per launch, folded in at tf_get_profile
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
-    std::vector<int> prof_kind;
+    std::vector<int> prof_kind, prof_mode;
+    std::vector<int32_t> trace_kind, trace_mode;
+    std::vector<float> trace_ms;
     int64_t prof_launches[TF_KIND_COUNT] = {0};
     double prof_ms[TF_KIND_COUNT] = {0};
 
-    int Cq = 0, W_last = 0;        // columns Q held by the copies' R-hat, slice stride
+    int Cq = 0, CM_last = 1;       // columns Q held by the copies' R-hat; register width
+                                   // (and so slice layout) of the sweep that left them
     bool dirty = false;            // residual copies must be rebuilt from the factors
     bool a0_zero = true;           // A^(1) known to be zero (R = X)
     int64_t sweeps = 0, last_launches = 0, loss_launches = 0;
@@ -117,6 +121,8 @@ struct Impl : CtxBase {
     }
 
     // Brackets one launch with events when profiling is on.
+    int cur_mode = -1;  // mode recorded with the next timed launches
+
     template <class F>
     void timed(int kind, F &&launch) {
         if (!prof_on) {
@@ -131,6 +137,7 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaEventRecord(b, st));
         prof_pending.push_back({a, b});
         prof_kind.push_back(kind);
+        prof_mode.push_back(cur_mode);
     }
 
     void profile(int enable) {
@@ -141,6 +148,10 @@ struct Impl : CtxBase {
         }
         prof_pending.clear();
         prof_kind.clear();
+        prof_mode.clear();
+        trace_kind.clear();
+        trace_mode.clear();
+        trace_ms.clear();
         for (int k = 0; k < TF_KIND_COUNT; ++k) {
             prof_launches[k] = 0;
             prof_ms[k] = 0.0;
@@ -155,11 +166,15 @@ struct Impl : CtxBase {
             TFS_CUDA(cudaEventElapsedTime(&ms, prof_pending[i].first, prof_pending[i].second));
             prof_launches[prof_kind[i]] += 1;
             prof_ms[prof_kind[i]] += ms;
+            trace_kind.push_back(prof_kind[i]);
+            trace_mode.push_back(prof_mode[i]);
+            trace_ms.push_back(ms);
             cudaEventDestroy(prof_pending[i].first);
             cudaEventDestroy(prof_pending[i].second);
         }
         prof_pending.clear();
         prof_kind.clear();
+        prof_mode.clear();
         for (int k = 0; k < TF_KIND_COUNT; ++k) {
             if (launches_out) launches_out[k] = prof_launches[k];
             if (ms_out) ms_out[k] = prof_ms[k];
@@ -287,28 +302,33 @@ struct Impl : CtxBase {
         int64_t n_slots = 0;
         tf_status s = plan_mode(off.data(), L.I, P, 0, policy, seed, items, n_slots, bin_ptr);
         if (s != TF_OK) throw ApiError{s, "row scheduling failed"};
-        // split rows: consecutive slots of one row, in entry order
-        std::vector<tf_item> chunks;
-        for (const auto &it : items)
-            if (it.slot >= 0) chunks.push_back(it);
-        std::sort(chunks.begin(), chunks.end(),
+        // rows and their slots (a row's slots are consecutive, in entry order):
+        // single-item rows are solved by k_solve_rows, split rows by k_combine
+        std::vector<tf_item> by_slot(items);
+        std::sort(by_slot.begin(), by_slot.end(),
                   [](const tf_item &a, const tf_item &b) { return a.slot < b.slot; });
-        std::vector<SplitRow> split;
-        for (size_t i = 0; i < chunks.size();) {
+        std::vector<SplitRow> split, single;
+        for (size_t i = 0; i < by_slot.size();) {
             size_t j = i;
-            while (j < chunks.size() && chunks[j].row == chunks[i].row) ++j;
-            const int64_t r = chunks[i].row;
-            split.push_back({chunks[i].row, chunks[i].slot, (int32_t)(j - i), 0,
-                             off[r + 1] - off[r]});
+            while (j < by_slot.size() && by_slot[j].row == by_slot[i].row) ++j;
+            const int64_t r = by_slot[i].row;
+            const SplitRow sr{by_slot[i].row, by_slot[i].slot, (int32_t)(j - i), 0,
+                              off[r + 1] - off[r]};
+            (j - i > 1 ? split : single).push_back(sr);
             i = j;
         }
         L.P = P;
         L.n_items = (int64_t)items.size();
         L.n_slots = n_slots;
         L.n_split = (int)split.size();
+        L.n_single = (int)single.size();
         L.items.alloc(items.size());
         L.bin_ptr.alloc(bin_ptr.size());
         L.split.alloc(split.size());
+        L.single.alloc(single.size());
+        if (!single.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.single.p, single.data(), single.size() * sizeof(SplitRow),
+                                     cudaMemcpyHostToDevice, st));
         if (!items.empty())
             TFS_CUDA(cudaMemcpyAsync(L.items.p, items.data(), items.size() * sizeof(tf_item),
                                      cudaMemcpyHostToDevice, st));
@@ -354,12 +374,12 @@ struct Impl : CtxBase {
     }
 
     template <class Args>
-    void fill_other(Args &a, int n, const ModeLayout &L, int W) {
+    void fill_other(Args &a, int n, const ModeLayout &L) {
+        (void)n;
         for (int t = 0; t < N - 1; ++t) {
             a.oidx[t] = L.oidx.p + (size_t)t * nnz;
             a.Zo[t] = Z[L.omode[t]].p;
         }
-        (void)W;
     }
 
     // copies: R-hat of columns Q  ->  true residual (subtract Q's part)
@@ -373,22 +393,31 @@ struct Impl : CtxBase {
             a.P = L.P;
             a.N = N;
             a.n = n;
-            a.W = W_last;
             a.Cq = Cq;
             a.what = 2;
-            fill_other(a, n, L, W_last);
+            fill_other(a, n, L);
             a.Zn = Z[n].p;
             a.res = res[n].p;
-            timed(TF_KIND_OTHER, [&] { launch_res<T>(a, pass_blocks(L.P), st); });
+            timed(TF_KIND_OTHER, [&] { launch_res<T>(a, CM_last, st); });
         }
         Cq = 0;
     }
 
+    void launch_trace(int64_t cap, int64_t *n, int32_t *kinds, int32_t *modes, float *ms) {
+        get_profile(nullptr, nullptr);
+        *n = (int64_t)trace_ms.size();
+        for (int64_t i = 0; i < std::min<int64_t>(cap, *n); ++i) {
+            if (kinds) kinds[i] = trace_kind[i];
+            if (modes) modes[i] = trace_mode[i];
+            if (ms) ms[i] = trace_ms[i];
+        }
+    }
+
     // ------------------------------------------------------------ the sweep
-    void sweep(int C, float lambda, int T_in, const int32_t *order, uint32_t flags) {
+    void sweep(int C, double lambda, int T_in, const int32_t *order, uint32_t flags) {
         if (C < 1 || C > K) throw ApiError{TF_EINVAL, "C must be in 1..K"};
         if (T_in < 1) throw ApiError{TF_EINVAL, "T_in must be >= 1"};
-        if (!(lambda >= 0.0f) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
+        if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
         const int CM = pick_cm(C);
         if (CM == 0) throw ApiError{TF_EINVAL, "C > 16 is not supported by this build"};
         int64_t launches0 = launches;
@@ -421,16 +450,20 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaEventRecord(order_ev, st));
         order_pending = true;
 
-        const int W = ((2 * C + std::max(C, Cq)) + 3) / 4 * 4;
-        const int off_old = C, off_prev = 2 * C;
+        const int W = slice_stride_elems(CM, (int)sizeof(T));
+        const int off_prev = CM, off_old = 2 * CM;
         int64_t max_slots = 0;
         for (int n = 0; n < N; ++n) {
-            Z[n].ensure((size_t)dims[n] * W);
+            if (Z[n].n < (size_t)dims[n] * W) {
+                Z[n].alloc((size_t)dims[n] * W);
+                TFS_CUDA(cudaMemsetAsync(Z[n].p, 0, Z[n].n * sizeof(T), st));
+            }
             max_slots = std::max(max_slots, mode[n].n_slots);
         }
         partials.ensure((size_t)std::max<int64_t>(max_slots, 1) * partial_stride(CM));
 
-        const int grid = mode_pass_grid<T>(CM, P, num_sms);
+        const int grid = mode_pass_grid<T>(CM, P, num_sms, N);
+        const int warps_per_block = mode_pass_warps<T>(CM, N);
         const int nsplit = (K + C - 1) / C;
         int cq = Cq;
         const int32_t *Qp = d_Q.p;
@@ -458,6 +491,7 @@ struct Impl : CtxBase {
             for (int t = 0; t < T_in; ++t) {
                 for (int n = 0; n < N; ++n) {
                     const ModeLayout &L = mode[n];
+                    cur_mode = n;
                     PassArgs<T> a{};
                     a.items = L.items.p;
                     a.bin_ptr = L.bin_ptr.p;
@@ -466,9 +500,6 @@ struct Impl : CtxBase {
                     a.n = n;
                     a.C = Cs;
                     a.Cq = cq;
-                    a.W = W;
-                    a.off_old = off_old;
-                    a.off_prev = off_prev;
                     a.first = (t == 0);
                     a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
                     a.lambda = (T)lambda;
@@ -486,9 +517,14 @@ struct Impl : CtxBase {
                     a.ticket = ticket.p;
                     a.ticket_base = ticket_base;
                     // every launched warp takes one ticket past the last bin
-                    ticket_base += (unsigned long long)L.P + (unsigned long long)grid * (kPassThreads / kWarp);
+                    ticket_base += (unsigned long long)L.P + (unsigned long long)grid * warps_per_block;
                     timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, grid, st); });
                     ++launches;
+                    if (L.n_single > 0) {
+                        timed(TF_KIND_SOLVE,
+                              [&] { launch_solve_rows<T>(a, CM, L.single.p, L.n_single, st); });
+                        ++launches;
+                    }
                     if (L.n_split > 0) {
                         timed(TF_KIND_COMBINE,
                               [&] { launch_combine<T>(a, CM, L.split.p, L.n_split, st); });
@@ -498,11 +534,12 @@ struct Impl : CtxBase {
             }
             cq = Cs;
             Qp = Sp;
+            cur_mode = -1;
         }
         // the copies now hold R-hat of the last split's columns
         TFS_CUDA(cudaMemcpyAsync(d_Q.p, Qp, sizeof(int32_t) * cq, cudaMemcpyDeviceToDevice, st));
         Cq = cq;
-        W_last = W;
+        CM_last = CM;
         ++sweeps;
         last_launches = launches - launches0;
     }
@@ -520,10 +557,10 @@ struct Impl : CtxBase {
     }
 
     // ------------------------------------------------------------ loss
-    void loss(float lambda, uint32_t flags, double *loss_out, double *rmse_out) {
+    void loss(double lambda, uint32_t flags, double *loss_out, double *rmse_out) {
         if (dirty) rebuild_residuals();
         const ModeLayout &L = mode[0];
-        const int blocks = pass_blocks(L.P);
+        const int blocks = res_grid<T>(CM_last, L.P, N);
         const int reg_blocks = 256;
         red.ensure((size_t)blocks + (size_t)N * reg_blocks + 4);
         ResArgs<T> a{};
@@ -532,7 +569,6 @@ struct Impl : CtxBase {
         a.P = L.P;
         a.N = N;
         a.n = 0;
-        a.W = W_last;
         a.Cq = Cq;
         a.what = 0;
         for (int t = 0; t < N - 1; ++t) {
@@ -544,7 +580,7 @@ struct Impl : CtxBase {
         a.block_out = red.p + 2;
         double *regp = red.p + 2 + blocks;
         timed(TF_KIND_LOSS, [&] {
-            launch_res<T>(a, blocks, st);
+            launch_res<T>(a, CM_last, st);
             launch_sum_blocks(red.p + 2, blocks, red.p + 0, st);
             for (int n = 0; n < N; ++n)
                 launch_reg<T>(A[n].p, dims[n], K,
@@ -557,7 +593,7 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaMemcpyAsync(h, red.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         TFS_CUDA(cudaStreamSynchronize(st));
         check_errors();
-        if (loss_out) *loss_out = h[0] + (double)lambda * h[1];
+        if (loss_out) *loss_out = h[0] + lambda * h[1];
         if (rmse_out) *rmse_out = nnz > 0 ? sqrt(h[0] / (double)nnz) : 0.0;
     }
 
@@ -572,7 +608,6 @@ struct Impl : CtxBase {
         a.P = L.P;
         a.N = N;
         a.n = 0;
-        a.W = W_last;
         a.Cq = Cq;
         a.what = 1;
         for (int t = 0; t < N - 1; ++t) {
@@ -583,7 +618,7 @@ struct Impl : CtxBase {
         a.res = res[0].p;
         a.perm = L.perm.p;
         a.out = out.p;
-        launch_res<T>(a, pass_blocks(L.P), st);
+        launch_res<T>(a, CM_last, st);
         if (nnz > 0)
             TFS_CUDA(cudaMemcpyAsync(host_r, out.p, nnz * sizeof(T), cudaMemcpyDeviceToHost, st));
         TFS_CUDA(cudaStreamSynchronize(st));
@@ -619,10 +654,10 @@ struct Impl : CtxBase {
     }
 
     // ------------------------------------------------------------ fold-in
-    void foldin(int md, const int32_t *other, const T *vals, int64_t m, float lambda, T *out) {
+    void foldin(int md, const int32_t *other, const T *vals, int64_t m, double lambda, T *out) {
         if (md < 0 || md >= N) throw ApiError{TF_EINVAL, "mode out of range"};
         if (m < 0) throw ApiError{TF_EINVAL, "m must be >= 0"};
-        if (!(lambda >= 0.0f)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
+        if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
         int dev = 0, maxsm = 0;
         TFS_CUDA(cudaGetDevice(&dev));
         TFS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -831,17 +866,17 @@ tf_status tf_get_factors(tf_ctx *ctx, int n, void *host_A) {
     });
 }
 
-tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, float lambda, int T_in, const int32_t *col_order,
+tf_status tf_sals_sweep_ex(tf_ctx *ctx, int C, double lambda, int T_in, const int32_t *col_order,
                            uint32_t flags) {
     return dispatch(ctx, [&](auto &c) { c.sweep(C, lambda, T_in, col_order, flags); });
 }
 
-tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, float lambda, int T_in,
+tf_status tf_sals_sweep_order(tf_ctx *ctx, int C, double lambda, int T_in,
                               const int32_t *col_order) {
     return tf_sals_sweep_ex(ctx, C, lambda, T_in, col_order, 0u);
 }
 
-tf_status tf_sals_sweep(tf_ctx *ctx, int C, float lambda, int T_in) {
+tf_status tf_sals_sweep(tf_ctx *ctx, int C, double lambda, int T_in) {
     return tf_sals_sweep_ex(ctx, C, lambda, T_in, nullptr, 0u);
 }
 
@@ -854,12 +889,12 @@ tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_ord
     return TF_OK;
 }
 
-tf_status tf_loss(tf_ctx *ctx, float lambda, uint32_t flags, double *loss, double *train_rmse) {
+tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss, double *train_rmse) {
     return dispatch(ctx, [&](auto &c) { c.loss(lambda, flags, loss, train_rmse); });
 }
 
 tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values, int64_t m,
-                    float lambda, void *out_row) {
+                    double lambda, void *out_row) {
     if (!out_row || (m > 0 && (!other || !values))) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         using T = typename std::remove_reference<decltype(*c.x.p)>::type;
@@ -891,6 +926,12 @@ tf_status tf_profile(tf_ctx *ctx, int enable) {
 
 tf_status tf_get_profile(tf_ctx *ctx, int64_t *launches, double *ms) {
     return dispatch(ctx, [&](auto &c) { c.get_profile(launches, ms); });
+}
+
+tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kinds,
+                              int32_t *modes, float *ms) {
+    if (!n || cap < 0) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { c.launch_trace(cap, n, kinds, modes, ms); });
 }
 
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P) {

@@ -10,14 +10,35 @@ void launch_mode_pass<double>(const PassArgs<double> &a, int CM, int grid, cudaS
 }
 
 template <>
-int mode_pass_grid<double>(int CM, int P, int num_sms) {
-    return mode_pass_grid_impl<double>(CM, P, num_sms);
+int mode_pass_grid<double>(int CM, int P, int num_sms, int N) {
+    return mode_pass_grid_impl<double>(CM, P, num_sms, N);
+}
+
+template <>
+int mode_pass_warps<double>(int CM, int N) {
+    return mode_pass_warps_impl<double>(CM, N);
+}
+
+template <>
+int res_grid<double>(int CM, int P, int N) {
+    return res_blocks_impl<double>(CM, P, N);
 }
 
 template <>
 void launch_combine<double>(const PassArgs<double> &a, int CM, const SplitRow *rows, int n_rows,
                           cudaStream_t st) {
     launch_combine_impl<double>(a, CM, rows, n_rows, st);
+}
+
+template <>
+void launch_res<double>(const ResArgs<double> &a, int CM, cudaStream_t st) {
+    launch_res_impl<double>(a, CM, st);
+}
+
+template <>
+void launch_solve_rows<double>(const PassArgs<double> &a, int CM, const SplitRow *rows, int n_rows,
+                            cudaStream_t st) {
+    launch_solve_rows_impl<double>(a, CM, rows, n_rows, st);
 }
 
 }  // namespace tfs

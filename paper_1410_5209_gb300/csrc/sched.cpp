@@ -119,7 +119,7 @@ tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_
         const int64_t len = off[i + 1] - off[i];
         if (policy != TF_SCHED_LPT || len <= cap) {
             if (len > INT32_MAX) return TF_EINVAL;
-            jobs.push_back({off[i], (int32_t)len, (int32_t)i, -1, -1});
+            jobs.push_back({off[i], (int32_t)len, (int32_t)i, (int32_t)n_slots++, -1});
             continue;
         }
         const int64_t k = (len + cap - 1) / cap;

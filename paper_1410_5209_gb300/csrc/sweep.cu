@@ -37,46 +37,6 @@ __global__ void k_pack(const PackArgs<T> a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kResThreads) k_res(const ResArgs<T> a) {
-    __shared__ double wsum[kResThreads / kWarp];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bin = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    double acc = 0.0;
-    if (bin < a.P) {
-        for (int64_t it = a.bin_ptr[bin]; it < a.bin_ptr[bin + 1]; ++it) {
-            const tf_item item = a.items[it];
-            const T *zown = a.Zn + (int64_t)item.row * a.W;
-            const int64_t jend = item.begin + item.len;
-            for (int64_t j = item.begin + lane; j < jend; j += kWarp) {
-                T p = T(0);
-                for (int c = 0; c < a.Cq; ++c) {
-                    T q = zown[c];
-                    for (int t = 0; t < a.N - 1; ++t)
-                        q *= a.Zo[t][(int64_t)a.oidx[t][j] * a.W + c];
-                    p += q;
-                }
-                const T r = a.res[j] - p;
-                if (a.what == 0)
-                    acc += (double)r * (double)r;
-                else if (a.what == 1)
-                    a.out[a.perm[j]] = r;
-                else
-                    a.res[j] = r;
-            }
-        }
-    }
-    if (a.what != 0) return;
-    acc = warp_sum_d(acc);
-    if (lane == 0) wsum[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kResThreads / kWarp; ++w) s += wsum[w];
-        a.block_out[blockIdx.x] = s;
-    }
-}
-
-template <class T>
 __global__ void __launch_bounds__(kResThreads) k_init_res(const InitArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int bin = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -168,14 +128,8 @@ void launch_pack(const PackArgs<T> &a, cudaStream_t st) {
 }
 
 template <class T>
-void launch_res(const ResArgs<T> &a, int grid_blocks, cudaStream_t st) {
-    k_res<T><<<grid_blocks, kResThreads, 0, st>>>(a);
-    TFS_CUDA(cudaGetLastError());
-}
-
-template <class T>
 void launch_init_res(const InitArgs<T> &a, cudaStream_t st) {
-    k_init_res<T><<<pass_blocks(a.P), kResThreads, 0, st>>>(a);
+    k_init_res<T><<<(unsigned)((a.P * kWarp + kResThreads - 1) / kResThreads), kResThreads, 0, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }
 
@@ -202,7 +156,6 @@ void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, 
 
 #define TFS_INST(T)                                                                        \
     template void launch_pack<T>(const PackArgs<T> &, cudaStream_t);                       \
-    template void launch_res<T>(const ResArgs<T> &, int, cudaStream_t);                    \
     template void launch_init_res<T>(const InitArgs<T> &, cudaStream_t);                   \
     template void launch_reg<T>(const T *, int64_t, int, const int64_t *, double *, int,   \
                                 cudaStream_t);                                             \

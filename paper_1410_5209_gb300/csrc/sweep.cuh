@@ -5,8 +5,8 @@
 
 namespace tfs {
 
-// A row split across bins: its chunks wrote partial Gram/rhs to slots
-// [first_slot, first_slot + n_slots), in entry order.
+// A row and its partial slots [first_slot, first_slot + n_slots) (one slot for a row
+// held by a single item; consecutive slots in entry order for a row split across bins).
 struct SplitRow {
     int32_t row;
     int32_t first_slot;
@@ -15,10 +15,11 @@ struct SplitRow {
     int64_t len;  // |Omega_i^(n)| (for weighted lambda)
 };
 
-// Packed slice layout, one row of W elements per factor row i of mode l:
-//   [0, C)                 "cur":  a^(l)_{i,S} as updated in this split
-//   [off_old, off_old + C) "old":  a^(l)_{i,S} at the start of the split
-//   [off_prev, +Cq)        "prev": a^(l)_{i,Q}, the previous split's columns (final)
+// Packed slice layout, one row of W = slice_stride_elems(CM) elements per factor row i
+// of mode l, where CM >= C is the register width the sweep was compiled for:
+//   [0, C)            "cur":  a^(l)_{i,S} as updated in this split
+//   [CM, CM + Cq)     "prev": a^(l)_{i,Q}, the previous split's columns (final values)
+//   [2CM, 2CM + C)    "old":  a^(l)_{i,S} at the start of the split
 // Residual copy n holds, for its entries in mode-n order, R-hat of the split during
 // which it was last refreshed (columns Q); its first pass of a new split turns it into
 // this split's R-hat: r_hat_S = r_hat_Q - sum_{c in Q} prod_l prev + sum_{c in S} prod_l old
@@ -30,7 +31,6 @@ struct PassArgs {
     int P;
     int N, n;       // number of modes, mode being updated
     int C, Cq;      // |S| of this split, |Q| of the previous one (Cq <= CM)
-    int W, off_old, off_prev;
     int first;      // first inner iteration of the split: refresh R-hat
     int weighted;   // weighted lambda
     T lambda;
@@ -65,7 +65,7 @@ struct ResArgs {
     const tf_item *items;
     const int64_t *bin_ptr;
     int P;
-    int N, n, W, Cq, what;
+    int N, n, Cq, what;
     const int32_t *oidx[kMaxModes - 1];
     const T *Zo[kMaxModes - 1];
     const T *Zn;
@@ -103,11 +103,24 @@ struct FoldArgs {
     DeviceStatus *stat;
 };
 
-constexpr int kPassThreads = 256;
+constexpr int kPassThreads = 128;
 constexpr int kCombineThreads = 512;
 constexpr int kMaxCSimt = 16;
 
 int pick_cm(int C);  // smallest instantiated register width >= C (0 if none)
+
+__host__ __device__ constexpr int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
+
+// Row stride (elements) of a packed slice for register width CM: three regions of CM
+// elements, padded to a power-of-two number of 16-byte vectors (so that a fixed group
+// of lanes can move one row with one vector each).
+__host__ __device__ constexpr int slice_stride_elems(int CM, int elem_bytes) {
+    return (16 / elem_bytes) * next_pow2((3 * CM + 16 / elem_bytes - 1) / (16 / elem_bytes));
+}
 inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
 
 template <class T>
@@ -116,9 +129,18 @@ template <class T>
 void launch_combine(const PassArgs<T> &a, int CM, const SplitRow *rows, int n_rows,
                     cudaStream_t st);
 template <class T>
+void launch_solve_rows(const PassArgs<T> &a, int CM, const SplitRow *rows, int n_rows,
+                       cudaStream_t st);
+template <class T>
 void launch_pack(const PackArgs<T> &a, cudaStream_t st);
 template <class T>
-void launch_res(const ResArgs<T> &a, int grid_blocks, cudaStream_t st);
+void launch_res(const ResArgs<T> &a, int CM, cudaStream_t st);
+// Blocks of a residual / loss launch (one warp per bin, every bin launched).
+template <class T>
+int res_grid(int CM, int P, int N);
+inline int res_blocks(int P, int warps_per_block) {
+    return (P + warps_per_block - 1) / warps_per_block;
+}
 template <class T>
 void launch_init_res(const InitArgs<T> &a, cudaStream_t st);
 template <class T>
@@ -137,6 +159,9 @@ inline int pass_blocks(int P) { return (P * kWarp + kPassThreads - 1) / kPassThr
 
 // Blocks of a mode-pass launch (at most one resident wave) for register width CM.
 template <class T>
-int mode_pass_grid(int CM, int P, int num_sms);
+int mode_pass_grid(int CM, int P, int num_sms, int N);
+// Warps per block of a mode-pass launch (shared memory decides).
+template <class T>
+int mode_pass_warps(int CM, int N);
 
 }  // namespace tfs

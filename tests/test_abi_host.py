@@ -108,13 +108,15 @@ def test_plan_covers_every_entry_once(lib, policy):
     assert bin_ptr[0] == 0 and bin_ptr[-1] == len(items)
     for b in range(P):
         assert np.all(items["bin"][bin_ptr[b]:bin_ptr[b + 1]] == b)
-    if policy != tf.SCHED_LPT:
-        assert n_slots == 0 and np.all(items["slot"] < 0)
+    assert n_slots == len(items)
+    assert sorted(items["slot"]) == list(range(len(items)))
+    if policy != tf.SCHED_LPT:   # whole rows only
+        assert len(items) == len(lengths)
 
 
 def test_lpt_splits_heavy_rows_and_balances(lib):
     rng = np.random.default_rng(8)
-    lengths = rng.zipf(1.1, 3000).clip(max=10 ** 6)
+    lengths = np.concatenate([rng.zipf(1.1, 3000).clip(max=10 ** 4), [400_000, 90_000]])
     off = _offsets(lengths)
     P = 64
     items, n_slots, bin_ptr = tf.plan_mode(off, P, 0, tf.SCHED_LPT)
@@ -122,9 +124,11 @@ def test_lpt_splits_heavy_rows_and_balances(lib):
     cap = -(-nnz // P)
     assert items["len"].max() <= cap
     # chunks of a split row take consecutive slots in entry order
-    chunks = items[items["slot"] >= 0]
-    assert n_slots == len(chunks)
-    for r in np.unique(chunks["row"]):
+    rows, counts = np.unique(items["row"], return_counts=True)
+    split = rows[counts > 1]
+    assert len(split) > 0 and n_slots == len(items)
+    chunks = items[np.isin(items["row"], split)]
+    for r in split:
         c = np.sort(chunks[chunks["row"] == r], order="slot")
         assert np.all(np.diff(c["slot"]) == 1)
         assert np.all(c["begin"][1:] == c["begin"][:-1] + c["len"][:-1])
@@ -137,4 +141,4 @@ def test_lpt_splits_heavy_rows_and_balances(lib):
 
 def test_plan_handles_empty_mode(lib):
     items, n_slots, bin_ptr = tf.plan_mode(np.zeros(4, np.int64), 8, 0, tf.SCHED_LPT)
-    assert len(items) == 3 and np.all(items["len"] == 0) and n_slots == 0
+    assert len(items) == 3 and np.all(items["len"] == 0) and n_slots == 3
