@@ -178,6 +178,12 @@ tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
  * for this GPU).  Results do not depend on the schedule. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
+/* Data path of the mode pass: 0 = automatic (TMA tile::gather4 feeding for float
+ * contexts with N = 3 and C <= 10, the cp.async SIMT pass otherwise), 1 = always the
+ * cp.async pass, 2 = require the TMA pass (TF_EINVAL from the next sweep if it does not
+ * apply).  Results agree to rounding; they are bit-identical within one path. */
+tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
+
 /* ------------------------------------------------------------------ timing */
 
 /* Kernel kinds reported by tf_get_profile. */

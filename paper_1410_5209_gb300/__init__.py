@@ -75,6 +75,7 @@ def load():
         "tf_get_residual": [P, P],
         "tf_get_counters": [P, P],
         "tf_set_schedule": [P, i32, i32],
+        "tf_set_kernel_path": [P, i32],
         "tf_profile": [P, i32],
         "tf_get_profile": [P, P, P],
         "tf_get_launch_trace": [P, i64, P, P, P, P],
@@ -231,6 +232,11 @@ class Factorization:
         out = np.empty(self.K, np.int32)
         self._check(self._lib.tf_default_order(self._ctx, int(sweep), int(C), _ptr(out)))
         return out
+
+    PATH_AUTO, PATH_SIMT, PATH_TMA = 0, 1, 2
+
+    def set_kernel_path(self, path):
+        self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
 
     def set_schedule(self, policy=SCHED_LPT, P=0):
         self._check(self._lib.tf_set_schedule(self._ctx, int(policy), int(P)))

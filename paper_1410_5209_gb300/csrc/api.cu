@@ -11,6 +11,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+
 #include "sweep.cuh"
 
 namespace tfs {
@@ -56,6 +58,9 @@ struct ModeLayout {
     Buf<SplitRow> single;   // rows held by one item
     int64_t n_items = 0, n_slots = 0;
     int n_split = 0, n_single = 0;
+    int64_t ostride = 0;    // elements between two other-mode index arrays
+    Buf<int32_t> rank_of;   // row id -> degree rank (slice row)
+    Buf<int32_t> id_of;     // degree rank -> row id
     int P = 0;
     int omode[kMaxModes - 1];
 };
@@ -104,6 +109,9 @@ struct Impl : CtxBase {
     int64_t prof_launches[TF_KIND_COUNT] = {0};
     double prof_ms[TF_KIND_COUNT] = {0};
 
+    int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported
+    CUtensorMap tmaps[kMaxModes][3];  // per mode: slice maps with boxes 8, 24, 40 floats
+    const void *tmaps_for_Z[kMaxModes] = {nullptr};
     int Cq = 0, CM_last = 1;       // columns Q held by the copies' R-hat; register width
                                    // (and so slice layout) of the sweep that left them
     bool dirty = false;            // residual copies must be rebuilt from the factors
@@ -256,13 +264,43 @@ struct Impl : CtxBase {
                     if (s.bits & kStatDup)
                         throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
                 }
-                L.oidx.alloc((size_t)std::max(N - 1, 1) * nnz);
+            }
+            // degree ranks: slices are stored with each mode's rows in decreasing order of
+            // their entry counts (equal counts by row id)
+            for (int n = 0; n < N; ++n) {
+                ModeLayout &L = mode[n];
+                std::vector<int64_t> off((size_t)L.I + 1);
+                TFS_CUDA(cudaMemcpyAsync(off.data(), L.off.p, off.size() * sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st));
+                TFS_CUDA(cudaStreamSynchronize(st));
+                std::vector<int32_t> id((size_t)L.I), rank((size_t)L.I);
+                for (int64_t i = 0; i < L.I; ++i) id[i] = (int32_t)i;
+                std::stable_sort(id.begin(), id.end(), [&](int32_t a_, int32_t b_) {
+                    return off[a_ + 1] - off[a_] > off[b_ + 1] - off[b_];
+                });
+                for (int64_t r = 0; r < L.I; ++r) rank[id[r]] = (int32_t)r;
+                L.id_of.alloc(L.I);
+                L.rank_of.alloc(L.I);
+                TFS_CUDA(cudaMemcpyAsync(L.id_of.p, id.data(), L.I * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, st));
+                TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, rank.data(), L.I * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, st));
+                TFS_CUDA(cudaStreamSynchronize(st));
+            }
+            for (int n = 0; n < N; ++n) {
+                ModeLayout &L = mode[n];
+                // index arrays start 256-byte aligned and end in 64 padding entries
+                // (bulk copies read fixed windows past a step's last entry)
+                L.ostride = (nnz + 64 + 63) / 64 * 64;
+                L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride);
+                TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0,
+                                         (size_t)std::max(N - 1, 1) * L.ostride * sizeof(int32_t), st));
                 int t = 0;
                 for (int l = 0; l < N; ++l) {
                     if (l == n) continue;
                     L.omode[t] = l;
-                    launch_gather_i32(soa.p + (size_t)l * nnz, L.perm.p, L.oidx.p + (size_t)t * nnz,
-                                      nnz, st);
+                    launch_gather_rank(soa.p + (size_t)l * nnz, L.perm.p, mode[l].rank_of.p,
+                                       L.oidx.p + (size_t)t * L.ostride, nnz, st);
                     ++t;
                 }
             }
@@ -284,7 +322,8 @@ struct Impl : CtxBase {
                 TFS_CUDA(cudaMemsetAsync(A[n].p, 0, (size_t)dims[n] * K * sizeof(T), st));
             else
                 launch_init_normal<T>(A[n].p, dims[n] * K, seed, (uint64_t)n, std, st);
-            res[n].alloc(nnz);
+            res[n].alloc(nnz + 64);
+            TFS_CUDA(cudaMemsetAsync(res[n].p, 0, (nnz + 64) * sizeof(T), st));
         }
         a0_zero = true;
         rebuild_residuals();
@@ -360,7 +399,8 @@ struct Impl : CtxBase {
             a.K = K;
             a.model_zero = a0_zero ? 1 : 0;
             for (int t = 0; t < N - 1; ++t) {
-                a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+                a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
+                a.id_o[t] = mode[L.omode[t]].id_of.p;
                 a.Ao[t] = A[L.omode[t]].p;
             }
             a.An = A[n].p;
@@ -377,7 +417,7 @@ struct Impl : CtxBase {
     void fill_other(Args &a, int n, const ModeLayout &L) {
         (void)n;
         for (int t = 0; t < N - 1; ++t) {
-            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
             a.Zo[t] = Z[L.omode[t]].p;
         }
     }
@@ -397,6 +437,7 @@ struct Impl : CtxBase {
             a.what = 2;
             fill_other(a, n, L);
             a.Zn = Z[n].p;
+            a.rank_n = L.rank_of.p;
             a.res = res[n].p;
             timed(TF_KIND_OTHER, [&] { launch_res<T>(a, CM_last, st); });
         }
@@ -462,6 +503,15 @@ struct Impl : CtxBase {
         }
         partials.ensure((size_t)std::max<int64_t>(max_slots, 1) * partial_stride(CM));
 
+        bool use_tma = false;
+        if constexpr (sizeof(T) == 4) {
+            if (path != 1 && tma_pass_supported(CM, N)) {
+                bool ok = true;
+                for (int l = 0; l < N; ++l) ok = ok && tmaps_for_Z[l] == (const void *)Z[l].p;
+                use_tma = ok || build_tmaps(W);
+            }
+        }
+        if (path == 2 && !use_tma) throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
         const int grid = mode_pass_grid<T>(CM, P, num_sms, N);
         const int warps_per_block = mode_pass_warps<T>(CM, N);
         const int nsplit = (K + C - 1) / C;
@@ -476,6 +526,7 @@ struct Impl : CtxBase {
             for (int l = 0; l < N; ++l) {
                 pk.Z[l] = Z[l].p;
                 pk.A[l] = A[l].p;
+                pk.id_of[l] = mode[l].id_of.p;
                 pk.row_base[l + 1] = pk.row_base[l] + dims[l];
             }
             pk.K = K;
@@ -504,10 +555,11 @@ struct Impl : CtxBase {
                     a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
                     a.lambda = (T)lambda;
                     for (int u = 0; u < N - 1; ++u) {
-                        a.oidx[u] = L.oidx.p + (size_t)u * nnz;
+                        a.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
                         a.Zo[u] = Z[L.omode[u]].p;
                     }
                     a.Zn = Z[n].p;
+                    a.rank_n = L.rank_of.p;
                     a.res = res[n].p;
                     a.A_n = A[n].p;
                     a.K = K;
@@ -516,10 +568,28 @@ struct Impl : CtxBase {
                     a.stat = stat.p;
                     a.ticket = ticket.p;
                     a.ticket_base = ticket_base;
+                    if constexpr (sizeof(T) == 4) {
+                        if (use_tma) {
+                            const int box[2] = {tma_box_for(CM, t == 0, L.omode[0] < n),
+                                                tma_box_for(CM, t == 0, L.omode[1] < n)};
+                            const int bidx[2] = {box[0] == 8 ? 0 : (box[0] == 24 ? 1 : 2),
+                                                 box[1] == 8 ? 0 : (box[1] == 24 ? 1 : 2)};
+                            CUtensorMap tm2[2] = {tmaps[L.omode[0]][bidx[0]],
+                                                  tmaps[L.omode[1]][bidx[1]]};
+                            const int tgrid = tma_pass_grid(CM, L.P, num_sms, t == 0, box);
+                            ticket_base += (unsigned long long)L.P +
+                                           (unsigned long long)tgrid * tma_pass_warps();
+                            timed(TF_KIND_MODE_PASS,
+                                  [&] { launch_mode_pass_tma(a, tm2, box, CM, tgrid, st); });
+                            ++launches;
+                            goto solved;
+                        }
+                    }
                     // every launched warp takes one ticket past the last bin
                     ticket_base += (unsigned long long)L.P + (unsigned long long)grid * warps_per_block;
                     timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, grid, st); });
                     ++launches;
+                solved:
                     if (L.n_single > 0) {
                         timed(TF_KIND_SOLVE,
                               [&] { launch_solve_rows<T>(a, CM, L.single.p, L.n_single, st); });
@@ -542,6 +612,44 @@ struct Impl : CtxBase {
         CM_last = CM;
         ++sweeps;
         last_launches = launches - launches0;
+    }
+
+    // Tensor maps of every mode's packed slice (float, W = 32): boxes of 8, 24, 40 floats,
+    // one row high (tile::gather4 loads), no swizzle, zero fill beyond the row.
+    bool build_tmaps(int W) {
+        typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                        const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                        const cuuint32_t *, CUtensorMapInterleave,
+                                        CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                        CUtensorMapFloatOOBfill);
+        static EncodeTiled enc = nullptr;
+        if (!enc) {
+            void *fp = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000,
+                                                 cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fp) {
+                cudaGetLastError();
+                return false;
+            }
+            enc = (EncodeTiled)fp;
+        }
+        static const cuuint32_t boxes[3] = {8, 24, 40};
+        for (int l = 0; l < N; ++l) {
+            const cuuint64_t gdim[2] = {(cuuint64_t)W, (cuuint64_t)dims[l]};
+            const cuuint64_t gstride[1] = {(cuuint64_t)W * sizeof(float)};
+            const cuuint32_t es[2] = {1, 1};
+            for (int b = 0; b < 3; ++b) {
+                const cuuint32_t box[2] = {boxes[b], 1};
+                if (enc(&tmaps[l][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)Z[l].p, gdim,
+                        gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return false;
+            }
+            tmaps_for_Z[l] = Z[l].p;
+        }
+        return true;
     }
 
     void default_order(int sweep_idx, int C, int32_t *out) const {
@@ -572,10 +680,11 @@ struct Impl : CtxBase {
         a.Cq = Cq;
         a.what = 0;
         for (int t = 0; t < N - 1; ++t) {
-            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
             a.Zo[t] = Z[L.omode[t]].p;
         }
         a.Zn = Z[0].p;
+        a.rank_n = L.rank_of.p;
         a.res = res[0].p;
         a.block_out = red.p + 2;
         double *regp = red.p + 2 + blocks;
@@ -611,10 +720,11 @@ struct Impl : CtxBase {
         a.Cq = Cq;
         a.what = 1;
         for (int t = 0; t < N - 1; ++t) {
-            a.oidx[t] = L.oidx.p + (size_t)t * nnz;
+            a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
             a.Zo[t] = Z[L.omode[t]].p;
         }
         a.Zn = Z[0].p;
+        a.rank_n = L.rank_of.p;
         a.res = res[0].p;
         a.perm = L.perm.p;
         a.out = out.p;
@@ -627,6 +737,11 @@ struct Impl : CtxBase {
 
     void check_errors() {
         DeviceStatus s = read_status();
+        if (s.bits & kStatTimeout) {
+            TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
+            TFS_CUDA(cudaStreamSynchronize(st));
+            throw ApiError{TF_ETIMEOUT, "a bounded wait in a kernel gave up; results are invalid"};
+        }
         if (s.bits & (kStatRange | kStatDup)) throw ApiError{TF_ECUDA, "device status corrupt"};
     }
 
@@ -932,6 +1047,11 @@ tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kin
                               int32_t *modes, float *ms) {
     if (!n || cap < 0) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) { c.launch_trace(cap, n, kinds, modes, ms); });
+}
+
+tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
+    if (path < 0 || path > 2) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { c.path = path; });
 }
 
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P) {

@@ -20,6 +20,7 @@ enum : int {
     kStatDup = 2,        // duplicate coordinate
     kStatFoldRange = 4,  // fold-in index out of range
     kStatFoldPivot = 8,  // fold-in Cholesky pivot <= 0
+    kStatTimeout = 16,   // a bounded wait on the device gave up
 };
 
 struct DeviceStatus {
@@ -103,6 +104,9 @@ void launch_gather_keys(const int32_t *col, const int32_t *perm, uint32_t *keys,
                         cudaStream_t st);
 void launch_gather_i32(const int32_t *col, const int32_t *perm, int32_t *out, int64_t n,
                        cudaStream_t st);
+// out[i] = rank[col[perm[i]]]
+void launch_gather_rank(const int32_t *col, const int32_t *perm, const int32_t *rank, int32_t *out,
+                        int64_t n, cudaStream_t st);
 void launch_offsets(const uint32_t *sorted_keys, int64_t n, int64_t I, int64_t *off,
                     cudaStream_t st);
 void launch_dup_check(const int32_t *coords_soa, int N, int64_t nnz, const int32_t *perm,

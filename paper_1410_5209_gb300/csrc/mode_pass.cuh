@@ -141,7 +141,7 @@ __device__ __forceinline__ bool chol_solve(T (&B)[CM * (CM + 1) / 2], const T (&
 
 template <class T, int CM>
 __device__ __forceinline__ void write_row(const PassArgs<T> &a, int row, const T (&x)[CM]) {
-    T *z = a.Zn + (int64_t)row * Geo<T, CM>::W;
+    T *z = a.Zn + (int64_t)a.rank_n[row] * Geo<T, CM>::W;
     T *Ar = a.A_n + (int64_t)row * a.K;
 #pragma unroll
     for (int c = 0; c < CM; ++c) {
@@ -317,8 +317,8 @@ struct OtherModes {
 template <class T, int CM, int NO>
 __device__ __forceinline__ void issue_idx(const Step &s, int32_t *ridx, T *rv, T *ownring,
                                           const OtherModes<T, NO> &om, const T *res,
-                                          const tf_item *items, const T *Zn, int own_off,
-                                          int own_len, int lane) {
+                                          const tf_item *items, const T *Zn, const int32_t *rank_n,
+                                          int own_off, int own_len, int lane) {
     if (!(s.flags & 1)) return;
     const int j = s.j0 + lane;
     if (j < s.jend) {
@@ -328,7 +328,7 @@ __device__ __forceinline__ void issue_idx(const Step &s, int32_t *ridx, T *rv, T
         cp_async_small<sizeof(T)>(rv + lane, res + j);
     }
     if ((s.flags & 2) && lane < own_len) {
-        const int64_t row = items[s.it].row;
+        const int64_t row = rank_n[items[s.it].row];
         cp_async_small<sizeof(T)>(ownring + lane, Zn + row * Geo<T, CM>::W + own_off + lane);
     }
 }
@@ -401,8 +401,8 @@ __device__ __forceinline__ void finish_item(const PassArgs<T> &a, const Step &s,
 // first inner iteration, the products that refresh R-hat: po = sum_{c<C} prod_l old_l[c]
 // (own old included) and pp = sum_{c<Cq} prod_l prev_l[c].  Other modes t >= n_lo come
 // after mode n and have not been updated in this split: their "old" is their "cur".
-// own = [prev (CM) | old (CM)] of the own row.
-template <class T, int CM, int NO, bool FIRST>
+// own is 16-byte aligned; its prev / old regions start at OWN_PREV / OWN_OLD.
+template <class T, int CM, int NO, bool FIRST, int OWN_PREV = 0, int OWN_OLD = CM>
 __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? NO : kMaxModes - 1)],
                                                const T *own, int no, int n_lo, int C, int Cq,
                                                T (&h)[CM], T &po, T &pp) {
@@ -422,7 +422,7 @@ __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? 
                 T x[CM], y[CM], o[CM];
                 lds_range<T, OP, CM>(x, r0);
                 lds_range<T, OP, CM>(y, r1);
-                lds_range<T, 0, CM>(o, own);
+                lds_range<T, OWN_PREV, CM>(o, own);
                 pp = T(0);
 #pragma unroll
                 for (int c = 0; c < CM; ++c)
@@ -430,7 +430,7 @@ __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? 
             }
             {
                 T o[CM];
-                lds_range<T, CM, CM>(o, own);
+                lds_range<T, OWN_OLD, CM>(o, own);
                 po = T(0);
                 if (n_lo == 0) {  // both other modes after n: old == cur, so po = own_old . h
 #pragma unroll
@@ -463,7 +463,7 @@ __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? 
             if (c >= C) h[c] = T(0);
         if constexpr (FIRST) {
             T q[CM];
-            lds_range<T, 0, CM>(q, own);  // own prev
+            lds_range<T, OWN_PREV, CM>(q, own);  // own prev
 #pragma unroll(NO > 0 ? NO : 1)
             for (int t = 0; t < (NO > 0 ? NO : no); ++t) {
                 lds_range<T, OP, CM>(x, rowp[t]);
@@ -474,7 +474,7 @@ __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? 
 #pragma unroll
             for (int c = 0; c < CM; ++c)
                 if (c < Cq) pp += q[c];
-            lds_range<T, CM, CM>(q, own);  // own old
+            lds_range<T, OWN_OLD, CM>(q, own);  // own old
 #pragma unroll(NO > 0 ? NO : 1)
             for (int t = 0; t < (NO > 0 ? NO : no); ++t) {
                 if (t < n_lo)
@@ -499,7 +499,8 @@ __device__ __forceinline__ void entry_products(const T *const (&rowp)[(NO > 0 ? 
 template <class T, int CM, int NV_LO, int NV_HI, int NO, class Consumer>
 __device__ __forceinline__ void run_bin(const tf_item *items, int64_t it0, int64_t it1,
                                         const OtherModes<T, NO> &om, const T *res, const T *Zn,
-                                        int n_lo, int own_off, int own_len, bool fetch_rows,
+                                        const int32_t *rank_n, int n_lo, int own_off, int own_len,
+                                        bool fetch_rows,
                                         PipeSmem<T, CM, NV_LO, NV_HI> &sm, Consumer &cons,
                                         int lane) {
     // prologue: steps 0 .. kLeadIdx-1 (indices), then rows of steps 0 .. kLeadRows-1
@@ -507,8 +508,8 @@ __device__ __forceinline__ void run_bin(const tf_item *items, int64_t it0, int64
 #pragma unroll
     for (int k = 0; k < kLeadIdx; ++k) {
         if (lane == 0) *sm.step(k) = gen;
-        issue_idx<T, CM, NO>(gen, sm.ridx(k), sm.rv(k), sm.ownring(k), om, res, items, Zn, own_off,
-                             own_len, lane);
+        issue_idx<T, CM, NO>(gen, sm.ridx(k), sm.rv(k), sm.ownring(k), om, res, items, Zn, rank_n,
+                             own_off, own_len, lane);
         gen = step_next(gen, items, it1);
     }
     cp_async_commit();
@@ -541,7 +542,7 @@ __device__ __forceinline__ void run_bin(const tf_item *items, int64_t it0, int64
             __syncwarp();  // everyone has read slot ia's step before it is replaced
             if (lane == 0) *sm.step(ia) = gen;
             issue_idx<T, CM, NO>(gen, sm.ridx(ia), sm.rv(ia), sm.ownring(ia), om, res, items, Zn,
-                                 own_off, own_len, lane);
+                                 rank_n, own_off, own_len, lane);
             gen = step_next(gen, items, it1);
             cp_async_commit();
         }
@@ -668,8 +669,8 @@ __global__ void __launch_bounds__(kPassThreads, (sizeof(T) == 4 && CM <= 12) ? 4
         if (tk >= (unsigned long long)a.P) break;
         const int bin = (int)tk;
         run_bin<T, CM, Cons::NV_LO, Cons::NV_HI, NO>(a.items, a.bin_ptr[bin], a.bin_ptr[bin + 1],
-                                                     om, a.res, a.Zn, n_lo, CM, own_len, true, sm,
-                                                     cons, lane);
+                                                     om, a.res, a.Zn, a.rank_n, n_lo, CM, own_len,
+                                                     true, sm, cons, lane);
     }
 }
 
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(kPassThreads) k_res(const ResArgs<T> a) {
     const int bin = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (bin < a.P)
         run_bin<T, CM, Cons::NV_LO, Cons::NV_HI, 0>(a.items, a.bin_ptr[bin], a.bin_ptr[bin + 1], om,
-                                                    a.res, a.Zn, no, 0, a.Cq > 0 ? CM : 0,
+                                                    a.res, a.Zn, a.rank_n, no, 0, a.Cq > 0 ? CM : 0,
                                                     a.Cq > 0, sm, cons, lane);
     if (a.what != 0) return;
     const double acc = warp_sum_d(cons.acc);

@@ -170,6 +170,13 @@ __global__ void k_gather_i32(const int32_t *__restrict__ col, const int32_t *__r
     if (i < n) out[i] = col[perm[i]];
 }
 
+__global__ void k_gather_rank(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
+                              const int32_t *__restrict__ rank, int32_t *__restrict__ out,
+                              int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = rank[col[perm[i]]];
+}
+
 // off[i] = first sorted position whose key is >= i, for i in 0..I (so off[I] = n).
 __global__ void k_offsets(const uint32_t *__restrict__ keys, int64_t n, int64_t I,
                           int64_t *__restrict__ off) {
@@ -306,6 +313,13 @@ void launch_gather_i32(const int32_t *col, const int32_t *perm, int32_t *out, in
                        cudaStream_t st) {
     if (n <= 0) return;
     k_gather_i32<<<grid_for(n, 256), 256, 0, st>>>(col, perm, out, n);
+    TFS_CUDA(cudaGetLastError());
+}
+
+void launch_gather_rank(const int32_t *col, const int32_t *perm, const int32_t *rank, int32_t *out,
+                        int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    k_gather_rank<<<grid_for(n, 256), 256, 0, st>>>(col, perm, rank, out, n);
     TFS_CUDA(cudaGetLastError());
 }
 

@@ -25,8 +25,8 @@ __global__ void k_pack(const PackArgs<T> a) {
     if (r >= a.row_base[a.N]) return;
     int l = 0;
     while (r >= a.row_base[l + 1]) ++l;
-    const int64_t i = r - a.row_base[l];
-    const T *Ar = a.A[l] + i * a.K;
+    const int64_t i = r - a.row_base[l];  // slice row (rank)
+    const T *Ar = a.A[l] + (int64_t)a.id_of[l][i] * a.K;
     T *z = a.Z[l] + i * a.W;
     for (int c = 0; c < a.C; ++c) {
         const T v = Ar[a.S[c]];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kResThreads) k_init_res(const InitArgs<T> a) {
                 for (int k = 0; k < a.K; ++k) {
                     T q = An[k];
                     for (int t = 0; t < a.N - 1; ++t)
-                        q *= a.Ao[t][(int64_t)a.oidx[t][j] * a.K + k];
+                        q *= a.Ao[t][(int64_t)a.id_o[t][a.oidx[t][j]] * a.K + k];
                     model += q;
                 }
             }

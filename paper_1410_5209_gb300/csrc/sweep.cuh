@@ -16,7 +16,9 @@ struct SplitRow {
 };
 
 // Packed slice layout, one row of W = slice_stride_elems(CM) elements per factor row i
-// of mode l, where CM >= C is the register width the sweep was compiled for:
+// of mode l, stored at the row's degree rank in that mode (rows with the most entries
+// first; the other-mode index streams hold ranks), where CM >= C is the register width
+// the sweep was compiled for:
 //   [0, C)            "cur":  a^(l)_{i,S} as updated in this split
 //   [CM, CM + Cq)     "prev": a^(l)_{i,Q}, the previous split's columns (final values)
 //   [2CM, 2CM + C)    "old":  a^(l)_{i,S} at the start of the split
@@ -36,7 +38,8 @@ struct PassArgs {
     T lambda;
     const int32_t *oidx[kMaxModes - 1];  // other-mode indices, mode-n order
     const T *Zo[kMaxModes - 1];          // packed slices of those modes
-    T *Zn;                               // packed slice of mode n
+    T *Zn;                               // packed slice of mode n (rows in rank order)
+    const int32_t *rank_n;               // row id of mode n -> slice row (degree rank)
     T *res;                              // residual copy of mode n
     T *A_n;                              // factor matrix of mode n [I_n][K]
     int K;
@@ -55,6 +58,7 @@ struct PackArgs {
     int64_t row_base[kMaxModes + 1];
     int K, W, C, Cq, off_old, off_prev;
     const int32_t *S, *Q;
+    const int32_t *id_of[kMaxModes];  // slice row (rank) -> row id, per mode
 };
 
 // Residual of copy n against the columns held in the slices' "cur" region:
@@ -69,6 +73,7 @@ struct ResArgs {
     const int32_t *oidx[kMaxModes - 1];
     const T *Zo[kMaxModes - 1];
     const T *Zn;
+    const int32_t *rank_n;
     T *res;
     double *block_out;
     const int32_t *perm;
@@ -82,7 +87,8 @@ struct InitArgs {
     const int64_t *bin_ptr;
     int P;
     int N, n, K, model_zero;
-    const int32_t *oidx[kMaxModes - 1];
+    const int32_t *oidx[kMaxModes - 1];   // ranks of the other modes' rows
+    const int32_t *id_o[kMaxModes - 1];   // rank -> row id of those modes
     const T *Ao[kMaxModes - 1];
     const T *An;
     const T *x;
@@ -163,5 +169,14 @@ int mode_pass_grid(int CM, int P, int num_sms, int N);
 // Warps per block of a mode-pass launch (shared memory decides).
 template <class T>
 int mode_pass_warps(int CM, int N);
+
+// TMA-fed mode pass (float, N = 3, CM <= 10): tensor maps of the other modes' slices
+// with box widths box[t] (tma_pass.cuh).  tmaps points at two CUtensorMap objects.
+bool tma_pass_supported(int CM, int N);
+int tma_box_for(int CM, bool first, bool before_n);
+int tma_pass_warps();
+int tma_pass_grid(int CM, int P, int num_sms, bool first, const int box[2]);
+void launch_mode_pass_tma(const PassArgs<float> &a, const void *tmaps, const int box[2], int CM,
+                          int grid, cudaStream_t st);
 
 }  // namespace tfs

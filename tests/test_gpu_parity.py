@@ -262,6 +262,22 @@ def test_schedule_does_not_change_results():
         assert np.array_equal(f1.factors(n), f2.factors(n))
 
 
+@pytest.mark.parametrize("C", [6, 8, 10])
+def test_tma_and_simt_paths_bit_identical(C):
+    """The TMA-fed pass (tile::gather4 rows, bulk index windows) and the cp.async pass
+    perform the same arithmetic in the same order: identical bits."""
+    p = synth.small(51, (3000, 2000, 300), 200_000, 4, 20, modes=["zipf", "zipf", "uniform"])
+    out = []
+    for path in (tf.Factorization.PATH_SIMT, tf.Factorization.PATH_TMA):
+        f, _, _ = make(p, tf.F32)
+        f.set_kernel_path(path)
+        for s in range(2):
+            f.sweep(C, 0.1, 1 if s == 0 else 2, p.column_order(s, C))
+        out.append([f.factors(n) for n in range(3)] + [f.residual(), np.array(f.loss(0.1))])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_deterministic_rerun_fp32():
     p = synth.small(34, (300, 300, 30), 50_000, 3, 10, modes=["zipf", "uniform", "uniform"])
     res = []
