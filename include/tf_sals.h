@@ -147,6 +147,32 @@ tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_ord
 tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
                   double *train_rmse);
 
+/* The loss of tf_loss, computed without allocating device memory; the paper has no
+ * counterpart (it is an interface for callers, not part of the method).
+ * Meant for callers that cannot call cudaMalloc at this point: a process whose device
+ * memory is already reserved by another allocator (a caching allocator or a serving
+ * engine that holds the free memory as its own pool), so that a new allocation fails
+ * or fragments that pool, and latency-bound loops that must not take the device-wide
+ * synchronisation a cudaMalloc or cudaFree may cause.  tf_loss keeps its reduction
+ * buffer in the context and allocates it on first use; this entry point instead uses a
+ * fixed device array of 8192 doubles (64 KiB) built into the library, one per device,
+ * and calls no allocating routine.
+ *   Arguments, result and synchronisation as tf_loss; the result is bit-identical to
+ *   tf_loss's on the same state.
+ *   Limit: the reduction needs 2 + B + 256 N doubles, B = the residual kernel's block
+ *   count (at most P, the schedule's bin count).  Beyond 8192 the call returns
+ *   TF_EINVAL, says so in tf_last_error, and launches nothing; the default schedule
+ *   fits for every N <= 8 on a 152-SM GPU.
+ *   Set-up: the first call on each device (the device current at the call) looks up
+ *   the array's device address with cudaGetSymbolAddress; make that first call before
+ *   any stream capture begins.
+ *   Sharing: every call on a device uses the same array, which keeps the previous
+ *   call's contents.  Each call writes every element it reads before reading it, so
+ *   nothing needs clearing.  Calls that overlap on the GPU (from several host threads,
+ *   or several contexts, on one device) race on the array: serialise them. */
+tf_status tf_loss_noalloc(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
+                          double *train_rmse);
+
 /* ------------------------------------------------------------------ fold-in */
 
 /* Least-squares row for a new slice of mode `mode` against the frozen factors: the

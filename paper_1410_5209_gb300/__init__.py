@@ -70,6 +70,7 @@ def load():
         "tf_sals_sweep_ex": [P, i32, f64, i32, P, u32],
         "tf_default_order": [P, i32, i32, P],
         "tf_loss": [P, f64, u32, P, P],
+        "tf_loss_noalloc": [P, f64, u32, P, P],
         "tf_foldin": [P, i32, P, P, i64, f64, P],
         "tf_get_grouping": [P, i32, P, P],
         "tf_get_residual": [P, P],
@@ -190,6 +191,14 @@ class Factorization:
         l, r = ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.tf_loss(self._ctx, float(lam), WEIGHTED_LAMBDA if weighted else 0,
                                       ctypes.byref(l), ctypes.byref(r)))
+        return l.value, r.value
+
+    def loss_noalloc(self, lam, weighted=False):
+        """As loss(), through tf_loss_noalloc: no device allocation, fixed-size scratch."""
+        l, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.tf_loss_noalloc(self._ctx, float(lam),
+                                              WEIGHTED_LAMBDA if weighted else 0,
+                                              ctypes.byref(l), ctypes.byref(r)))
         return l.value, r.value
 
     def foldin(self, mode, other, values, lam):

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -706,6 +707,51 @@ struct Impl : CtxBase {
         if (rmse_out) *rmse_out = nnz > 0 ? sqrt(h[0] / (double)nnz) : 0.0;
     }
 
+    // loss() with its block partials and two sums in `scratch` (cap doubles, device
+    // memory the caller owns) instead of the context's reduction buffer: the same
+    // kernels in the same order, so the result is bit-identical to loss().
+    void loss_into(double lambda, uint32_t flags, double *loss_out, double *rmse_out,
+                   double *scratch, size_t cap) {
+        const ModeLayout &L = mode[0];
+        const int blocks = res_grid<T>(CM_last, L.P, N);
+        const int reg_blocks = 256;
+        const size_t need = 2 + (size_t)blocks + (size_t)N * reg_blocks;
+        if (need > cap)
+            throw ApiError{TF_EINVAL, "loss reduction needs " + std::to_string(need) +
+                                          " scratch doubles; the static array holds " +
+                                          std::to_string(cap) + " (lower P in tf_set_schedule)"};
+        if (dirty) rebuild_residuals();
+        ResArgs<T> a{};
+        a.items = L.items.p;
+        a.bin_ptr = L.bin_ptr.p;
+        a.P = L.P;
+        a.N = N;
+        a.n = 0;
+        a.Cq = Cq;
+        a.what = 0;
+        for (int t = 0; t < N - 1; ++t) {
+            a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
+            a.Zo[t] = Z[L.omode[t]].p;
+        }
+        a.Zn = Z[0].p;
+        a.rank_n = L.rank_of.p;
+        a.res = res[0].p;
+        a.block_out = scratch + 2;
+        double *regp = scratch + 2 + blocks;
+        launch_res<T>(a, CM_last, st);
+        launch_sum_blocks(scratch + 2, blocks, scratch + 0, st);
+        for (int n = 0; n < N; ++n)
+            launch_reg<T>(A[n].p, dims[n], K, (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,
+                          regp + (size_t)n * reg_blocks, reg_blocks, st);
+        launch_sum_blocks(regp, N * reg_blocks, scratch + 1, st);
+        double h[2];
+        TFS_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+        if (loss_out) *loss_out = h[0] + lambda * h[1];
+        if (rmse_out) *rmse_out = nnz > 0 ? sqrt(h[0] / (double)nnz) : 0.0;
+    }
+
     void get_residual(T *host_r) {
         if (dirty) rebuild_residuals();
         Buf<T> out;
@@ -863,6 +909,40 @@ struct tf_ctx {
     std::string err;
 };
 
+// ------------------------------------------------------------ loss without allocation
+// Scratch of tf_loss_noalloc: the per-block partial sums of the loss reductions and the
+// two totals, in a fixed device array instead of memory the context allocates.  One
+// array per device, shared by every call on that device.
+static constexpr size_t kLossScratchDoubles = 8192;  // 64 KiB
+static __device__ __align__(256) double g_loss_scratch[kLossScratchDoubles];
+
+namespace {
+
+// Device address of g_loss_scratch on the current device, looked up once per device
+// (the first call on a device does the lookup; later calls reuse it).
+double *loss_scratch_current_device() {
+    int dev = 0;
+    TFS_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::vector<double *> addr;  // by device ordinal
+    std::lock_guard<std::mutex> lock(mu);
+    if ((size_t)dev >= addr.size()) addr.resize((size_t)dev + 1, nullptr);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            throw tfs::ApiError{TF_ECUDA, std::string("cudaGetSymbolAddress of the loss scratch "
+                                                      "array failed: ") +
+                                              cudaGetErrorString(e)};
+        }
+        addr[dev] = static_cast<double *>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
 namespace {
 
 thread_local std::string g_create_err;
@@ -1006,6 +1086,14 @@ tf_status tf_default_order(const tf_ctx *ctx, int sweep, int C, int32_t *col_ord
 
 tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss, double *train_rmse) {
     return dispatch(ctx, [&](auto &c) { c.loss(lambda, flags, loss, train_rmse); });
+}
+
+tf_status tf_loss_noalloc(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
+                          double *train_rmse) {
+    return dispatch(ctx, [&](auto &c) {
+        c.loss_into(lambda, flags, loss, train_rmse, loss_scratch_current_device(),
+                    kLossScratchDoubles);
+    });
 }
 
 tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values, int64_t m,

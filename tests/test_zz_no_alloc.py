@@ -1,0 +1,80 @@
+"""tf_loss_noalloc -- the loss of tf_loss computed with a fixed, library-owned device
+array as its scratch instead of memory the context allocates -- checked through the C
+ABI against tf_loss on the same state.
+
+The loss tolerance of the other device tests applies (1e-9 relative); the two entry
+points run the same kernels in the same order, so in practice they agree exactly.
+This file is collected last so that it also runs after everything else has used the
+device; it needs nothing from the other test files and passes on its own."""
+import numpy as np
+import pytest
+
+import paper_1410_5209_gb300 as tf
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1410_5209_gb300 import build
+    build.build()
+
+
+def close(got, ref):
+    return all(abs(g - r) <= TOL * abs(r) for g, r in zip(got, ref))
+
+
+def factorization(p, dtype):
+    c, x = p.numpy()
+    return tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=dtype)
+
+
+@pytest.mark.parametrize("dtype", [tf.F64, tf.F32])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_noalloc_loss_matches_tf_loss(dtype, weighted):
+    """Two calls in a row (a sweep between them, so the second call finds the first
+    call's partial sums in the array), each against tf_loss.  The first call comes
+    before tf_loss has ever allocated its buffer on this context."""
+    p = synth.small(41, (300, 200, 50), 30_000, 3, 8)
+    f = factorization(p, dtype)
+    for call in range(2):
+        f.sweep(4, 0.3, 1, p.column_order(call, 4), weighted=weighted)
+        got = f.loss_noalloc(0.3, weighted)
+        ref = f.loss(0.3, weighted)
+        assert close(got, ref), (call, got, ref)
+        assert got[1] > 0
+
+
+def test_noalloc_loss_across_contexts():
+    """Contexts of different shapes (N = 4, then N = 3, other block counts) share the
+    array; stale partial sums of the larger reduction never reach the smaller one."""
+    p4 = synth.small(42, (120, 90, 60, 30), 25_000, 2, 6)
+    p3 = synth.small(43, (500, 40, 30), 4_000, 2, 5)
+    f4, f3 = factorization(p4, tf.F64), factorization(p3, tf.F64)
+    f4.sweep(2, 0.1, 1, p4.column_order(0, 2))
+    f3.sweep(1, 0.1, 1, p3.column_order(0, 1))
+    for _ in range(2):
+        for f in (f4, f3):
+            got = f.loss_noalloc(0.1)
+            assert close(got, f.loss(0.1)), got
+
+
+def test_noalloc_loss_rejects_oversized_reduction():
+    """A schedule with far more bins than the array has room for partial sums is
+    refused with TF_EINVAL before anything is launched; tf_loss still works and the
+    context stays usable."""
+    p = synth.small(44, (300, 200, 50), 30_000, 3, 4)
+    f = factorization(p, tf.F64)
+    f.sweep(2, 0.2, 1, p.column_order(0, 2))
+    ref = f.loss(0.2)
+    f.set_schedule(tf.SCHED_LPT, 200_000)
+    with pytest.raises(tf.TFError) as e:
+        f.loss_noalloc(0.2)
+    assert e.value.status == tf.EINVAL
+    assert "scratch" in str(e.value)
+    assert close(f.loss(0.2), ref)
+    f.set_schedule(tf.SCHED_LPT, 0)
+    assert close(f.loss_noalloc(0.2), ref)
