@@ -31,16 +31,18 @@ UNIT = "nnz*rank/s"
 WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=100_000_000,
                 K=100, C=10, T_in=1, lam=0.1, rank_truth=50, zipf=1.1)
 
-# DRAM traffic of one k_mode_pass launch from the ncu capture summarised in
-# profiles/k_mode_pass_skewed_3way.md, and a hash of the kernel source it was taken
-# with; reported as null once the kernel changes.
-NCU_TRAFFIC = None   # bytes per launch, filled from the capture
-NCU_SOURCE_HASH = None
+# DRAM traffic (read + write) of one mode-pass launch from the ncu capture summarised in
+# profiles/k_mode_pass_tma_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
+# 1e8-entry launch), and the hash of the kernel sources it was taken with; the bench
+# reports traffic as null once the sources differ or the entry count is not 1e8.
+NCU_TRAFFIC = 1.852e9
+NCU_TRAFFIC_NNZ = 100_000_000
+NCU_SOURCE_HASH = "91b1500e293e1634"
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mode_pass.cuh", "sweep.cuh"):
+    for f in ("mode_pass.cuh", "tma_pass.cuh", "sweep.cuh"):
         with open(os.path.join(ROOT, "paper_1410_5209_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -244,9 +246,11 @@ def main():
     mp_avg_ms = mp_ms / max(mp_n, 1)
     bytes_per_launch = nnz * (4 * (N - 1) + 4 + 4.0 / (N * T_in))
     achieved = bytes_per_launch / (mp_avg_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC if (NCU_SOURCE_HASH and NCU_SOURCE_HASH == kernel_source_hash()) else None
+    traffic = NCU_TRAFFIC if (NCU_SOURCE_HASH == kernel_source_hash()
+                              and nnz == NCU_TRAFFIC_NNZ) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_mode_pass",
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": "k_mode_pass_tma" if cnt["pass_path"] == 2 else "k_mode_pass",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": mp_avg_ms}
@@ -284,7 +288,7 @@ def main():
     cn, xn = c_pin.numpy(), x_pin.numpy()
     outs = [np.empty((d, K), np.float32) for d in WORKLOAD["dims"]]
     e2e_times = []
-    for s in range(args.e2e_steps + 1):
+    for s in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = tf.Factorization(cn, xn, WORKLOAD["dims"], K, seed=args.seed + rank, dtype=tf.F32,
@@ -297,12 +301,12 @@ def main():
         g.close()
         if s > 0:   # the first one is a warm-up
             e2e_times.append(time.perf_counter() - t0)
-    e2e_s = max(e2e_times) if world == 1 else max(e2e_times)
-    if world > 1:
+    e2e_s = max(e2e_times) if e2e_times else float("nan")
+    if world > 1 and e2e_times:
         tt = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    out["e2e"] = {"value": units / e2e_s, "unit": UNIT,
+    out["e2e"] = None if not e2e_times else {"value": units / e2e_s, "unit": UNIT,
                   "h2d_bytes_per_step": nnz * (4 * N + 4),
                   "d2h_bytes_per_step": sum(WORKLOAD["dims"]) * K * 4 + 16,
                   "what": "tf_create from pinned host COO + 1 sweep + tf_loss + factors to host "

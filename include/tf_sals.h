@@ -197,7 +197,10 @@ tf_status tf_get_residual(tf_ctx *ctx, void *host_r);
 
 /* counters[0] = rows left unchanged by a non-positive pivot since creation,
  * counters[1] = sweeps run, counters[2] = kernels launched by the last sweep,
- * counters[3] = work items of all modes, counters[4] = rows split across bins. */
+ * counters[3] = work items of all modes, counters[4] = rows split across bins,
+ * counters[5] = bins P of the schedule, counters[6] = kernels launched by the last
+ * tf_loss, counters[7] = mode-pass data path of the last sweep (1 = cp.async SIMT
+ * pass, 2 = TMA gather pass, 0 = no sweep yet). */
 tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
 
 /* Re-plans the row schedule of every mode (policy, P bins; P = 0 picks the default

@@ -234,7 +234,7 @@ class Factorization:
         c = np.zeros(8, np.int64)
         self._check(self._lib.tf_get_counters(self._ctx, _ptr(c)))
         keys = ["singular_rows", "sweeps", "last_sweep_launches", "items", "split_rows", "bins",
-                "loss_launches"]
+                "loss_launches", "pass_path"]
         return {k: int(v) for k, v in zip(keys, c)}
 
     def default_order(self, sweep, C):

@@ -118,6 +118,7 @@ struct Impl : CtxBase {
     bool dirty = false;            // residual copies must be rebuilt from the factors
     bool a0_zero = true;           // A^(1) known to be zero (R = X)
     int64_t sweeps = 0, last_launches = 0, loss_launches = 0;
+    int64_t last_path = 0;  // mode-pass data path of the last sweep: 1 cp.async, 2 TMA
     int64_t launches = 0;
 
     ~Impl() override {
@@ -513,6 +514,7 @@ struct Impl : CtxBase {
             }
         }
         if (path == 2 && !use_tma) throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
+        last_path = use_tma ? 2 : 1;
         const int grid = mode_pass_grid<T>(CM, P, num_sms, N);
         const int warps_per_block = mode_pass_warps<T>(CM, N);
         const int nsplit = (K + C - 1) / C;
@@ -889,7 +891,7 @@ struct Impl : CtxBase {
         c[4] = split;
         c[5] = P;
         c[6] = loss_launches;
-        c[7] = 0;
+        c[7] = last_path;
     }
 
     void set_schedule(tf_sched_policy pol, int P_) {
