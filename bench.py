@@ -250,7 +250,8 @@ def main():
                               and nnz == NCU_TRAFFIC_NNZ) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "k_mode_pass_tma" if cnt["pass_path"] == 2 else "k_mode_pass",
+                "kernel": {1: "k_mode_pass", 2: "k_mode_pass_tma",
+                           3: "k_mode_pass + k_mode_pass_tma"}.get(cnt["pass_path"], "?"),
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": mp_avg_ms}

@@ -199,18 +199,19 @@ tf_status tf_get_residual(tf_ctx *ctx, void *host_r);
  * counters[1] = sweeps run, counters[2] = kernels launched by the last sweep,
  * counters[3] = work items of all modes, counters[4] = rows split across bins,
  * counters[5] = bins P of the schedule, counters[6] = kernels launched by the last
- * tf_loss, counters[7] = mode-pass data path of the last sweep (1 = cp.async SIMT
- * pass, 2 = TMA gather pass, 0 = no sweep yet). */
+ * tf_loss, counters[7] = mode-pass data paths the last sweep used (bit 0: cp.async
+ * SIMT pass, bit 1: TMA gather pass; 0 = no sweep yet). */
 tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
 
 /* Re-plans the row schedule of every mode (policy, P bins; P = 0 picks the default
  * for this GPU).  Results do not depend on the schedule. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
-/* Data path of the mode pass: 0 = automatic (TMA tile::gather4 feeding for float
- * contexts with N = 3 and C <= 10, the cp.async SIMT pass otherwise), 1 = always the
- * cp.async pass, 2 = require the TMA pass (TF_EINVAL from the next sweep if it does not
- * apply).  Results agree to rounding; they are bit-identical within one path. */
+/* Data path of the mode pass: 0 = automatic (per pass: the TMA tile::gather4 pass for
+ * float contexts with N = 3 and C <= 10 when one other mode's slice fits its
+ * shared-memory row cache whole, the cp.async SIMT pass otherwise), 1 = always the
+ * cp.async pass, 2 = the TMA pass wherever it applies (TF_EINVAL from the next sweep if
+ * it does not).  Both paths give bit-identical results. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
 /* ------------------------------------------------------------------ timing */

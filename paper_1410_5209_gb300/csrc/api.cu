@@ -118,7 +118,7 @@ struct Impl : CtxBase {
     bool dirty = false;            // residual copies must be rebuilt from the factors
     bool a0_zero = true;           // A^(1) known to be zero (R = X)
     int64_t sweeps = 0, last_launches = 0, loss_launches = 0;
-    int64_t last_path = 0;  // mode-pass data path of the last sweep: 1 cp.async, 2 TMA
+    int64_t last_path = 0;  // mode-pass paths of the last sweep: bit 0 cp.async, bit 1 TMA
     int64_t launches = 0;
 
     ~Impl() override {
@@ -514,7 +514,7 @@ struct Impl : CtxBase {
             }
         }
         if (path == 2 && !use_tma) throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
-        last_path = use_tma ? 2 : 1;
+        last_path = 0;
         const int grid = mode_pass_grid<T>(CM, P, num_sms, N);
         const int warps_per_block = mode_pass_warps<T>(CM, N);
         const int nsplit = (K + C - 1) / C;
@@ -573,24 +573,33 @@ struct Impl : CtxBase {
                     a.ticket_base = ticket_base;
                     if constexpr (sizeof(T) == 4) {
                         if (use_tma) {
-                            const int box[2] = {tma_box_for(CM, t == 0, L.omode[0] < n),
-                                                tma_box_for(CM, t == 0, L.omode[1] < n)};
-                            const int bidx[2] = {box[0] == 8 ? 0 : (box[0] == 24 ? 1 : 2),
-                                                 box[1] == 8 ? 0 : (box[1] == 24 ? 1 : 2)};
+                            const bool before[2] = {L.omode[0] < n, L.omode[1] < n};
+                            const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                            const TmaPlan plan =
+                                tma_pass_plan(CM, t == 0, before, dims_o, num_sms, L.P);
+                            // automatic choice: the TMA pass wins where it holds a whole
+                            // other mode in its row cache, the cp.async pass elsewhere
+                            if (path == 0 && !(plan.whole[0] || plan.whole[1])) goto simt;
+                            const int bidx[2] = {
+                                plan.box[0] == 8 ? 0 : (plan.box[0] == 24 ? 1 : 2),
+                                plan.box[1] == 8 ? 0 : (plan.box[1] == 24 ? 1 : 2)};
                             CUtensorMap tm2[2] = {tmaps[L.omode[0]][bidx[0]],
                                                   tmaps[L.omode[1]][bidx[1]]};
-                            const int tgrid = tma_pass_grid(CM, L.P, num_sms, t == 0, box);
                             ticket_base += (unsigned long long)L.P +
-                                           (unsigned long long)tgrid * tma_pass_warps();
-                            timed(TF_KIND_MODE_PASS,
-                                  [&] { launch_mode_pass_tma(a, tm2, box, CM, tgrid, st); });
+                                           (unsigned long long)plan.grid * plan.warps;
+                            timed(TF_KIND_MODE_PASS, [&] {
+                                launch_mode_pass_tma(a, tm2, plan, CM, t == 0, before, st);
+                            });
+                            last_path |= 2;
                             ++launches;
                             goto solved;
                         }
                     }
+                simt:
                     // every launched warp takes one ticket past the last bin
                     ticket_base += (unsigned long long)L.P + (unsigned long long)grid * warps_per_block;
                     timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, grid, st); });
+                    last_path |= 1;
                     ++launches;
                 solved:
                     if (L.n_single > 0) {

@@ -170,13 +170,22 @@ int mode_pass_grid(int CM, int P, int num_sms, int N);
 template <class T>
 int mode_pass_warps(int CM, int N);
 
-// TMA-fed mode pass (float, N = 3, CM <= 10): tensor maps of the other modes' slices
-// with box widths box[t] (tma_pass.cuh).  tmaps points at two CUtensorMap objects.
+// TMA-fed mode pass (float, N = 3, CM <= 10; tma_pass.cuh).  A plan fixes the gather
+// box width per other mode, the rows of each other mode's slice held in the block's
+// shared-memory cache, and the warps per block (one block per SM).
 bool tma_pass_supported(int CM, int N);
 int tma_box_for(int CM, bool first, bool before_n);
-int tma_pass_warps();
-int tma_pass_grid(int CM, int P, int num_sms, bool first, const int box[2]);
-void launch_mode_pass_tma(const PassArgs<float> &a, const void *tmaps, const int box[2], int CM,
-                          int grid, cudaStream_t st);
+struct TmaPlan {
+    int warps = 0, grid = 0;
+    int box[2] = {0, 0};
+    int hot[2] = {0, 0};
+    bool whole[2] = {false, false};  // cached whole: never gathered, no row-slot space
+    size_t smem = 0;
+};
+TmaPlan tma_pass_plan(int CM, bool first, const bool before_n[2], const int64_t dims_o[2],
+                      int num_sms, int P);
+// tmaps points at two CUtensorMap objects (the other modes' slices, box widths plan.box).
+void launch_mode_pass_tma(const PassArgs<float> &a, const void *tmaps, const TmaPlan &plan,
+                          int CM, bool first, const bool before_n[2], cudaStream_t st);
 
 }  // namespace tfs
