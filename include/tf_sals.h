@@ -207,11 +207,11 @@ tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
  * for this GPU).  Results do not depend on the schedule. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
-/* Data path of the mode pass: 0 = automatic (per pass: the TMA tile::gather4 pass for
- * float contexts with N = 3 and C <= 10 when one other mode's slice fits its
- * shared-memory row cache whole, the cp.async SIMT pass otherwise), 1 = always the
- * cp.async pass, 2 = the TMA pass wherever it applies (TF_EINVAL from the next sweep if
- * it does not).  Both paths give bit-identical results. */
+/* Data path of the mode pass: 0 = automatic (the cp.async SIMT pass, whose slice-row
+ * gathers are served by L1 for hot rows), 1 = the cp.async pass, 2 = the TMA
+ * tile::gather4 pass with its shared-memory row cache (float contexts with N = 3 and
+ * C <= 10; TF_EINVAL from the next sweep where it does not apply).  Both paths give
+ * bit-identical results. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
 /* ------------------------------------------------------------------ timing */

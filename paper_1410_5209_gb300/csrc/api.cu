@@ -507,7 +507,9 @@ struct Impl : CtxBase {
 
         bool use_tma = false;
         if constexpr (sizeof(T) == 4) {
-            if (path != 1 && tma_pass_supported(CM, N)) {
+            // the TMA pass only on request: the cp.async pass reads hot slice rows from
+            // L1, which TMA loads bypass, and measures faster on skewed tensors
+            if (path == 2 && tma_pass_supported(CM, N)) {
                 bool ok = true;
                 for (int l = 0; l < N; ++l) ok = ok && tmaps_for_Z[l] == (const void *)Z[l].p;
                 use_tma = ok || build_tmaps(W);
@@ -515,8 +517,6 @@ struct Impl : CtxBase {
         }
         if (path == 2 && !use_tma) throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
         last_path = 0;
-        const int grid = mode_pass_grid<T>(CM, P, num_sms, N);
-        const int warps_per_block = mode_pass_warps<T>(CM, N);
         const int nsplit = (K + C - 1) / C;
         int cq = Cq;
         const int32_t *Qp = d_Q.p;
@@ -577,9 +577,7 @@ struct Impl : CtxBase {
                             const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
                             const TmaPlan plan =
                                 tma_pass_plan(CM, t == 0, before, dims_o, num_sms, L.P);
-                            // automatic choice: the TMA pass wins where it holds a whole
-                            // other mode in its row cache, the cp.async pass elsewhere
-                            if (path == 0 && !(plan.whole[0] || plan.whole[1])) goto simt;
+
                             const int bidx[2] = {
                                 plan.box[0] == 8 ? 0 : (plan.box[0] == 24 ? 1 : 2),
                                 plan.box[1] == 8 ? 0 : (plan.box[1] == 24 ? 1 : 2)};
@@ -595,11 +593,14 @@ struct Impl : CtxBase {
                             goto solved;
                         }
                     }
-                simt:
+                {
+                    const PassPlan plan = mode_pass_plan<T>(CM, N, n, t == 0, num_sms, L.P);
                     // every launched warp takes one ticket past the last bin
-                    ticket_base += (unsigned long long)L.P + (unsigned long long)grid * warps_per_block;
-                    timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, grid, st); });
+                    ticket_base += (unsigned long long)L.P +
+                                   (unsigned long long)plan.grid * plan.warps;
+                    timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, plan, st); });
                     last_path |= 1;
+                }
                     ++launches;
                 solved:
                     if (L.n_single > 0) {

@@ -166,8 +166,8 @@ __device__ __forceinline__ void write_row(const PassArgs<T> &a, int row, const T
 // the newest kLeadRows - 1 groups makes both this step's rows and the indices of the
 // step whose rows are issued next available.
 
-constexpr int kLeadRows = 2;
-constexpr int kLeadIdx = 4;
+constexpr int kLeadRows = 1;
+constexpr int kLeadIdx = 2;
 constexpr int kRowSlots = kLeadRows + 1;
 constexpr int kIdxSlots = kLeadIdx + 1;
 
@@ -644,10 +644,17 @@ __host__ __device__ size_t pass_warp_bytes(int N, int n) {
     return PG::warp_bytes(N - 1, n);
 }
 
+// Warps per block of the mode pass (one block per SM): as many as the registers of the
+// per-lane Gram accumulators allow without spilling.
+template <class T>
+constexpr int pass_max_warps() { return sizeof(T) == 4 ? 12 : 8; }
+
 // NO: number of other modes (N - 1) when specialised, 0 for any N (runtime loops).
 // FIRST: the split's first inner iteration (R-hat refresh) or a later one.
+// One block per SM (the staging rings are small, so most of the SM's shared memory
+// stays L1 cache: the hottest slice rows are served from there).
 template <class T, int CM, int NO, bool FIRST>
-__global__ void __launch_bounds__(kPassThreads, (sizeof(T) == 4 && CM <= 12) ? 4 : 2)
+__global__ void __launch_bounds__(pass_max_warps<T>() * kWarp, 1)
     k_mode_pass(const PassArgs<T> a) {
     using Cons = PassConsumer<T, CM, NO, FIRST>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -841,43 +848,29 @@ auto mode_pass_kernel(int N, bool first) {
     return first ? k_mode_pass<T, CM, 0, true> : k_mode_pass<T, CM, 0, false>;
 }
 
-template <class T, int CM>
-size_t pass_bytes_cm(int N, int n, bool first) {
-    return first ? pass_warp_bytes<T, CM, true>(N, n) : pass_warp_bytes<T, CM, false>(N, n);
+// Plan of a mode-n pass: one block per SM with as many warps as fit (up to
+// pass_max_warps); the shared memory the rings leave is L1 cache.
+template <class T, int CM, bool FIRST>
+PassPlan mode_pass_plan_cm(int N, int n, int num_sms, int P) {
+    constexpr size_t kReserve = 1024;  // static shared memory of the kernel
+    int dev = 0, smem_blk = 0;
+    TFS_CUDA(cudaGetDevice(&dev));
+    TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t ring = pass_warp_bytes<T, CM, FIRST>(N, n);
+    PassPlan plan;
+    plan.warps = (int)std::min<size_t>(pass_max_warps<T>(), ((size_t)smem_blk - kReserve) / ring);
+    if (plan.warps < 1) throw ApiError{TF_EINVAL, "mode pass does not fit in shared memory"};
+    plan.smem = (size_t)plan.warps * ring;
+    plan.grid = std::max(1, std::min(num_sms, (P + plan.warps - 1) / plan.warps));
+    return plan;
 }
 
 template <class T, int CM>
-int pipe_warps(int N) {  // per mode-pass launch the layout differs; use the largest
-    size_t wb = 0;
-    for (int n = 0; n < N; ++n) wb = std::max(wb, pass_bytes_cm<T, CM>(N, n, true));
-    return best_warps_per_block(wb);
-}
-
-template <class T, int CM>
-int mode_pass_grid_cm(int P, int num_sms, int N) {
-    const int wpb = pipe_warps<T, CM>(N);
-    int per_sm = 1 << 30;
-    for (int f = 0; f < 2; ++f) {
-        size_t wb = 0;
-        for (int n = 0; n < N; ++n) wb = std::max(wb, pass_bytes_cm<T, CM>(N, n, f == 1));
-        const size_t smem = wpb * wb;
-        auto kern = mode_pass_kernel<T, CM>(N, f == 1);
-        TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        int b = 0;
-        TFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, wpb * kWarp, smem));
-        per_sm = std::min(per_sm, b);
-    }
-    const int need = (P + wpb - 1) / wpb;
-    return std::max(1, std::min(need, std::max(per_sm, 1) * num_sms));
-}
-
-template <class T, int CM>
-void launch_mode_pass_cm(const PassArgs<T> &a, int grid, cudaStream_t st) {
-    const int wpb = pipe_warps<T, CM>(a.N);
+void launch_mode_pass_cm(const PassArgs<T> &a, const PassPlan &plan, cudaStream_t st) {
     auto kern = mode_pass_kernel<T, CM>(a.N, a.first != 0);
-    const size_t smem = wpb * pass_bytes_cm<T, CM>(a.N, a.n, a.first != 0);
-    kern<<<grid, wpb * kWarp, smem, st>>>(a);
+    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)plan.smem));
+    kern<<<plan.grid, plan.warps * kWarp, plan.smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }
 
@@ -919,11 +912,11 @@ int res_blocks_cm(int P, int N) {
 #define TFS_FOR_EACH_CM(X) X(1) X(2) X(4) X(6) X(8) X(10) X(12) X(16)
 
 template <class T>
-void launch_mode_pass_impl(const PassArgs<T> &a, int CM, int grid, cudaStream_t st) {
+void launch_mode_pass_impl(const PassArgs<T> &a, int CM, const PassPlan &plan, cudaStream_t st) {
     switch (CM) {
 #define TFS_CASE(cm)                             \
     case cm:                                     \
-        launch_mode_pass_cm<T, cm>(a, grid, st); \
+        launch_mode_pass_cm<T, cm>(a, plan, st); \
         return;
         TFS_FOR_EACH_CM(TFS_CASE)
 #undef TFS_CASE
@@ -933,24 +926,12 @@ void launch_mode_pass_impl(const PassArgs<T> &a, int CM, int grid, cudaStream_t 
 }
 
 template <class T>
-int mode_pass_grid_impl(int CM, int P, int num_sms, int N) {
+PassPlan mode_pass_plan_impl(int CM, int N, int n, bool first, int num_sms, int P) {
     switch (CM) {
-#define TFS_CASE(cm) \
-    case cm:         \
-        return mode_pass_grid_cm<T, cm>(P, num_sms, N);
-        TFS_FOR_EACH_CM(TFS_CASE)
-#undef TFS_CASE
-        default:
-            throw ApiError{TF_EINVAL, "no mode-pass instance for this C"};
-    }
-}
-
-template <class T>
-int mode_pass_warps_impl(int CM, int N) {
-    switch (CM) {
-#define TFS_CASE(cm) \
-    case cm:         \
-        return pipe_warps<T, cm>(N);
+#define TFS_CASE(cm)                                                       \
+    case cm:                                                               \
+        return first ? mode_pass_plan_cm<T, cm, true>(N, n, num_sms, P)    \
+                     : mode_pass_plan_cm<T, cm, false>(N, n, num_sms, P);
         TFS_FOR_EACH_CM(TFS_CASE)
 #undef TFS_CASE
         default:

@@ -7,18 +7,13 @@
 namespace tfs {
 
 template <>
-void launch_mode_pass<float>(const PassArgs<float> &a, int CM, int grid, cudaStream_t st) {
-    launch_mode_pass_impl<float>(a, CM, grid, st);
+void launch_mode_pass<float>(const PassArgs<float> &a, int CM, const PassPlan &plan, cudaStream_t st) {
+    launch_mode_pass_impl<float>(a, CM, plan, st);
 }
 
 template <>
-int mode_pass_grid<float>(int CM, int P, int num_sms, int N) {
-    return mode_pass_grid_impl<float>(CM, P, num_sms, N);
-}
-
-template <>
-int mode_pass_warps<float>(int CM, int N) {
-    return mode_pass_warps_impl<float>(CM, N);
+PassPlan mode_pass_plan<float>(int CM, int N, int n, bool first, int num_sms, int P) {
+    return mode_pass_plan_impl<float>(CM, N, n, first, num_sms, P);
 }
 
 template <>

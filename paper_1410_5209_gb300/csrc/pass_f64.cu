@@ -5,18 +5,13 @@
 namespace tfs {
 
 template <>
-void launch_mode_pass<double>(const PassArgs<double> &a, int CM, int grid, cudaStream_t st) {
-    launch_mode_pass_impl<double>(a, CM, grid, st);
+void launch_mode_pass<double>(const PassArgs<double> &a, int CM, const PassPlan &plan, cudaStream_t st) {
+    launch_mode_pass_impl<double>(a, CM, plan, st);
 }
 
 template <>
-int mode_pass_grid<double>(int CM, int P, int num_sms, int N) {
-    return mode_pass_grid_impl<double>(CM, P, num_sms, N);
-}
-
-template <>
-int mode_pass_warps<double>(int CM, int N) {
-    return mode_pass_warps_impl<double>(CM, N);
+PassPlan mode_pass_plan<double>(int CM, int N, int n, bool first, int num_sms, int P) {
+    return mode_pass_plan_impl<double>(CM, N, n, first, num_sms, P);
 }
 
 template <>

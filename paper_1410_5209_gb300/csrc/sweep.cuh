@@ -129,8 +129,15 @@ __host__ __device__ constexpr int slice_stride_elems(int CM, int elem_bytes) {
 }
 inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
 
+// Launch plan of one cp.async mode pass: one block per SM, warps per block.
+struct PassPlan {
+    int warps = 0, grid = 0;
+    size_t smem = 0;
+};
 template <class T>
-void launch_mode_pass(const PassArgs<T> &a, int CM, int grid, cudaStream_t st);
+PassPlan mode_pass_plan(int CM, int N, int n, bool first, int num_sms, int P);
+template <class T>
+void launch_mode_pass(const PassArgs<T> &a, int CM, const PassPlan &plan, cudaStream_t st);
 template <class T>
 void launch_combine(const PassArgs<T> &a, int CM, const SplitRow *rows, int n_rows,
                     cudaStream_t st);
@@ -162,13 +169,6 @@ template <class T>
 size_t foldin_smem_bytes(int K);
 
 inline int pass_blocks(int P) { return (P * kWarp + kPassThreads - 1) / kPassThreads; }
-
-// Blocks of a mode-pass launch (at most one resident wave) for register width CM.
-template <class T>
-int mode_pass_grid(int CM, int P, int num_sms, int N);
-// Warps per block of a mode-pass launch (shared memory decides).
-template <class T>
-int mode_pass_warps(int CM, int N);
 
 // TMA-fed mode pass (float, N = 3, CM <= 10; tma_pass.cuh).  A plan fixes the gather
 // box width per other mode, the rows of each other mode's slice held in the block's

@@ -4,10 +4,10 @@
 // Algorithm 1), different data movement.  One block per SM, W warps, each warp working
 // through bins taken from the ticket counter with a ring of shared-memory slots filled
 // by TMA, one mbarrier per slot (no ordering between slots):
-//   4 steps ahead: one lane issues 1D bulk copies of the step's index windows of both
+//   2 steps ahead: one lane issues 1D bulk copies of the step's index windows of both
 //                  other modes, its residual window and (first step of an item) the own
 //                  slice row;
-//   2 steps ahead: the warp finds the step's distinct slice rows that are not cached
+//   1 step ahead:  the warp finds the step's distinct slice rows that are not cached
 //                  (consecutive entries of a row share their leading other-mode index
 //                  in long runs), lists them, and up to 16 lanes each issue one
 //                  tile::gather4 of 4 listed rows into the step's row slot;
@@ -29,7 +29,7 @@
 
 namespace tfs {
 
-constexpr int kTmaLeadRows = 2, kTmaLeadIdx = 4;
+constexpr int kTmaLeadRows = 1, kTmaLeadIdx = 2;
 constexpr int kTmaRowSlots = kTmaLeadRows + 1, kTmaIdxSlots = kTmaLeadIdx + 1;
 constexpr int kTmaWin = 36;               // window entries: 32 + alignment slack (4)
 constexpr int kTmaMaxWarps = 12;          // warps per block (one block per SM)
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kTmaMaxWarps * kWarp, 1)
         }
         int is = 0, rs = 0;
         while ((st[0].flags & 1) && !timed_out) {
-            {   // rows of step +2 (its indices are 2 steps old), indices of step +4
+            {   // rows of step +kTmaLeadRows, indices of step +kTmaLeadIdx
                 const Step &sb = st[kTmaLeadRows];
                 const int ib = (is + kTmaLeadRows) % kTmaIdxSlots;
                 const int rb = (rs + kTmaLeadRows) % kTmaRowSlots;
