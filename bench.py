@@ -174,6 +174,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
+    ap.add_argument("--foldin-requests", type=int, default=200)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -275,6 +276,24 @@ def main():
                               if sweep_ms else None},
            "kernels": kernel_breakdown, "gpu_launches": launches_per_step * args.steps,
            "clocks": clocks, "loss": loss, "train_rmse": rmse}
+    # fold-in latency (Eq. 2 row solve for a new mode-1 slice) against the factors the
+    # timed sweeps left: one synchronous tf_foldin per request, submit to result on host
+    if args.foldin_requests > 0:
+        reqs = synth.foldin_requests(p, args.foldin_requests + 10, args.seed + 17 + rank)
+        lat = []
+        for q, (other, xv) in enumerate(reqs):
+            t0 = time.perf_counter()
+            f.foldin(0, other, xv, lam)
+            if q >= 10:   # the first ten are a warm-up
+                lat.append(time.perf_counter() - t0)
+        lat_ms = np.sort(np.array(lat)) * 1e3
+        ms_sizes = [r[0].shape[0] for r in reqs[10:]]
+        out["foldin"] = {"p50_ms": float(np.percentile(lat_ms, 50)),
+                         "p99_ms": float(np.percentile(lat_ms, 99)),
+                         "requests": len(lat), "req_per_s": len(lat) / float(lat_ms.sum() / 1e3),
+                         "entries_min": int(min(ms_sizes)), "entries_max": int(max(ms_sizes)),
+                         "K": K, "what": "sequential tf_foldin calls: host request -> device "
+                                         "Gram + Cholesky -> host row"}
     f.close()
     del f
 

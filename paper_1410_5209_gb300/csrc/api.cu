@@ -462,7 +462,8 @@ struct Impl : CtxBase {
         if (T_in < 1) throw ApiError{TF_EINVAL, "T_in must be >= 1"};
         if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
         const int CM = pick_cm(C);
-        if (CM == 0) throw ApiError{TF_EINVAL, "C > 16 is not supported by this build"};
+        if (CM == 0) throw ApiError{TF_EINVAL, "C >= 128 is not supported by this build"};
+        const bool wide = CM > 16;
         int64_t launches0 = launches;
         if (dirty) {
             rebuild_residuals();
@@ -571,6 +572,27 @@ struct Impl : CtxBase {
                     a.stat = stat.p;
                     a.ticket = ticket.p;
                     a.ticket_base = ticket_base;
+                    if (wide) {
+                        const int wgrid = pass_wide_grid<T>(num_sms, L.P);
+                        // every block takes one ticket past the last bin
+                        ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
+                        timed(TF_KIND_MODE_PASS,
+                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, st); });
+                        ++launches;
+                        if (L.n_single > 0) {
+                            timed(TF_KIND_SOLVE, [&] {
+                                launch_solve_wide<T>(a, L.single.p, L.n_single, CM, W, st);
+                            });
+                            ++launches;
+                        }
+                        if (L.n_split > 0) {
+                            timed(TF_KIND_COMBINE, [&] {
+                                launch_solve_wide<T>(a, L.split.p, L.n_split, CM, W, st);
+                            });
+                            ++launches;
+                        }
+                        continue;
+                    }
                     if constexpr (sizeof(T) == 4) {
                         if (use_tma) {
                             const bool before[2] = {L.omode[0] < n, L.omode[1] < n};

@@ -979,6 +979,10 @@ void launch_res_impl(const ResArgs<T> &a, int CM, cudaStream_t st) {
         TFS_FOR_EACH_CM(TFS_CASE)
 #undef TFS_CASE
         default:
+            if (CM > 16) {
+                launch_res_wide<T>(a, slice_stride_elems(CM, (int)sizeof(T)), st);
+                return;
+            }
             throw ApiError{TF_EINVAL, "no residual instance for this C"};
     }
 }
@@ -992,6 +996,7 @@ int res_blocks_impl(int CM, int P, int N) {
         TFS_FOR_EACH_CM(TFS_CASE)
 #undef TFS_CASE
         default:
+            if (CM > 16) return res_wide_blocks(P);
             throw ApiError{TF_EINVAL, "no residual instance for this C"};
     }
 }

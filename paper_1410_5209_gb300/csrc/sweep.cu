@@ -12,6 +12,7 @@ int pick_cm(int C) {
     static const int cms[] = {1, 2, 4, 6, 8, 10, 12, 16};
     for (int cm : cms)
         if (C <= cm) return cm;
+    if (wide_tile_width(C) > 0) return (C + 3) / 4 * 4;
     return 0;
 }
 

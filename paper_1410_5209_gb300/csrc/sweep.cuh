@@ -113,7 +113,8 @@ constexpr int kPassThreads = 128;
 constexpr int kCombineThreads = 512;
 constexpr int kMaxCSimt = 16;
 
-int pick_cm(int C);  // smallest instantiated register width >= C (0 if none)
+int pick_cm(int C);  // smallest instantiated register width >= C (0 if none); C > 16
+                     // takes the wide path (wide.cu) with CM = C rounded up to 4
 
 __host__ __device__ constexpr int next_pow2(int v) {
     int p = 1;
@@ -125,9 +126,24 @@ __host__ __device__ constexpr int next_pow2(int v) {
 // elements, padded to a power-of-two number of 16-byte vectors (so that a fixed group
 // of lanes can move one row with one vector each).
 __host__ __device__ constexpr int slice_stride_elems(int CM, int elem_bytes) {
-    return (16 / elem_bytes) * next_pow2((3 * CM + 16 / elem_bytes - 1) / (16 / elem_bytes));
+    return CM <= 16 ? (16 / elem_bytes) * next_pow2((3 * CM + 16 / elem_bytes - 1) / (16 / elem_bytes))
+                    : (16 / elem_bytes) * ((3 * CM + 16 / elem_bytes - 1) / (16 / elem_bytes));
 }
 inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
+
+// Wide column subsets, 16 < C < 128 (wide.cu): block-per-bin mode pass with a tiled
+// Gram update, block-per-row Cholesky solves, warp-per-bin residual reductions.
+int wide_tile_width(int C);
+template <class T>
+int pass_wide_grid(int num_sms, int P);
+template <class T>
+void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st);
+template <class T>
+void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,
+                       cudaStream_t st);
+int res_wide_blocks(int P);
+template <class T>
+void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st);
 
 // Launch plan of one cp.async mode pass: one block per SM, warps per block.
 struct PassPlan {

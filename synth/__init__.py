@@ -258,6 +258,48 @@ def skewed_3way(seed=2, nnz=100_000_000, dims=(100_000, 100_000, 1_000), K=100,
                         noise_std=0.1, dtype=torch.float32, device=device)
 
 
+def foldin_requests(p, count, seed, mode=0, m_min=10, m_max=10_000, noise_std=0.1,
+                    zipf_s=1.1, modes=("zipf", "zipf", "uniform")):
+    """Fold-in requests against a problem's ground truth: each a new slice of `mode`
+    with m log-uniform in [m_min, m_max] distinct entries whose other-mode indices are
+    drawn like the tensor's (Zipf / uniform per mode), values from a fresh ground-truth
+    row of the same law plus noise.  Returns [(other [m][N-1] int32, x [m])] on the host."""
+    N = p.N
+    rank = p.truth[0].shape[1]
+    std = float(rank) ** (-1.0 / (2 * N))
+    others = [l for l in range(N) if l != mode]
+    samplers = {l: Zipf(int(p.dims[l]), zipf_s, seed, 700 + l) for l in others
+                if modes[l] == "zipf"}
+    truth = [t.to("cpu", torch.float64) for t in p.truth]
+    u = uniform01(seed, 710, 0, count)
+    ms = torch.exp(math.log(m_min) + u * (math.log(m_max) - math.log(m_min))).long()
+    out = []
+    base = 0
+    for q in range(count):
+        m = int(ms[q])
+        row = normal(seed, 720, q * rank, rank, std)
+        cols = []
+        for l in others:
+            n_draw = 4 * m + 64
+            if l in samplers:
+                cols.append(samplers[l].sample(uniform01(seed, 730 + l, base, n_draw)))
+            else:
+                cols.append(uniform_int(seed, 730 + l, base, n_draw, int(p.dims[l])))
+        base += 4 * m + 64
+        c = torch.stack(cols, 1)
+        key = c[:, 0].clone()
+        for k in range(1, c.shape[1]):
+            key = key * int(p.dims[others[k]]) + c[:, k]
+        _, first = np.unique(key.numpy(), return_index=True)
+        c = c[torch.from_numpy(np.sort(first))[:m]]
+        val = row.clone().expand(c.shape[0], rank).clone()
+        for k, l in enumerate(others):
+            val *= truth[l][c[:, k]]
+        x = val.sum(1) + normal(seed, 740, q * m_max, c.shape[0], noise_std)
+        out.append((c.to(torch.int32).numpy(), x.numpy()))
+    return out
+
+
 def small(seed, dims, nnz, rank, K, noise_std=0.1, modes=None, dtype=torch.float64,
           device="cpu"):
     """Small tensors for tests (any shape)."""

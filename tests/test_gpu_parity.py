@@ -409,3 +409,53 @@ def test_skewed_full_size_sampled_rows():
     model = (Af[0][c[:, 0]] * Af[1][c[:, 1]] * Af[2][c[:, 2]]).sum(1)
     x = p.x[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
     assert np.max(np.abs(r[idx] - (x - model))) <= 1e-4 * np.max(np.abs(x))
+
+
+# --------------------------------------------------------------------------- wide C
+
+
+@pytest.mark.parametrize("C,K,T_in,weighted", [(20, 40, 1, False), (33, 40, 2, False),
+                                                (40, 40, 1, True), (17, 50, 1, False),
+                                                (70, 70, 1, False)])
+def test_wide_subsets_match_oracle_fp64(C, K, T_in, weighted):
+    """C > 16 takes the tiled wide path (block Gram tiles, shared-memory Cholesky); C = K
+    is the ALS row update of Eq. (2).  Ragged last split when C does not divide K."""
+    p = synth.small(60 + C, (301, 157, 97), 12_000, 4, K)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.3, T_in, order, weighted=weighted)
+        oracle.sals_sweep(t, A, r, C, 0.3, T_in, order, weighted=weighted)
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    assert rel(f.residual(), r) < 1e-9
+    L, _ = f.loss(0.3, weighted=weighted)
+    Lo, _ = oracle.loss(t, r, A, 0.3, weighted=weighted)
+    assert abs(L - Lo) <= 1e-9 * Lo
+
+
+def test_wide_subsets_fp32_rmse_and_switching():
+    """FP32 wide path: training RMSE within 1e-3 of the FP64 oracle, also when C changes
+    between narrow and wide from one sweep to the next (the copies' R-hat is flushed)."""
+    p = synth.small(70, (400, 300, 60), 40_000, 5, 48)
+    f, t, A = make(p, tf.F32)
+    r = oracle.residual(t, A)
+    for s, C in enumerate((24, 8, 48, 30)):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.5, 1, order)
+        oracle.sals_sweep(t, A, r, C, 0.5, 1, order)
+    _, rmse = f.loss(0.5)
+    _, rmseo = oracle.loss(t, r, A, 0.5)
+    assert abs(rmse - rmseo) <= 1e-3 * rmseo
+
+
+def test_wide_singular_rows_left_unchanged():
+    p = synth.small(71, (500, 40, 30), 1_500, 2, 20)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    bad_o = oracle.sals_sweep(t, A, r, 20, 0.0, 1, np.arange(20))
+    f.sweep(20, 0.0, 1, np.arange(20, dtype=np.int32))
+    assert f.counters()["singular_rows"] == bad_o > 0
+    for n in range(3):
+        assert rel(f.factors(n), A[n]) < 1e-8
