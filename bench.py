@@ -32,12 +32,12 @@ WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=
                 K=100, C=10, T_in=1, lam=0.1, rank_truth=50, zipf=1.1)
 
 # DRAM traffic (read + write) of one mode-pass launch from the ncu capture summarised in
-# profiles/k_mode_pass_tma_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
+# profiles/k_mode_pass_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
 # 1e8-entry launch), and the hash of the kernel sources it was taken with; the bench
 # reports traffic as null once the sources differ or the entry count is not 1e8.
-NCU_TRAFFIC = 1.852e9
+NCU_TRAFFIC = 1.807e9
 NCU_TRAFFIC_NNZ = 100_000_000
-NCU_SOURCE_HASH = "91b1500e293e1634"
+NCU_SOURCE_HASH = "618fa14e004aac14"
 
 
 def kernel_source_hash():

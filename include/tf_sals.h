@@ -120,8 +120,10 @@ tf_status tf_get_factors(tf_ctx *ctx, int n, void *host_A);
  * The last split holds K mod C columns when C does not divide K.
  * Column order: a seeded permutation per sweep for C > 1 (chosen without replacement,
  * Algorithm 1), the identity for C = 1 (CDTF keeps a fixed order, Section 3.1).
- *   C in 1..K (C <= 16 on the SIMT path, larger C on the tiled path), lambda >= 0
- *   (double; converted to the context dtype), T_in >= 1.  Asynchronous: returns once the work is queued on the stream.
+ *   C in 1..min(K, 127) (C <= 16: per-lane register Gram; 16 < C < 128: block-tiled
+ *   Gram and shared-memory Cholesky), lambda >= 0 (double; converted to the context
+ *   dtype), T_in >= 1.  C = K is the ALS row update of Eq. (2).  Asynchronous: returns
+ *   once the work is queued on the stream.
  * A row whose B + lambda I has a non-positive Cholesky pivot (e.g. an empty row with
  * lambda = 0) is left unchanged and counted (tf_get_counters). */
 tf_status tf_sals_sweep(tf_ctx *ctx, int C, double lambda, int T_in);

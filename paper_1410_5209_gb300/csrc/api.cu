@@ -96,7 +96,7 @@ struct Impl : CtxBase {
     Buf<double> red;               // reduction scratch
     Buf<int64_t> d_dims;
     Buf<int32_t> f_other;          // fold-in scratch
-    Buf<T> f_x, f_out;
+    Buf<T> f_x, f_out, f_part;
     int32_t *h_order = nullptr;    // pinned staging of the column order
     cudaEvent_t order_ev = nullptr;
     bool order_pending = false;
@@ -880,13 +880,20 @@ struct Impl : CtxBase {
         a.lambda = (T)lambda;
         a.out = f_out.p;
         a.stat = stat.p;
-        launch_foldin<T>(a, st);
+        const int fb = foldin_blocks(K, m, num_sms);
+        if (fb > 0) {
+            f_part.ensure(foldin_part_elems(K, fb));
+            a.part = f_part.p;
+            launch_foldin_tiled<T>(a, fb, st);
+        } else {
+            launch_foldin<T>(a, st);
+        }
         DeviceStatus s = read_status();
-        const int fb = s.bits & (kStatFoldRange | kStatFoldPivot);
-        if (fb) {
+        const int fbits = s.bits & (kStatFoldRange | kStatFoldPivot);
+        if (fbits) {
             TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
             TFS_CUDA(cudaStreamSynchronize(st));
-            if (fb & kStatFoldRange) throw ApiError{TF_ERANGE, "fold-in index out of range"};
+            if (fbits & kStatFoldRange) throw ApiError{TF_ERANGE, "fold-in index out of range"};
             throw ApiError{TF_EINVAL, "fold-in system is not positive definite"};
         }
         TFS_CUDA(cudaMemcpyAsync(out, f_out.p, K * sizeof(T), cudaMemcpyDeviceToHost, st));

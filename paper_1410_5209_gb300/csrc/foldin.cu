@@ -7,6 +7,9 @@
 // entries of the lower triangle of B (kept in shared memory) and of c.  The K x K
 // system is factored in place by a right-looking Cholesky (one column per step), and
 // warp 0 does the two triangular solves.
+#include <algorithm>
+
+#include "dense_solve.cuh"
 #include "sweep.cuh"
 
 namespace tfs {
@@ -118,7 +121,143 @@ __global__ void __launch_bounds__(kFoldThreads) k_foldin(const FoldArgs<T> a) {
         for (int q = tid; q < K; q += blockDim.x) a.out[q] = cv[q];
 }
 
+// Tiled fold-in for K < 128 (several blocks per request): block b takes entries
+// [b E, (b + 1) E); tiles of 32 entries build H' = [H | x] in shared memory (8 threads
+// per entry, columns strided by 8, one round of independent row loads), and a 16 x 16
+// grid of register tiles accumulates the lower triangle of H'^T H' (B and, in row K,
+// c).  Each block writes its partial; k_fold_solve sums them in block order and solves
+// with one warp.
+constexpr int kFoldTile = 32;
+constexpr int kFoldGramThreads = 256;
+
+template <class T, int CW>
+__global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T> a, int64_t E) {
+    constexpr int R = CW / 16, HS = CW + 4;
+    __shared__ __align__(16) T H[kFoldTile * HS];
+    __shared__ int bad;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int K = a.K;
+    const bool active = ty >= tx;
+    if (tid == 0) bad = 0;
+    T acc[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = T(0);
+    const int64_t b0 = (int64_t)blockIdx.x * E;
+    const int64_t b1 = b0 + E < a.m ? b0 + E : a.m;
+    for (int64_t e0 = b0; e0 < b1; e0 += kFoldTile) {
+        const int ne = (int)(b1 - e0 < kFoldTile ? b1 - e0 : kFoldTile);
+        __syncthreads();
+        {
+            const int e = tid >> 3, g = tid & 7;
+            const bool valid = e < ne;
+            T *h = H + e * HS;
+            const T *rows[kMaxModes];
+            int t = 0;
+            bool ok = valid;
+            for (int l = 0; l < a.N; ++l) {
+                if (l == a.mode) continue;
+                const int32_t idx = valid ? a.other[(e0 + e) * (a.N - 1) + t] : 0;
+                const bool in = idx >= 0 && idx < a.I[l];
+                ok = ok && in;
+                rows[t++] = a.A[l] + (int64_t)(in ? idx : 0) * K;
+            }
+            if (valid && !ok) bad = 1;
+            for (int c = g; c < CW; c += 8) {
+                T hv = T(0);
+                if (ok && c < K) {
+                    hv = T(1);
+                    for (int u = 0; u < a.N - 1; ++u) hv *= rows[u][c];
+                }
+                h[c] = hv;
+            }
+            __syncwarp();
+            if (g == 0) h[K] = ok ? a.x[e0 + e] : T(0);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int e = 0; e < ne; ++e) {
+                const T *h = H + e * HS;
+                T x[R], y[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) x[i] = h[ty * R + i];
+#pragma unroll
+                for (int j = 0; j < R; ++j) y[j] = h[tx * R + j];
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+#pragma unroll
+                    for (int j = 0; j < R; ++j) acc[i][j] += x[i] * y[j];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && bad) atomicOr(&a.stat->bits, kStatFoldRange);
+    const int NT = K * (K + 1) / 2;
+    T *p = a.part + (int64_t)blockIdx.x * (NT + K);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int r = ty * R + i, cc = tx * R + j;
+                if (r < K && cc <= r) p[r * (r + 1) / 2 + cc] = acc[i][j];
+                if (r == K && cc < K) p[NT + cc] = acc[i][j];
+            }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32) k_fold_solve(const FoldArgs<T> a, int blocks) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K = a.K, lane = threadIdx.x;
+    const int NT = K * (K + 1) / 2, NB = NT + K;
+    T *P = reinterpret_cast<T *>(smem_raw);
+    T *cv = P + NT;
+    for (int q = lane; q < NB; q += 32) {
+        T s = T(0);
+        for (int b = 0; b < blocks; ++b) s += a.part[(int64_t)b * NB + q];
+        P[q] = s;  // cv follows P: q >= NT lands in cv[q - NT]
+    }
+    __syncwarp();
+    const bool ok = warp_chol_solve<T>(P, cv, K, a.lambda, lane);
+    if (!ok) {
+        if (lane == 0) atomicOr(&a.stat->bits, kStatFoldPivot);
+        return;
+    }
+    for (int q = lane; q < K; q += 32) a.out[q] = cv[q];
+}
+
 }  // namespace
+
+int foldin_blocks(int K, int64_t m, int num_sms) {
+    if (K + 1 > 128 || m <= 0) return 0;
+    const int64_t b = (m + 255) / 256;
+    return (int)std::min<int64_t>(b, 2 * (int64_t)num_sms);
+}
+
+size_t foldin_part_elems(int K, int blocks) {
+    return (size_t)std::max(blocks, 1) * ((size_t)K * (K + 1) / 2 + K);
+}
+
+template <class T>
+void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, cudaStream_t st) {
+    const int64_t E = (a.m + blocks - 1) / blocks;
+    const int cw = a.K + 1 <= 32 ? 32 : (a.K + 1 <= 64 ? 64 : 128);
+    if (cw == 32)
+        k_fold_gram<T, 32><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
+    else if (cw == 64)
+        k_fold_gram<T, 64><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
+    else
+        k_fold_gram<T, 128><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
+    TFS_CUDA(cudaGetLastError());
+    const size_t smem = sizeof(T) * ((size_t)a.K * (a.K + 1) / 2 + a.K);
+    TFS_CUDA(cudaFuncSetAttribute(k_fold_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    k_fold_solve<T><<<1, 32, smem, st>>>(a, blocks);
+    TFS_CUDA(cudaGetLastError());
+}
 
 template <class T>
 size_t foldin_smem_bytes(int K) {
@@ -138,5 +277,7 @@ template size_t foldin_smem_bytes<float>(int);
 template size_t foldin_smem_bytes<double>(int);
 template void launch_foldin<float>(const FoldArgs<float> &, cudaStream_t);
 template void launch_foldin<double>(const FoldArgs<double> &, cudaStream_t);
+template void launch_foldin_tiled<float>(const FoldArgs<float> &, int, cudaStream_t);
+template void launch_foldin_tiled<double>(const FoldArgs<double> &, int, cudaStream_t);
 
 }  // namespace tfs

@@ -107,6 +107,7 @@ struct FoldArgs {
     T lambda;
     T *out;
     DeviceStatus *stat;
+    T *part;      // [blocks][K (K + 1) / 2 + K] partial Gram / rhs of the tiled fold-in
 };
 
 constexpr int kPassThreads = 128;
@@ -181,6 +182,12 @@ void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, 
                         cudaStream_t st);
 template <class T>
 void launch_foldin(const FoldArgs<T> &a, cudaStream_t st);
+// Blocks of the tiled fold-in for a request of m entries (0: the one-block kernel),
+// and its partial buffer length in elements.
+int foldin_blocks(int K, int64_t m, int num_sms);
+size_t foldin_part_elems(int K, int blocks);
+template <class T>
+void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, cudaStream_t st);
 template <class T>
 size_t foldin_smem_bytes(int K);
 

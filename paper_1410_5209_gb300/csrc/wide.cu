@@ -10,11 +10,12 @@
 // end of an item the lower triangle of B and c go to the item's partial slot, in the
 // packed layout the narrow kernels use.
 //
-// Row solve: one block per row sums the row's slots in slot order, factors B + lambda I
+// Row solve: one warp per row sums the row's slots in slot order, factors B + lambda I
 // (right-looking Cholesky in shared memory, Section 3.1) and writes the row.  A
 // non-positive pivot leaves the row unchanged and is counted.
 #include <algorithm>
 
+#include "dense_solve.cuh"
 #include "sweep.cuh"
 
 namespace tfs {
@@ -22,7 +23,7 @@ namespace {
 
 constexpr int kWideThreads = 256;
 constexpr int kWideTile = 32;        // entries per tile
-constexpr int kSolveThreads = 128;
+constexpr int kSolveWarps = 4;        // rows per solve block
 
 template <class T>
 __device__ __forceinline__ T wsum(T v) {
@@ -39,6 +40,8 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *H = reinterpret_cast<T *>(smem_raw);           // [kWideTile][HS]
     T *own = H + kWideTile * HS;                       // prev | old of the own row (2 CM)
+    T *s_res = own + 2 * CM;                           // [kWideTile]
+    int32_t *s_idx = reinterpret_cast<int32_t *>(s_res + kWideTile);  // [no][kWideTile]
     __shared__ unsigned long long s_tk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ty = tid >> 4, tx = tid & 15;
@@ -65,22 +68,30 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
             for (int64_t j0 = item.begin; j0 < item.begin + item.len; j0 += kWideTile) {
                 const int64_t left = item.begin + item.len - j0;
                 const int ne = left < kWideTile ? (int)left : kWideTile;
-                __syncthreads();  // H and own are ready to be (over)written / read
-                for (int e = warp; e < kWideTile; e += kWideThreads / 32) {
-                    T *h = H + e * HS;
-                    if (e >= ne) {
-                        for (int c = lane; c < CW; c += 32) h[c] = T(0);
-                        continue;
+                __syncthreads();  // H, the tile's indices and own are free to be rewritten
+                for (int q = tid; q < kWideTile * (no + 1); q += kWideThreads) {
+                    const int t = q / kWideTile, e = q - t * kWideTile;
+                    if (e < ne) {
+                        if (t < no)
+                            s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
+                        else
+                            s_res[e] = a.res[j0 + e];
                     }
-                    const int64_t jj = j0 + e;
+                }
+                __syncthreads();
+                {   // 8 lanes per entry, columns g, g + 8, ...: one round of independent loads
+                    const int e = tid >> 3, g = tid & 7;
+                    const bool valid = e < ne;
+                    T *h = H + e * HS;
                     const T *rows[kMaxModes - 1];
-                    for (int t = 0; t < no; ++t) rows[t] = a.Zo[t] + (int64_t)a.oidx[t][jj] * W;
+                    for (int t = 0; t < no; ++t)
+                        rows[t] = a.Zo[t] + (int64_t)(valid ? s_idx[t * kWideTile + e] : 0) * W;
                     T pp = T(0), po = T(0);
                     // columns of S (< C <= CW - 1) and of the previous subset Q (< Cq <= CM)
                     const int cmax = CW > CM ? CW : CM;
-                    for (int c = lane; c < cmax; c += 32) {
+                    for (int c = g; c < cmax; c += 8) {
                         T hv = T(0);
-                        if (c < C) {
+                        if (valid && c < C) {
                             hv = T(1);
                             for (int t = 0; t < no; ++t) hv *= rows[t][c];
                             if (FIRST) {
@@ -89,22 +100,27 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
                                 po += o;
                             }
                         }
-                        if (FIRST && c < Cq) {
+                        if (FIRST && valid && c < Cq) {
                             T p = own[c];
                             for (int t = 0; t < no; ++t) p *= rows[t][CM + c];
                             pp += p;
                         }
                         if (c < CW) h[c] = hv;
                     }
-                    T v = a.res[jj];
-                    if (FIRST) {
-                        pp = wsum(pp);
-                        po = wsum(po);
-                        v = v - pp + po;
-                        if (lane == 0) a.res[jj] = v;
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) {
+                        pp += __shfl_xor_sync(0xFFFFFFFFu, pp, o);
+                        po += __shfl_xor_sync(0xFFFFFFFFu, po, o);
                     }
                     __syncwarp();
-                    if (lane == 0) h[C] = v;
+                    if (valid && g == 0) {
+                        T v = s_res[e];
+                        if (FIRST) {
+                            v = v - pp + po;
+                            a.res[j0 + e] = v;
+                        }
+                        h[C] = v;
+                    }
                 }
                 __syncthreads();
                 if (active) {
@@ -143,82 +159,43 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
     }
 }
 
-// One block per row: (B + lambda I) x = c for the C x C system summed over the row's
-// slots; writes x to A_n[row][S[c]] and to the cur region of the own slice row.
+// One warp per row (kSolveWarps rows per block): sums the row's slots in slot order
+// into a packed lower triangle in shared memory, solves (B + lambda I) x = c and writes
+// x to A_n[row][S[c]] and to the cur region of the own slice row.
 template <class T>
-__global__ void __launch_bounds__(kSolveThreads) k_solve_wide(const PassArgs<T> a,
-                                                              const SplitRow *rows, int CM, int W) {
+__global__ void __launch_bounds__(kSolveWarps * 32) k_solve_wide(const PassArgs<T> a,
+                                                                 const SplitRow *rows, int n_rows,
+                                                                 int CM, int W) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int C = a.C;
-    T *B = reinterpret_cast<T *>(smem_raw);  // C x C, lower triangle used
-    T *cv = B + (size_t)C * C;
-    __shared__ int bad;
-    const SplitRow sr = rows[blockIdx.x];
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * (int)(blockDim.x >> 5) + warp;
+    if (r >= n_rows) return;
     const int NT = CM * (CM + 1) / 2, NB = NT + CM;
-    if (tid == 0) bad = 0;
-    for (int q = tid; q < C * C; q += blockDim.x) {
-        const int i = q / C, j = q - i * C;
-        if (j > i) continue;
+    const size_t per_warp = (size_t)C * (C + 1) / 2 + C;
+    T *P = reinterpret_cast<T *>(smem_raw) + warp * per_warp;
+    T *cv = P + (size_t)C * (C + 1) / 2;
+    const SplitRow sr = rows[r];
+    // the first C rows of the packed CM-triangle are the packed C-triangle
+    for (int q = lane; q < C * (C + 1) / 2; q += 32) {
         T s = T(0);
-        for (int k = 0; k < sr.n_slots; ++k)
-            s += a.partials[(int64_t)(sr.first_slot + k) * NB + i * (i + 1) / 2 + j];
-        B[q] = s;
+        for (int k = 0; k < sr.n_slots; ++k) s += a.partials[(int64_t)(sr.first_slot + k) * NB + q];
+        P[q] = s;
     }
-    for (int q = tid; q < C; q += blockDim.x) {
+    for (int q = lane; q < C; q += 32) {
         T s = T(0);
         for (int k = 0; k < sr.n_slots; ++k) s += a.partials[(int64_t)(sr.first_slot + k) * NB + NT + q];
         cv[q] = s;
     }
-    __syncthreads();
+    __syncwarp();
     const T lam = a.weighted ? a.lambda * (T)sr.len : a.lambda;
-    for (int q = tid; q < C; q += blockDim.x) B[q * C + q] += lam;
-    for (int j = 0; j < C; ++j) {
-        __syncthreads();
-        if (tid == 0) {
-            T d = B[j * C + j];
-            if (!(d > T(0))) {
-                bad = 1;
-                d = T(1);
-            }
-            B[j * C + j] = sqrt(d);
-        }
-        __syncthreads();
-        const T ljj = B[j * C + j];
-        for (int i = j + 1 + tid; i < C; i += blockDim.x) B[i * C + j] /= ljj;
-        __syncthreads();
-        const int rem = C - j - 1;
-        for (int q = tid; q < rem * rem; q += blockDim.x) {
-            const int i = j + 1 + q / rem, k = j + 1 + q % rem;
-            if (k <= i) B[i * C + k] -= B[i * C + j] * B[k * C + j];
-        }
-    }
-    __syncthreads();
-    if (tid < 32) {
-        const int lane = tid;
-        for (int i = 0; i < C; ++i) {  // L y = c
-            T s = T(0);
-            for (int k = lane; k < i; k += 32) s += B[i * C + k] * cv[k];
-            s = wsum(s);
-            if (lane == 0) cv[i] = (cv[i] - s) / B[i * C + i];
-            __syncwarp();
-        }
-        for (int i = C - 1; i >= 0; --i) {  // L^T x = y
-            T s = T(0);
-            for (int k = i + 1 + lane; k < C; k += 32) s += B[k * C + i] * cv[k];
-            s = wsum(s);
-            if (lane == 0) cv[i] = (cv[i] - s) / B[i * C + i];
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    if (bad) {
-        if (tid == 0) atomicAdd(&a.stat->singular_rows, 1ull);
+    if (!warp_chol_solve<T>(P, cv, C, lam, lane)) {
+        if (lane == 0) atomicAdd(&a.stat->singular_rows, 1ull);
         return;
     }
     T *z = a.Zn + (int64_t)a.rank_n[sr.row] * W;
     T *Ar = a.A_n + (int64_t)sr.row * a.K;
-    for (int q = tid; q < C; q += blockDim.x) {
+    for (int q = lane; q < C; q += 32) {
         z[q] = cv[q];
         Ar[a.S[q]] = cv[q];
     }
@@ -270,7 +247,8 @@ __global__ void __launch_bounds__(kWideThreads) k_res_wide(const ResArgs<T> a, i
 
 template <class T, int CW>
 void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st) {
-    const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM);
+    const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM + kWideTile) +
+                        sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
     auto kern = a.first ? k_pass_wide<T, CW, true> : k_pass_wide<T, CW, false>;
     TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
@@ -307,10 +285,15 @@ template <class T>
 void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,
                        cudaStream_t st) {
     if (n_rows <= 0) return;
-    const size_t smem = sizeof(T) * ((size_t)a.C * a.C + a.C);
+    int dev = 0, smem_blk = 0;
+    TFS_CUDA(cudaGetDevice(&dev));
+    TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t per_warp = sizeof(T) * ((size_t)a.C * (a.C + 1) / 2 + a.C);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kSolveWarps, smem_blk / per_warp));
+    const size_t smem = per_warp * wpb;
     TFS_CUDA(cudaFuncSetAttribute(k_solve_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    k_solve_wide<T><<<n_rows, kSolveThreads, smem, st>>>(a, rows, CM, W);
+    k_solve_wide<T><<<(n_rows + wpb - 1) / wpb, wpb * 32, smem, st>>>(a, rows, n_rows, CM, W);
     TFS_CUDA(cudaGetLastError());
 }
 

@@ -352,6 +352,29 @@ def test_foldin_matches_oracle(dtype, tol):
         assert rel(got.astype(np.float64), ref) < tol or np.linalg.norm(ref) < 1e-12
 
 
+@pytest.mark.parametrize("dtype,tol", [(tf.F64, 1e-9), (tf.F32, 1e-4)])
+def test_foldin_tiled_large_requests(dtype, tol):
+    """K = 100 and requests of up to 20,000 entries: the fold-in is split over many
+    blocks whose partial Gram matrices are summed in block order before the solve."""
+    p = synth.small(43, (60, 2000, 300), 60_000, 6, 100)
+    f, t, A = make(p, dtype)
+    rng = np.random.default_rng(2)
+    for m in (1, 255, 257, 5_000, 20_000):
+        other = np.stack([rng.integers(0, 2000, m), rng.integers(0, 300, m)], 1).astype(np.int32)
+        x = rng.standard_normal(m)
+        if dtype == tf.F32:
+            x = x.astype(np.float32).astype(np.float64)
+        got = f.foldin(0, other, x, 0.7)
+        ref, st = oracle.foldin(A, 0, other, x, 0.7)
+        assert st == 0
+        assert rel(got.astype(np.float64), ref) < tol
+    other = np.stack([rng.integers(0, 2000, 5000), rng.integers(0, 300, 5000)], 1).astype(np.int32)
+    other[4321, 1] = 300
+    with pytest.raises(tf.TFError) as e:
+        f.foldin(0, other, np.ones(5000), 0.7)
+    assert e.value.status == tf.ERANGE
+
+
 def test_foldin_rejects_bad_index():
     p = synth.small(41, (20, 30, 40), 2_000, 2, 4)
     f, _, _ = make(p, tf.F32)
