@@ -251,8 +251,9 @@ def main():
                               and nnz == NCU_TRAFFIC_NNZ) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
-                "kernel": {1: "k_mode_pass", 2: "k_mode_pass_tma",
-                           3: "k_mode_pass + k_mode_pass_tma"}.get(cnt["pass_path"], "?"),
+                "kernel": " + ".join(n for b, n in ((1, "k_mode_pass"), (2, "k_mode_pass_tma"),
+                                                   (4, "k_pass_wide_tc"))
+                                     if cnt["pass_path"] & b) or "?",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": mp_avg_ms}

@@ -201,19 +201,22 @@ tf_status tf_get_residual(tf_ctx *ctx, void *host_r);
  * counters[1] = sweeps run, counters[2] = kernels launched by the last sweep,
  * counters[3] = work items of all modes, counters[4] = rows split across bins,
  * counters[5] = bins P of the schedule, counters[6] = kernels launched by the last
- * tf_loss, counters[7] = mode-pass data paths the last sweep used (bit 0: cp.async
- * SIMT pass, bit 1: TMA gather pass; 0 = no sweep yet). */
+ * tf_loss, counters[7] = mode-pass data paths the last sweep used (bit 0: SIMT pass,
+ * bit 1: TMA gather pass, bit 2: tensor-core Gram pass of wide subsets; 0 = no sweep). */
 tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
 
 /* Re-plans the row schedule of every mode (policy, P bins; P = 0 picks the default
  * for this GPU).  Results do not depend on the schedule. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
-/* Data path of the mode pass: 0 = automatic (the cp.async SIMT pass, whose slice-row
- * gathers are served by L1 for hot rows), 1 = the cp.async pass, 2 = the TMA
- * tile::gather4 pass with its shared-memory row cache (float contexts with N = 3 and
- * C <= 10; TF_EINVAL from the next sweep where it does not apply).  Both paths give
- * bit-identical results. */
+/* Data path of the mode pass: 0 = automatic (C <= 16: the cp.async SIMT pass, whose
+ * slice-row gathers are served by L1 for hot rows; 16 < C < 128: for float contexts the
+ * Gram on the tensor cores (tcgen05, three TF32 products per term, FP32 accumulation)
+ * when C >= 64, where it measures faster, SIMT FMAs otherwise and for double),
+ * 1 = SIMT everywhere, 2 = the TMA tile::gather4 pass with its shared-memory row cache
+ * for C <= 10 (float, N = 3; TF_EINVAL from the next sweep where it does not apply)
+ * and the tensor-core Gram for every wide C.  For C <= 16 all paths give bit-identical
+ * results; the tensor-core Gram agrees with the SIMT one to FP32 rounding. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
 /* ------------------------------------------------------------------ timing */

@@ -516,7 +516,8 @@ struct Impl : CtxBase {
                 use_tma = ok || build_tmaps(W);
             }
         }
-        if (path == 2 && !use_tma) throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
+        if (path == 2 && !use_tma && !(wide && sizeof(T) == 4))
+            throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
         last_path = 0;
         const int nsplit = (K + C - 1) / C;
         int cq = Cq;
@@ -576,8 +577,13 @@ struct Impl : CtxBase {
                         const int wgrid = pass_wide_grid<T>(num_sms, L.P);
                         // every block takes one ticket past the last bin
                         ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
+                        // float: the tensor-core Gram where it measures faster (the
+                        // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
+                        const bool tc = sizeof(T) == 4 && path != 1 &&
+                                        (path == 2 || wide_tile_width(Cs) == 128);
                         timed(TF_KIND_MODE_PASS,
-                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, st); });
+                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, st); });
+                        last_path |= tc ? 4 : 1;
                         ++launches;
                         if (L.n_single > 0) {
                             timed(TF_KIND_SOLVE, [&] {

@@ -137,8 +137,10 @@ inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
 int wide_tile_width(int C);
 template <class T>
 int pass_wide_grid(int num_sms, int P);
+// tensor_cores: float contexts only (tcgen05 3xTF32 Gram); otherwise SIMT FMAs.
 template <class T>
-void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st);
+void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores,
+                      cudaStream_t st);
 template <class T>
 void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,
                        cudaStream_t st);

@@ -159,6 +159,273 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
     }
 }
 
+// ---------------------------------------------------------------- tensor-core Gram
+// Float contexts: the same pass with H'^T H' on the 5th-generation tensor cores.  The
+// tile's H' is stored transposed in shared memory (columns of H' as M rows, entries as
+// K, no swizzle: 8-row x 16-byte core matrices, K-adjacent ones 128 bytes apart, 8-row
+// groups kTcSbo bytes apart), split into a TF32 high part and a TF32 remainder; three
+// tcgen05.mma kind::tf32 per 8 entries (hi.hi + hi.lo + lo.hi) accumulate the Gram in a
+// 128 x CW fp32 tile of tensor memory, which keeps FP32-level accuracy.  One thread
+// issues the MMAs and commits them to the mbarrier of the operand stage; a stage is
+// rewritten only after its commit arrived (bounded waits).  At the end of an item warps 0-3 read
+// the tile back (tcgen05.ld, one row per thread) and store the item's partial.
+
+constexpr int kTcM = 128;                          // MMA rows (H' columns, padded)
+constexpr int kTcSbo = (kWideTile / 4) * 128;      // bytes between 8-row groups
+constexpr int kTcBuf = (kTcM / 8) * kTcSbo;        // one operand copy: 16 KB
+constexpr long long kTcSpin = 1ll << 24;
+// Operand stages.  Two let the next tile be built while the MMAs run, but cost a block
+// per SM; the tile build (row gathers) dominates and measured faster with one.
+constexpr int kTcStages = 1;
+
+__device__ __forceinline__ unsigned tc_saddr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t tc_desc(const void *p) {
+    const uint64_t a = tc_saddr(p);
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(kTcSbo >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity) {
+    for (long long i = 0; i < kTcSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, "
+            "0, p; }"
+            : "=r"(ok)
+            : "r"(tc_saddr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int CW, bool FIRST>
+__global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<float> a, int CM, int W) {
+    using T = float;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // kTcStages operand stages (hi and lo copies each)
+    unsigned char *stage0 = smem_raw;
+    T *own = reinterpret_cast<T *>(smem_raw + 2 * kTcStages * kTcBuf);  // prev | old (2 CM)
+    T *s_res = own + 2 * CM;                                   // [kWideTile]
+    int32_t *s_idx = reinterpret_cast<int32_t *>(s_res + kWideTile);
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_taddr;
+    __shared__ unsigned long long s_tk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int no = a.N - 1, n_lo = a.n, C = a.C, Cq = a.Cq;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_saddr(&s_taddr)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(CW >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    // per stage: the parity the next wait expects, and whether a commit is outstanding
+    // (every thread tracks the same values)
+    unsigned phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool timed_out = false;
+    unsigned tiles = 0;
+    auto drain = [&](int st) {
+        if (!pending[st]) return true;
+        const bool ok = tc_wait(&mbar[st], phase[st]);
+        phase[st] ^= 1u;
+        pending[st] = false;
+        return ok;
+    };
+
+    for (;;) {
+        if (tid == 0) s_tk = atomicAdd(a.ticket, 1ull) - a.ticket_base;
+        __syncthreads();
+        const unsigned long long tk = s_tk;
+        __syncthreads();
+        if (tk >= (unsigned long long)a.P) break;
+        for (int64_t it = a.bin_ptr[tk]; it < a.bin_ptr[tk + 1] && !timed_out; ++it) {
+            const tf_item item = a.items[it];
+            if (FIRST) {
+                const T *z = a.Zn + (int64_t)a.rank_n[item.row] * W;
+                for (int q = tid; q < 2 * CM; q += kWideThreads) own[q] = z[CM + q];
+            }
+            bool first_tile = true;
+            for (int64_t j0 = item.begin; j0 < item.begin + item.len; j0 += kWideTile) {
+                const int64_t left = item.begin + item.len - j0;
+                const int ne = left < kWideTile ? (int)left : kWideTile;
+                const int st = kTcStages == 1 ? 0 : (int)(tiles & 1u);
+                unsigned char *ahi = stage0 + st * 2 * kTcBuf, *alo = ahi + kTcBuf;
+                // the stage's previous MMAs must be done before its operands change
+                const bool ok = drain(st);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (__syncthreads_or(!ok)) {
+                    timed_out = true;
+                    break;
+                }
+                for (int q = tid; q < kWideTile * (no + 1); q += kWideThreads) {
+                    const int t = q / kWideTile, e = q - t * kWideTile;
+                    if (e < ne) {
+                        if (t < no)
+                            s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
+                        else
+                            s_res[e] = a.res[j0 + e];
+                    }
+                }
+                __syncthreads();
+                {
+                    const int e = tid >> 3, g = tid & 7;
+                    const bool valid = e < ne;
+                    const T *rows[kMaxModes - 1];
+                    for (int t = 0; t < no; ++t)
+                        rows[t] = a.Zo[t] + (int64_t)(valid ? s_idx[t * kWideTile + e] : 0) * W;
+                    T pp = T(0), po = T(0);
+                    const int cmax = CW > CM ? CW : CM;
+                    const int eoff = (e >> 2) * 128 + (e & 3) * 4;
+                    for (int c = g; c < cmax; c += 8) {
+                        T hv = T(0);
+                        if (valid && c < C) {
+                            hv = T(1);
+                            for (int t = 0; t < no; ++t) hv *= rows[t][c];
+                            if (FIRST) {
+                                T o = own[CM + c];
+                                for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
+                                po += o;
+                            }
+                        }
+                        if (FIRST && valid && c < Cq) {
+                            T p = own[c];
+                            for (int t = 0; t < no; ++t) p *= rows[t][CM + c];
+                            pp += p;
+                        }
+                        if (c < CW && c != C) {
+                            const int off = (c >> 3) * kTcSbo + eoff + (c & 7) * 16;
+                            const uint32_t hb = tf32_bits(hv);
+                            *reinterpret_cast<uint32_t *>(ahi + off) = hb;
+                            *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(hv - __uint_as_float(hb));
+                        }
+                    }
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) {
+                        pp += __shfl_xor_sync(0xFFFFFFFFu, pp, o);
+                        po += __shfl_xor_sync(0xFFFFFFFFu, po, o);
+                    }
+                    if (g == 0) {
+                        T v = valid ? s_res[e] : T(0);
+                        if (FIRST && valid) {
+                            v = v - pp + po;
+                            a.res[j0 + e] = v;
+                        }
+                        const int off = (C >> 3) * kTcSbo + eoff + (C & 7) * 16;
+                        const uint32_t hb = tf32_bits(v);
+                        *reinterpret_cast<uint32_t *>(ahi + off) = hb;
+                        *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(v - __uint_as_float(hb));
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int k = 0; k < kWideTile / 8; ++k) {
+                        const uint64_t dh = tc_desc(ahi + k * 256), dl = tc_desc(alo + k * 256);
+                        const uint64_t A[3] = {dh, dh, dl}, B[3] = {dh, dl, dh};
+#pragma unroll
+                        for (int u = 0; u < 3; ++u) {
+                            const uint32_t acc = (first_tile && k == 0 && u == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                                "l"(A[u]), "l"(B[u]), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            tc_saddr(&mbar[st]))
+                        : "memory");
+                }
+                pending[st] = true;
+                ++tiles;
+                first_tile = false;
+            }
+            if (timed_out) break;
+            // item end: wait for its MMAs, then rows of the Gram tile -> lower triangle
+            // of B and c = row C
+            {
+                const bool ok0 = drain(0), ok1 = drain(1);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (__syncthreads_or(!(ok0 && ok1))) {
+                    timed_out = true;
+                    break;
+                }
+            }
+            T *p = a.partials + (int64_t)item.slot * (CM * (CM + 1) / 2 + CM);
+            const int NT = CM * (CM + 1) / 2;
+            if (warp < 4) {
+                const int r = warp * 32 + lane;
+                for (int cc = 0; cc < CW; cc += 32) {
+                    uint32_t v[32];
+                    if (!first_tile) {
+                        tc_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] = 0u;  // empty item: B = 0, c = 0
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int j = cc + q;
+                        const T val = __uint_as_float(v[q]);
+                        if (r < CM && j <= r) p[r * (r + 1) / 2 + j] = (r < C && j < C) ? val : T(0);
+                        if (r == C && j < CM) p[NT + j] = j < C ? val : T(0);
+                    }
+                }
+            }
+            if (C < CM)
+                for (int q = C + tid; q < CM; q += kWideThreads) p[NT + q] = T(0);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (timed_out) break;
+    }
+    {   // MMAs still in flight (after a timeout) finish before the tensor memory goes
+        const bool ok0 = drain(0), ok1 = drain(1);
+        if ((timed_out || !ok0 || !ok1) && tid == 0) atomicOr(&a.stat->bits, kStatTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(128)
+                     : "memory");
+}
+
 // One warp per row (kSolveWarps rows per block): sums the row's slots in slot order
 // into a packed lower triangle in shared memory, solves (B + lambda I) x = c and writes
 // x to A_n[row][S[c]] and to the cur region of the own slice row.
@@ -245,6 +512,19 @@ __global__ void __launch_bounds__(kWideThreads) k_res_wide(const ResArgs<T> a, i
     }
 }
 
+template <int CW>
+void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, cudaStream_t st) {
+    // at least 48 KB of shared memory per block keeps at most four blocks (4 x 128 tensor
+    // memory columns) on an SM, so no allocation ever waits
+    size_t smem = 2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + kWideTile) +
+                  sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
+    smem = std::max<size_t>(smem, 48 * 1024);
+    auto kern = a.first ? k_pass_wide_tc<CW, true> : k_pass_wide_tc<CW, false>;
+    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
+    TFS_CUDA(cudaGetLastError());
+}
+
 template <class T, int CW>
 void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st) {
     const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM + kWideTile) +
@@ -261,11 +541,29 @@ int wide_tile_width(int C) { return C + 1 <= 32 ? 32 : (C + 1 <= 64 ? 64 : (C + 
 
 template <class T>
 int pass_wide_grid(int num_sms, int P) {
-    return std::max(1, std::min(P, num_sms * 4));
+    return std::max(1, std::min(P, num_sms * 4));  // the tensor-core variant: 4 blocks per SM
 }
 
 template <class T>
-void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st) {
+void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores,
+                      cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (tensor_cores) {
+            switch (wide_tile_width(a.C)) {
+                case 32:
+                    launch_pass_wide_tc_cw<32>(a, CM, W, grid, st);
+                    return;
+                case 64:
+                    launch_pass_wide_tc_cw<64>(a, CM, W, grid, st);
+                    return;
+                case 128:
+                    launch_pass_wide_tc_cw<128>(a, CM, W, grid, st);
+                    return;
+                default:
+                    throw ApiError{TF_EINVAL, "C >= 128 is not supported"};
+            }
+        }
+    }
     switch (wide_tile_width(a.C)) {
         case 32:
             launch_pass_wide_cw<T, 32>(a, CM, W, grid, st);
@@ -307,7 +605,7 @@ void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st) {
 
 #define TFS_INST(T)                                                                           \
     template int pass_wide_grid<T>(int, int);                                                 \
-    template void launch_pass_wide<T>(const PassArgs<T> &, int, int, int, cudaStream_t);      \
+    template void launch_pass_wide<T>(const PassArgs<T> &, int, int, int, bool, cudaStream_t); \
     template void launch_solve_wide<T>(const PassArgs<T> &, const SplitRow *, int, int, int,  \
                                        cudaStream_t);                                         \
     template void launch_res_wide<T>(const ResArgs<T> &, int, cudaStream_t);

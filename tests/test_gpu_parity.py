@@ -482,3 +482,28 @@ def test_wide_singular_rows_left_unchanged():
     assert f.counters()["singular_rows"] == bad_o > 0
     for n in range(3):
         assert rel(f.factors(n), A[n]) < 1e-8
+
+
+@pytest.mark.parametrize("C,K", [(20, 40), (40, 40), (70, 100)])
+def test_wide_tensor_core_gram_fp32(C, K):
+    """Float contexts compute the wide Gram on the tensor cores (3xTF32, FP32
+    accumulation): factors agree with the FP64 oracle to FP32-level error normwise, and
+    with the SIMT path of the same library to the same level."""
+    p = synth.small(80 + C, (301, 157, 97), 15_000, 4, K)
+    f, t, A = make(p, tf.F32)
+    f.set_kernel_path(tf.Factorization.PATH_TMA)   # tensor-core Gram for every wide C
+    g, _, _ = make(p, tf.F32)
+    g.set_kernel_path(tf.Factorization.PATH_SIMT)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.3, 1, order)
+        g.sweep(C, 0.3, 1, order)
+        oracle.sals_sweep(t, A, r, C, 0.3, 1, order)
+    assert f.counters()["pass_path"] & 4 and not g.counters()["pass_path"] & 4
+    for n in range(3):
+        assert rel(f.factors(n).astype(np.float64), A[n]) < 2e-4
+        assert rel(f.factors(n), g.factors(n)) < 2e-4
+    _, rmse = f.loss(0.3)
+    _, rmseo = oracle.loss(t, r, A, 0.3)
+    assert abs(rmse - rmseo) <= 1e-4 * rmseo
