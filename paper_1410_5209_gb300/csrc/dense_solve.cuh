@@ -1,7 +1,8 @@
 // One warp solves (B + lam I) x = c for a C x C symmetric positive definite system held
 // in shared memory (Section 3.1's Cholesky row solve, for systems too wide for the
 // per-thread register version): B as a packed lower triangle P[i (i + 1) / 2 + j],
-// factored in place by a right-looking Cholesky; c is overwritten by x.  Returns false
+// factored in place by a left-looking Cholesky (lanes over rows, dot products with the
+// pivot row); c is overwritten by x.  Returns false
 // (P and c then meaningless) when a pivot is not positive.  Every lane calls it.
 #pragma once
 
@@ -18,23 +19,32 @@ __device__ __forceinline__ T warp_allsum(T v) {
 
 template <class T>
 __device__ bool warp_chol_solve(T *P, T *c, int C, T lam, int lane) {
-    for (int i = lane; i < C; i += 32) P[ptri(i, i)] += lam;
-    __syncwarp();
+    // left-looking: column j from the finished columns 0..j-1, lanes over the rows below
+    // the diagonal (each a dot product with the broadcast row j)
     bool ok = true;
     for (int j = 0; j < C; ++j) {
-        const T d = P[ptri(j, j)];
+        const T *rj = P + ptri(j, 0);
+        T s = T(0);
+        for (int k = lane; k < j; k += 32) s += rj[k] * rj[k];
+        s = warp_allsum(s);
+        const T d = P[ptri(j, j)] + lam - s;
         ok = ok && (d > T(0));
         const T ljj = sqrt(d > T(0) ? d : T(1));
+        for (int i = j + 1 + lane; i < C; i += 32) {
+            const T *ri = P + ptri(i, 0);
+            T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);  // four independent chains
+            int k = 0;
+            for (; k + 4 <= j; k += 4) {
+                t0 += ri[k] * rj[k];
+                t1 += ri[k + 1] * rj[k + 1];
+                t2 += ri[k + 2] * rj[k + 2];
+                t3 += ri[k + 3] * rj[k + 3];
+            }
+            for (; k < j; ++k) t0 += ri[k] * rj[k];
+            P[ptri(i, j)] = (ri[j] - ((t0 + t1) + (t2 + t3))) / ljj;
+        }
         __syncwarp();
         if (lane == 0) P[ptri(j, j)] = ljj;
-        for (int i = j + 1 + lane; i < C; i += 32) P[ptri(i, j)] /= ljj;
-        __syncwarp();
-        // trailing update of the lower triangle: rows i > j, columns j < k <= i
-        for (int i = j + 1; i < C; ++i) {
-            const T lij = P[ptri(i, j)];
-            T *row = P + ptri(i, 0);
-            for (int k = j + 1 + lane; k <= i; k += 32) row[k] -= lij * P[ptri(k, j)];
-        }
         __syncwarp();
     }
     // L y = c, then L^T x = y
