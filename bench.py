@@ -162,6 +162,64 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def study(args, rank, world):
+    """Section 5.5-style studies on the same workload, one JSON line per configuration:
+    sweeps at each C (time per sweep and training RMSE after each, from the same initial
+    factors; C = K is ALS), then the row-assignment policies at the workload's C."""
+    import numpy as np
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    from paper_1410_5209_gb300 import build as tfbuild
+    if rank != 0:
+        return 0
+    tfbuild.build()
+    tf.load()
+    K, lam = WORKLOAD["K"], WORKLOAD["lam"]
+    p = synth.skewed_3way(seed=args.seed, nnz=args.nnz, device="cuda")
+    stream = torch.cuda.current_stream()
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+                         stream=stream.cuda_stream, device_input=True)
+    A0 = [a.numpy().astype(np.float32) for a in p.init_factors(torch.float64, "cpu")]
+    p_nnz = p.nnz
+
+    def run(C, sweeps):
+        for n in range(3):
+            f.set_factors(n, A0[n])
+        times, rmses = [], []
+        for s in range(sweeps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            f.sweep(C, lam, 1, p.column_order(s, C))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            rmses.append(f.loss(lam)[1])
+        return times, rmses
+
+    for C in [int(c) for c in args.study_c.split(",")]:
+        run(C, 1)  # warm-up (kernel selection, buffers)
+        times, rmses = run(C, args.study_sweeps)
+        ms = float(np.median(times))
+        print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz, "ms_per_sweep": ms,
+                          "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
+                          "sweep_ms": times, "train_rmse": rmses,
+                          "pass_path": f.counters()["pass_path"]}), flush=True)
+    C = WORKLOAD["C"]
+    for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),
+                      ("seq", tf.SCHED_SEQ), ("ran", tf.SCHED_RAN)):
+        f.set_schedule(pol, 0)
+        run(C, 1)
+        times, rmses = run(C, args.study_sweeps)
+        ms = float(np.median(times))
+        print(json.dumps({"study": "schedule", "policy": name, "C": C, "ms_per_sweep": ms,
+                          "nnz_rank_per_s": p_nnz * K / (ms / 1e3), "train_rmse": rmses,
+                          "split_rows": f.counters()["split_rows"]}), flush=True)
+    f.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,8 +233,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
     ap.add_argument("--foldin-requests", type=int, default=200)
+    ap.add_argument("--study", action="store_true",
+                    help="C-sweep and row-assignment policy study instead of the benchmark")
+    ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
+    ap.add_argument("--study-sweeps", type=int, default=3)
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.study:
+        return study(args, rank, world)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

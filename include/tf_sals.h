@@ -187,6 +187,16 @@ tf_status tf_loss_noalloc(tf_ctx *ctx, double lambda, uint32_t flags, double *lo
 tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *values,
                     int64_t m, double lambda, void *out_row);
 
+/* ------------------------------------------------------------------ prediction */
+
+/* Model values x_hat_e = sum_k prod_n a^(n)_{i_n k} (the CP model of Eq. 1) at m
+ * coordinates, e.g. held-out entries for a test RMSE.
+ *   coords [m][N] int32, 0-based; out [m] context dtype.  Both host buffers, or both
+ *   device buffers on the context's device with flags = TF_INPUT_DEVICE.
+ * Products and the sum over k in double on the device.  Synchronises.  TF_ERANGE if a
+ * coordinate is out of range (out is then unspecified). */
+tf_status tf_predict(tf_ctx *ctx, const int32_t *coords, int64_t m, void *out, uint32_t flags);
+
 /* ------------------------------------------------------------------ inspection */
 
 /* Row offsets off[I_n + 1] (int64) and, if perm != NULL, the canonical entry index of

@@ -72,6 +72,7 @@ def load():
         "tf_loss": [P, f64, u32, P, P],
         "tf_loss_noalloc": [P, f64, u32, P, P],
         "tf_foldin": [P, i32, P, P, i64, f64, P],
+        "tf_predict": [P, P, i64, P, u32],
         "tf_get_grouping": [P, i32, P, P],
         "tf_get_residual": [P, P],
         "tf_get_counters": [P, P],
@@ -108,6 +109,10 @@ def _ptr(a):
 
 def _tensor_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _is_cuda_tensor(x):
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
 
 
 def _np_dtype(dtype):
@@ -200,6 +205,21 @@ class Factorization:
                                               WEIGHTED_LAMBDA if weighted else 0,
                                               ctypes.byref(l), ctypes.byref(r)))
         return l.value, r.value
+
+    def predict(self, coords):
+        """Model values at coordinates [m][N] (host arrays, or torch CUDA tensors)."""
+        if _is_cuda_tensor(coords):
+            import torch
+            c = coords.to(torch.int32).contiguous()
+            out = torch.empty(c.shape[0], dtype=torch.float32 if self.dtype == F32 else torch.float64,
+                              device=c.device)
+            self._check(self._lib.tf_predict(self._ctx, _tensor_ptr(c), int(c.shape[0]),
+                                             _tensor_ptr(out), INPUT_DEVICE))
+            return out
+        c = np.ascontiguousarray(coords, np.int32).reshape(-1, self.N)
+        out = np.zeros(c.shape[0], self.npdt)
+        self._check(self._lib.tf_predict(self._ctx, _ptr(c), int(c.shape[0]), _ptr(out), 0))
+        return out
 
     def foldin(self, mode, other, values, lam):
         other = np.ascontiguousarray(other, np.int32).reshape(-1, self.N - 1)

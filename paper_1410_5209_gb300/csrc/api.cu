@@ -97,6 +97,8 @@ struct Impl : CtxBase {
     Buf<int64_t> d_dims;
     Buf<int32_t> f_other;          // fold-in scratch
     Buf<T> f_x, f_out, f_part;
+    Buf<int32_t> p_coords;         // tf_predict staging
+    Buf<T> p_out;
     int32_t *h_order = nullptr;    // pinned staging of the column order
     cudaEvent_t order_ev = nullptr;
     bool order_pending = false;
@@ -574,13 +576,13 @@ struct Impl : CtxBase {
                     a.ticket = ticket.p;
                     a.ticket_base = ticket_base;
                     if (wide) {
-                        const int wgrid = pass_wide_grid<T>(num_sms, L.P);
-                        // every block takes one ticket past the last bin
-                        ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
                         // float: the tensor-core Gram where it measures faster (the
                         // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
                         const bool tc = sizeof(T) == 4 && path != 1 &&
                                         (path == 2 || wide_tile_width(Cs) == 128);
+                        const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
+                        // every block takes one ticket past the last bin
+                        ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
                         timed(TF_KIND_MODE_PASS,
                               [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, st); });
                         last_path |= tc ? 4 : 1;
@@ -852,6 +854,45 @@ struct Impl : CtxBase {
                                  cudaMemcpyDeviceToHost, st));
         TFS_CUDA(cudaStreamSynchronize(st));
         check_errors();
+    }
+
+    // ------------------------------------------------------------ prediction
+    void predict(const int32_t *coords, int64_t m, T *out, uint32_t flags) {
+        if (m < 0) throw ApiError{TF_EINVAL, "m must be >= 0"};
+        if (m == 0) return;
+        const bool dev = (flags & TF_INPUT_DEVICE) != 0;
+        const int32_t *dc = coords;
+        T *dout = out;
+        if (!dev) {
+            p_coords.ensure((size_t)m * N);
+            p_out.ensure((size_t)m);
+            TFS_CUDA(cudaMemcpyAsync(p_coords.p, coords, (size_t)m * N * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+            dc = p_coords.p;
+            dout = p_out.p;
+        }
+        PredictArgs<T> a{};
+        a.N = N;
+        a.K = K;
+        for (int l = 0; l < N; ++l) {
+            a.A[l] = A[l].p;
+            a.I[l] = dims[l];
+        }
+        a.m = m;
+        a.coords = dc;
+        a.out = dout;
+        a.stat = stat.p;
+        launch_predict<T>(a, st);
+        DeviceStatus s = read_status();
+        if (s.bits & kStatPredictRange) {
+            TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
+            TFS_CUDA(cudaStreamSynchronize(st));
+            throw ApiError{TF_ERANGE, "prediction coordinate out of range"};
+        }
+        if (!dev) {
+            TFS_CUDA(cudaMemcpyAsync(out, dout, (size_t)m * sizeof(T), cudaMemcpyDeviceToHost, st));
+            TFS_CUDA(cudaStreamSynchronize(st));
+        }
     }
 
     // ------------------------------------------------------------ fold-in
@@ -1149,6 +1190,14 @@ tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *val
     return dispatch(ctx, [&](auto &c) {
         using T = typename std::remove_reference<decltype(*c.x.p)>::type;
         c.foldin(mode, other, static_cast<const T *>(values), m, lambda, static_cast<T *>(out_row));
+    });
+}
+
+tf_status tf_predict(tf_ctx *ctx, const int32_t *coords, int64_t m, void *out, uint32_t flags) {
+    if (m > 0 && (!coords || !out)) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.predict(coords, m, static_cast<T *>(out), flags);
     });
 }
 

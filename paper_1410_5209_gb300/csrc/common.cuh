@@ -21,6 +21,7 @@ enum : int {
     kStatFoldRange = 4,  // fold-in index out of range
     kStatFoldPivot = 8,  // fold-in Cholesky pivot <= 0
     kStatTimeout = 16,   // a bounded wait on the device gave up
+    kStatPredictRange = 32,  // tf_predict coordinate out of range
 };
 
 struct DeviceStatus {

@@ -114,6 +114,29 @@ __global__ void k_init_normal(T *A, int64_t count, uint64_t key, double std) {
     A[i] = (T)(std * sqrt(-2.0 * log1p(-u1)) * cospi(2.0 * u2));
 }
 
+// One warp per coordinate, lanes over the K columns (coalesced factor rows), FP64 sum.
+template <class T>
+__global__ void __launch_bounds__(256) k_predict(const PredictArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= a.m) return;
+    const int32_t *c = a.coords + e * a.N;
+    bool ok = true;
+    for (int n = 0; n < a.N; ++n) ok = ok && c[n] >= 0 && c[n] < a.I[n];
+    double s = 0.0;
+    if (ok)
+        for (int k = lane; k < a.K; k += 32) {
+            double p = 1.0;
+            for (int n = 0; n < a.N; ++n) p *= (double)a.A[n][(int64_t)c[n] * a.K + k];
+            s += p;
+        }
+    s = warp_sum_d(s);
+    if (lane == 0) {
+        a.out[e] = ok ? (T)s : T(0);
+        if (!ok) atomicOr(&a.stat->bits, kStatPredictRange);
+    }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) {
     return (unsigned)((n > 0 ? n : 1) + threads - 1) / threads;
 }
@@ -147,6 +170,13 @@ void launch_sum_blocks(const double *in, int n, double *out, cudaStream_t st) {
 }
 
 template <class T>
+void launch_predict(const PredictArgs<T> &a, cudaStream_t st) {
+    if (a.m <= 0) return;
+    k_predict<T><<<blocks_for(a.m * 32, 256), 256, 0, st>>>(a);
+    TFS_CUDA(cudaGetLastError());
+}
+
+template <class T>
 void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, double std,
                         cudaStream_t st) {
     if (count <= 0) return;
@@ -160,7 +190,8 @@ void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, 
     template void launch_init_res<T>(const InitArgs<T> &, cudaStream_t);                   \
     template void launch_reg<T>(const T *, int64_t, int, const int64_t *, double *, int,   \
                                 cudaStream_t);                                             \
-    template void launch_init_normal<T>(T *, int64_t, uint64_t, uint64_t, double, cudaStream_t);
+    template void launch_init_normal<T>(T *, int64_t, uint64_t, uint64_t, double, cudaStream_t); \
+    template void launch_predict<T>(const PredictArgs<T> &, cudaStream_t);
 TFS_INST(float)
 TFS_INST(double)
 #undef TFS_INST

@@ -136,7 +136,7 @@ inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
 // Gram update, block-per-row Cholesky solves, warp-per-bin residual reductions.
 int wide_tile_width(int C);
 template <class T>
-int pass_wide_grid(int num_sms, int P);
+int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first);
 // tensor_cores: float contexts only (tcgen05 3xTF32 Gram); otherwise SIMT FMAs.
 template <class T>
 void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores,
@@ -184,6 +184,21 @@ void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, 
                         cudaStream_t st);
 template <class T>
 void launch_foldin(const FoldArgs<T> &a, cudaStream_t st);
+
+// Model values x_hat_e = sum_k prod_n A^(n)[i_n, k] (the CP model of Eq. 1) at m
+// coordinates [m][N]; an out-of-range coordinate sets kStatPredictRange (its value 0).
+template <class T>
+struct PredictArgs {
+    int N, K;
+    const T *A[kMaxModes];
+    int64_t I[kMaxModes];
+    int64_t m;
+    const int32_t *coords;
+    T *out;
+    DeviceStatus *stat;
+};
+template <class T>
+void launch_predict(const PredictArgs<T> &a, cudaStream_t st);
 // Blocks of the tiled fold-in for a request of m entries (0: the one-block kernel),
 // and its partial buffer length in elements.
 int foldin_blocks(int K, int64_t m, int num_sms);

@@ -539,9 +539,28 @@ void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStre
 
 int wide_tile_width(int C) { return C + 1 <= 32 ? 32 : (C + 1 <= 64 ? 64 : (C + 1 <= 128 ? 128 : 0)); }
 
+// Blocks of a wide pass: every block that can be resident (the SIMT variant's few
+// registers allow up to 8 per SM; the tensor-core one is held to 4 by its shared memory,
+// 4 x 128 tensor-memory columns).
 template <class T>
-int pass_wide_grid(int num_sms, int P) {
-    return std::max(1, std::min(P, num_sms * 4));  // the tensor-core variant: 4 blocks per SM
+int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first) {
+    int per_sm = 4;
+    if (!(sizeof(T) == 4 && tensor_cores)) {
+        const int cw = wide_tile_width(C);
+        const size_t smem = sizeof(T) * ((size_t)kWideTile * (cw + 4) + 2 * (size_t)CM + kWideTile) +
+                            sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
+        const void *kern = nullptr;
+        if (cw == 32)
+            kern = first ? (const void *)k_pass_wide<T, 32, true> : (const void *)k_pass_wide<T, 32, false>;
+        else if (cw == 64)
+            kern = first ? (const void *)k_pass_wide<T, 64, true> : (const void *)k_pass_wide<T, 64, false>;
+        else
+            kern = first ? (const void *)k_pass_wide<T, 128, true> : (const void *)k_pass_wide<T, 128, false>;
+        TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWideThreads, smem));
+        per_sm = std::max(1, std::min(per_sm, 8));
+    }
+    return std::max(1, std::min(P, num_sms * per_sm));
 }
 
 template <class T>
@@ -604,7 +623,7 @@ void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st) {
 }
 
 #define TFS_INST(T)                                                                           \
-    template int pass_wide_grid<T>(int, int);                                                 \
+    template int pass_wide_grid<T>(int, int, int, int, bool, bool);                           \
     template void launch_pass_wide<T>(const PassArgs<T> &, int, int, int, bool, cudaStream_t); \
     template void launch_solve_wide<T>(const PassArgs<T> &, const SplitRow *, int, int, int,  \
                                        cudaStream_t);                                         \

@@ -507,3 +507,36 @@ def test_wide_tensor_core_gram_fp32(C, K):
     _, rmse = f.loss(0.3)
     _, rmseo = oracle.loss(t, r, A, 0.3)
     assert abs(rmse - rmseo) <= 1e-4 * rmseo
+
+
+# --------------------------------------------------------------------------- predict
+
+
+@pytest.mark.parametrize("dtype,tol", [(tf.F64, 1e-12), (tf.F32, 1e-5)])
+def test_predict_matches_model(dtype, tol):
+    """tf_predict is the CP model of Eq. (1): at the observed coordinates it equals
+    x - residual of the oracle (the residual is pinned against a dense reconstruction),
+    and a held-out set gives the test RMSE; bad coordinates are rejected."""
+    p = synth.small(90, (300, 200, 50), 20_000, 4, 12)
+    f, t, A = make(p, dtype)
+    for s in range(2):
+        order = p.column_order(s, 4)
+        f.sweep(4, 0.2, 1, order)
+    A_dev = [f.factors(n).astype(np.float64) for n in range(3)]
+    held = np.stack([np.arange(500) % 300, (np.arange(500) * 7) % 200,
+                     (np.arange(500) * 13) % 50], 1).astype(np.int32)
+    got = f.predict(held)
+    ref = -oracle.residual(oracle.Tensor(held, np.zeros(500), p.dims), A_dev)
+    assert np.max(np.abs(got - ref)) <= tol * max(1.0, np.max(np.abs(ref)))
+    got_obs = f.predict(t.coords)
+    res = f.residual()
+    assert np.max(np.abs((t.x - got_obs) - res)) <= 10 * tol * max(1.0, np.max(np.abs(t.x)))
+    import torch
+    dev = f.predict(torch.from_numpy(held).cuda())
+    assert np.allclose(dev.cpu().numpy(), got, rtol=0, atol=tol * max(1.0, np.max(np.abs(ref))))
+    bad = held.copy()
+    bad[7, 2] = 50
+    with pytest.raises(tf.TFError) as e:
+        f.predict(bad)
+    assert e.value.status == tf.ERANGE
+    assert np.allclose(f.predict(held), got)
