@@ -579,7 +579,7 @@ struct Impl : CtxBase {
                         // float: the tensor-core Gram where it measures faster (the
                         // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
                         const bool tc = sizeof(T) == 4 && path != 1 &&
-                                        (path == 2 || wide_tile_width(Cs) == 128);
+                                        (path == 2 || wide_split_width(Cs, CM) == 128);
                         const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
                         // every block takes one ticket past the last bin
                         ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;

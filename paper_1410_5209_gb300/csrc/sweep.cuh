@@ -135,6 +135,7 @@ inline int partial_stride(int CM) { return CM * (CM + 1) / 2 + CM; }
 // Wide column subsets, 16 < C < 128 (wide.cu): block-per-bin mode pass with a tiled
 // Gram update, block-per-row Cholesky solves, warp-per-bin residual reductions.
 int wide_tile_width(int C);
+int wide_split_width(int C, int CM);
 template <class T>
 int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first);
 // tensor_cores: float contexts only (tcgen05 3xTF32 Gram); otherwise SIMT FMAs.

@@ -32,7 +32,48 @@ __device__ __forceinline__ T wsum(T v) {
     return v;
 }
 
-// CW: Gram tile width (32, 64 or 128), at least C + 1 (column C holds r_hat).
+// Columns g, g + 8, ... (< CW) of one entry's H' row: h_c for c < C, and on the first
+// inner iteration the R-hat refresh products po (c < C) and pp (c < Cq).  The loop is
+// unrolled over the compile-time width so all slice-row loads issue together; three
+// modes (two other rows) take a path without the runtime mode loop.
+template <class T, int CW, bool FIRST, class Store>
+__device__ __forceinline__ void wide_entry_columns(const T *const *rows, int no, int n_lo, int C,
+                                                   int Cq, int CM, const T *own, bool valid,
+                                                   int g, T &pp, T &po, Store store) {
+#pragma unroll
+    for (int k = 0; k < CW / 8; ++k) {
+        const int c = g + 8 * k;
+        T hv = T(0);
+        if (valid && c < C) {
+            if (no == 2) {
+                const T x0 = rows[0][c], x1 = rows[1][c];
+                hv = x0 * x1;
+                if (FIRST) {
+                    const T o0 = n_lo > 0 ? rows[0][2 * CM + c] : x0;
+                    const T o1 = n_lo > 1 ? rows[1][2 * CM + c] : x1;
+                    po += own[CM + c] * (o0 * o1);
+                }
+            } else {
+                hv = T(1);
+                for (int t = 0; t < no; ++t) hv *= rows[t][c];
+                if (FIRST) {
+                    T o = own[CM + c];
+                    for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
+                    po += o;
+                }
+            }
+        }
+        if (FIRST && valid && c < Cq) {
+            T p = own[c];
+            for (int t = 0; t < no; ++t) p *= rows[t][CM + c];
+            pp += p;
+        }
+        store(c, hv);
+    }
+}
+
+// CW: Gram tile width (32, 64 or 128), at least C + 1 (column C holds r_hat) and at least
+// CM (the previous subset's columns are read through the same loop).
 template <class T, int CW, bool FIRST>
 __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a, int CM, int W) {
     constexpr int R = CW / 16;       // register tile edge
@@ -87,26 +128,10 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
                     for (int t = 0; t < no; ++t)
                         rows[t] = a.Zo[t] + (int64_t)(valid ? s_idx[t * kWideTile + e] : 0) * W;
                     T pp = T(0), po = T(0);
-                    // columns of S (< C <= CW - 1) and of the previous subset Q (< Cq <= CM)
-                    const int cmax = CW > CM ? CW : CM;
-                    for (int c = g; c < cmax; c += 8) {
-                        T hv = T(0);
-                        if (valid && c < C) {
-                            hv = T(1);
-                            for (int t = 0; t < no; ++t) hv *= rows[t][c];
-                            if (FIRST) {
-                                T o = own[CM + c];
-                                for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
-                                po += o;
-                            }
-                        }
-                        if (FIRST && valid && c < Cq) {
-                            T p = own[c];
-                            for (int t = 0; t < no; ++t) p *= rows[t][CM + c];
-                            pp += p;
-                        }
-                        if (c < CW) h[c] = hv;
-                    }
+                    // columns of S (< C <= CW - 1) and of the previous subset Q (< Cq <= CM
+                    // <= CW)
+                    wide_entry_columns<T, CW, FIRST>(rows, no, n_lo, C, Cq, CM, own, valid, g, pp,
+                                                     po, [&](int c, T hv) { h[c] = hv; });
 #pragma unroll
                     for (int o = 4; o > 0; o >>= 1) {
                         pp += __shfl_xor_sync(0xFFFFFFFFu, pp, o);
@@ -306,31 +331,15 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                     for (int t = 0; t < no; ++t)
                         rows[t] = a.Zo[t] + (int64_t)(valid ? s_idx[t * kWideTile + e] : 0) * W;
                     T pp = T(0), po = T(0);
-                    const int cmax = CW > CM ? CW : CM;
                     const int eoff = (e >> 2) * 128 + (e & 3) * 4;
-                    for (int c = g; c < cmax; c += 8) {
-                        T hv = T(0);
-                        if (valid && c < C) {
-                            hv = T(1);
-                            for (int t = 0; t < no; ++t) hv *= rows[t][c];
-                            if (FIRST) {
-                                T o = own[CM + c];
-                                for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
-                                po += o;
-                            }
-                        }
-                        if (FIRST && valid && c < Cq) {
-                            T p = own[c];
-                            for (int t = 0; t < no; ++t) p *= rows[t][CM + c];
-                            pp += p;
-                        }
-                        if (c < CW && c != C) {
+                    wide_entry_columns<T, CW, FIRST>(
+                        rows, no, n_lo, C, Cq, CM, own, valid, g, pp, po, [&](int c, T hv) {
+                            if (c == C) return;
                             const int off = (c >> 3) * kTcSbo + eoff + (c & 7) * 16;
                             const uint32_t hb = tf32_bits(hv);
                             *reinterpret_cast<uint32_t *>(ahi + off) = hb;
                             *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(hv - __uint_as_float(hb));
-                        }
-                    }
+                        });
 #pragma unroll
                     for (int o = 4; o > 0; o >>= 1) {
                         pp += __shfl_xor_sync(0xFFFFFFFFu, pp, o);
@@ -539,6 +548,13 @@ void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStre
 
 int wide_tile_width(int C) { return C + 1 <= 32 ? 32 : (C + 1 <= 64 ? 64 : (C + 1 <= 128 ? 128 : 0)); }
 
+// Tile width of a split: H' needs C + 1 columns, and the R-hat refresh reads the previous
+// subset's Cq <= CM columns through the same column loop.
+int wide_split_width(int C, int CM) {
+    const int need = std::max(C + 1, CM);
+    return need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : 0));
+}
+
 // Blocks of a wide pass: every block that can be resident (the SIMT variant's few
 // registers allow up to 8 per SM; the tensor-core one is held to 4 by its shared memory,
 // 4 x 128 tensor-memory columns).
@@ -546,7 +562,7 @@ template <class T>
 int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first) {
     int per_sm = 4;
     if (!(sizeof(T) == 4 && tensor_cores)) {
-        const int cw = wide_tile_width(C);
+        const int cw = wide_split_width(C, CM);
         const size_t smem = sizeof(T) * ((size_t)kWideTile * (cw + 4) + 2 * (size_t)CM + kWideTile) +
                             sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
         const void *kern = nullptr;
@@ -568,7 +584,7 @@ void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor
                       cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (tensor_cores) {
-            switch (wide_tile_width(a.C)) {
+            switch (wide_split_width(a.C, CM)) {
                 case 32:
                     launch_pass_wide_tc_cw<32>(a, CM, W, grid, st);
                     return;
@@ -583,7 +599,7 @@ void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor
             }
         }
     }
-    switch (wide_tile_width(a.C)) {
+    switch (wide_split_width(a.C, CM)) {
         case 32:
             launch_pass_wide_cw<T, 32>(a, CM, W, grid, st);
             return;
