@@ -164,8 +164,9 @@ def reference_arm(args, rank, world):
 
 def study(args, rank, world):
     """Section 5.5-style studies on the same workload, one JSON line per configuration:
-    sweeps at each C (time per sweep and training RMSE after each, from the same initial
-    factors; C = K is ALS), then the row-assignment policies at the workload's C."""
+    sweeps at each C (time per sweep, training RMSE and the RMSE on 1% held-out entries
+    after each, from the same initial factors; C = K is ALS), then the row-assignment
+    policies at the workload's C."""
     import numpy as np
     import torch
     import paper_1410_5209_gb300 as tf
@@ -176,17 +177,25 @@ def study(args, rank, world):
     tfbuild.build()
     tf.load()
     K, lam = WORKLOAD["K"], WORKLOAD["lam"]
+    # 1% of the drawn entries are held out (never trained on) for the test RMSE
     p = synth.skewed_3way(seed=args.seed, nnz=args.nnz, device="cuda")
+    hold = max(1, p.nnz // 100)
+    train_c, train_x = p.coords[:-hold], p.x[:-hold]
+    test_c, test_x = p.coords[-hold:].contiguous(), p.x[-hold:].double()
     stream = torch.cuda.current_stream()
-    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+    f = tf.Factorization(train_c, train_x, p.dims, K, seed=args.seed, dtype=tf.F32,
                          stream=stream.cuda_stream, device_input=True)
     A0 = [a.numpy().astype(np.float32) for a in p.init_factors(torch.float64, "cpu")]
-    p_nnz = p.nnz
+    p_nnz = int(train_c.shape[0])
+
+    def test_rmse():
+        pred = f.predict(test_c).double()
+        return float(torch.sqrt(torch.mean((test_x - pred) ** 2)))
 
     def run(C, sweeps):
         for n in range(3):
             f.set_factors(n, A0[n])
-        times, rmses = [], []
+        times, rmses, tests = [], [], []
         for s in range(sweeps):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -196,25 +205,27 @@ def study(args, rank, world):
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
             rmses.append(f.loss(lam)[1])
-        return times, rmses
+            tests.append(test_rmse())
+        return times, rmses, tests
 
     for C in [int(c) for c in args.study_c.split(",")]:
         run(C, 1)  # warm-up (kernel selection, buffers)
-        times, rmses = run(C, args.study_sweeps)
+        times, rmses, tests = run(C, args.study_sweeps)
         ms = float(np.median(times))
         print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz, "ms_per_sweep": ms,
                           "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
-                          "sweep_ms": times, "train_rmse": rmses,
+                          "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
                           "pass_path": f.counters()["pass_path"]}), flush=True)
     C = WORKLOAD["C"]
     for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),
                       ("seq", tf.SCHED_SEQ), ("ran", tf.SCHED_RAN)):
         f.set_schedule(pol, 0)
         run(C, 1)
-        times, rmses = run(C, args.study_sweeps)
+        times, rmses, tests = run(C, args.study_sweeps)
         ms = float(np.median(times))
         print(json.dumps({"study": "schedule", "policy": name, "C": C, "ms_per_sweep": ms,
                           "nnz_rank_per_s": p_nnz * K / (ms / 1e3), "train_rmse": rmses,
+                          "test_rmse": tests,
                           "split_rows": f.counters()["split_rows"]}), flush=True)
     f.close()
     return 0
@@ -233,6 +244,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
     ap.add_argument("--foldin-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-batch", type=int, default=256)
     ap.add_argument("--study", action="store_true",
                     help="C-sweep and row-assignment policy study instead of the benchmark")
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
@@ -359,6 +373,34 @@ def main():
                          "entries_min": int(min(ms_sizes)), "entries_max": int(max(ms_sizes)),
                          "K": K, "what": "sequential tf_foldin calls: host request -> device "
                                          "Gram + Cholesky -> host row"}
+    # serving: Poisson arrivals of fold-in requests, continuous batching (every batch
+    # takes all requests that arrived while the previous one ran, up to --serve-batch);
+    # a virtual clock advances by the measured wall time of each tf_foldin_batch call
+    if args.serve_requests > 0:
+        reqs = synth.foldin_requests(p, args.serve_requests, args.seed + 29 + rank)
+        f.foldin_batch(0, reqs[:8], lam)   # warm-up
+        rng = np.random.default_rng(args.seed + 31)
+        arrive = np.cumsum(rng.exponential(1.0 / args.serve_rate, len(reqs)))
+        clock, nxt, lat, batches = 0.0, 0, np.zeros(len(reqs)), []
+        while nxt < len(reqs):
+            clock = max(clock, arrive[nxt])
+            end = nxt
+            while end < len(reqs) and arrive[end] <= clock and end - nxt < args.serve_batch:
+                end += 1
+            t0 = time.perf_counter()
+            _, status = f.foldin_batch(0, reqs[nxt:end], lam)
+            clock += time.perf_counter() - t0
+            assert not status.any()
+            lat[nxt:end] = clock - arrive[nxt:end]
+            batches.append(end - nxt)
+            nxt = end
+        out["serving"] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                          "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                          "req_per_s": len(reqs) / clock, "offered_req_per_s": args.serve_rate,
+                          "requests": len(reqs), "mean_batch": float(np.mean(batches)),
+                          "max_batch": args.serve_batch,
+                          "what": "Poisson fold-in arrivals, continuous batching through "
+                                  "tf_foldin_batch (latency = arrival -> rows on host)"}
     f.close()
     del f
 

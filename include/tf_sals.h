@@ -197,6 +197,18 @@ tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *val
  * coordinate is out of range (out is then unspecified). */
 tf_status tf_predict(tf_ctx *ctx, const int32_t *coords, int64_t m, void *out, uint32_t flags);
 
+/* Many fold-in requests of one mode in one batch (one launch of the tiled Gram over all
+ * of their entries, one warp-level solve per request): request r has the entries
+ * offsets[r] .. offsets[r + 1] - 1 of the concatenated other [total][N-1] and values
+ * [total] (host; offsets[n_req + 1] int64 with offsets[0] = 0, non-decreasing).
+ * out_rows [n_req][K] (host, context dtype); status [n_req] (host): 0 ok, 1 an index
+ * out of range, 2 a non-positive pivot — the row of a failed request is left untouched
+ * and the others are still solved.  Synchronises.  Results equal tf_foldin's per
+ * request (same blocks, same summation order). */
+tf_status tf_foldin_batch(tf_ctx *ctx, int mode, int n_req, const int64_t *offsets,
+                          const int32_t *other, const void *values, double lambda, void *out_rows,
+                          int32_t *status);
+
 /* ------------------------------------------------------------------ inspection */
 
 /* Row offsets off[I_n + 1] (int64) and, if perm != NULL, the canonical entry index of

@@ -73,6 +73,7 @@ def load():
         "tf_loss_noalloc": [P, f64, u32, P, P],
         "tf_foldin": [P, i32, P, P, i64, f64, P],
         "tf_predict": [P, P, i64, P, u32],
+        "tf_foldin_batch": [P, i32, i32, P, P, P, f64, P, P],
         "tf_get_grouping": [P, i32, P, P],
         "tf_get_residual": [P, P],
         "tf_get_counters": [P, P],
@@ -205,6 +206,24 @@ class Factorization:
                                               WEIGHTED_LAMBDA if weighted else 0,
                                               ctypes.byref(l), ctypes.byref(r)))
         return l.value, r.value
+
+    def foldin_batch(self, mode, requests, lam):
+        """Fold-in of many requests [(other [m][N-1], values [m])] in one batch: returns
+        (rows [n][K], status [n]) with status 0 ok, 1 bad index, 2 bad pivot."""
+        n = len(requests)
+        offs = np.zeros(n + 1, np.int64)
+        for r, (o, _) in enumerate(requests):
+            offs[r + 1] = offs[r] + len(o)
+        other = np.ascontiguousarray(np.concatenate([np.asarray(o, np.int32).reshape(-1, self.N - 1)
+                                                     for o, _ in requests]) if n else
+                                     np.zeros((0, self.N - 1), np.int32), np.int32)
+        vals = np.ascontiguousarray(np.concatenate([np.asarray(v) for _, v in requests]) if n else
+                                    np.zeros(0), self.npdt)
+        out = np.zeros((n, self.K), self.npdt)
+        status = np.zeros(n, np.int32)
+        self._check(self._lib.tf_foldin_batch(self._ctx, int(mode), n, _ptr(offs), _ptr(other),
+                                              _ptr(vals), float(lam), _ptr(out), _ptr(status)))
+        return out, status
 
     def predict(self, coords):
         """Model values at coordinates [m][N] (host arrays, or torch CUDA tensors)."""

@@ -97,6 +97,7 @@ struct Impl : CtxBase {
     Buf<int64_t> d_dims;
     Buf<int32_t> f_other;          // fold-in scratch
     Buf<T> f_x, f_out, f_part;
+    Buf<int64_t> f_meta;           // tiled fold-in block table / request offsets / status
     Buf<int32_t> p_coords;         // tf_predict staging
     Buf<T> p_out;
     int32_t *h_order = nullptr;    // pinned staging of the column order
@@ -896,7 +897,110 @@ struct Impl : CtxBase {
     }
 
     // ------------------------------------------------------------ fold-in
+    // Requests r = 0..n_req-1 with entries offsets[r] .. offsets[r + 1] of the
+    // concatenated (other, vals); out [n_req][K]; status[r] = 0 ok, 1 index out of range,
+    // 2 non-positive pivot (out row then untouched).
+    void foldin_batch(int md, int n_req, const int64_t *offsets, const int32_t *other,
+                      const T *vals, double lambda, T *out, int32_t *status) {
+        if (md < 0 || md >= N) throw ApiError{TF_EINVAL, "mode out of range"};
+        if (n_req < 0) throw ApiError{TF_EINVAL, "n_req must be >= 0"};
+        if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
+        if (n_req == 0) return;
+        if (offsets[0] != 0) throw ApiError{TF_EINVAL, "offsets[0] must be 0"};
+        for (int r = 0; r < n_req; ++r)
+            if (offsets[r + 1] < offsets[r]) throw ApiError{TF_EINVAL, "offsets must not decrease"};
+        const int64_t m = offsets[n_req];
+        if (!foldin_tiled_ok(K)) {  // one block per request
+            for (int r = 0; r < n_req; ++r) {
+                status[r] = 0;
+                try {
+                    foldin_one(md, other + offsets[r] * (N - 1), vals + offsets[r],
+                               offsets[r + 1] - offsets[r], lambda, out + (int64_t)r * K);
+                } catch (const ApiError &e) {
+                    if (e.status == TF_ERANGE || e.status == TF_EINVAL)
+                        status[r] = e.status == TF_ERANGE ? 1 : 2;
+                    else
+                        throw;
+                }
+            }
+            return;
+        }
+        std::vector<int64_t> blk_range;
+        std::vector<int32_t> blk_req, req_blk;
+        const int blocks = foldin_plan_blocks(offsets, n_req, blk_range, blk_req, req_blk);
+        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1));
+        f_x.ensure((size_t)std::max<int64_t>(m, 1));
+        f_out.ensure((size_t)n_req * K);
+        f_part.ensure(foldin_part_elems(K, blocks));
+        // one int64 staging buffer: block entry ranges [2B], then as int32 the blocks'
+        // requests [B], the requests' first blocks [n_req + 1] and their status [n_req]
+        const size_t B = (size_t)std::max(blocks, 1);
+        const size_t n32 = B + 2 * (size_t)n_req + 1;
+        const size_t n64 = 2 * B + (n32 + 1) / 2;
+        f_meta.ensure(n64);
+        std::vector<int64_t> meta(n64, 0);
+        std::copy(blk_range.begin(), blk_range.end(), meta.begin());
+        int32_t *m32 = reinterpret_cast<int32_t *>(meta.data() + 2 * B);
+        std::copy(blk_req.begin(), blk_req.end(), m32);
+        std::copy(req_blk.begin(), req_blk.end(), m32 + B);
+        int32_t *st_host = m32 + B + n_req + 1;
+        std::fill(st_host, st_host + n_req, 0);
+        if (m > 0) {
+            TFS_CUDA(cudaMemcpyAsync(f_other.p, other, (size_t)m * (N - 1) * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+            TFS_CUDA(cudaMemcpyAsync(f_x.p, vals, (size_t)m * sizeof(T), cudaMemcpyHostToDevice, st));
+        }
+        TFS_CUDA(cudaMemcpyAsync(f_meta.p, meta.data(), meta.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st));
+        const int32_t *d32 = reinterpret_cast<const int32_t *>(f_meta.p + 2 * B);
+        FoldArgs<T> a{};
+        a.N = N;
+        a.K = K;
+        a.mode = md;
+        for (int l = 0; l < N; ++l) {
+            a.A[l] = A[l].p;
+            a.I[l] = dims[l];
+        }
+        a.m = m;
+        a.other = f_other.p;
+        a.x = f_x.p;
+        a.lambda = (T)lambda;
+        a.out = f_out.p;
+        a.stat = stat.p;
+        a.part = f_part.p;
+        a.blk_range = f_meta.p;
+        a.blk_req = d32;
+        a.req_blk = d32 + B;
+        a.req_status = const_cast<int32_t *>(d32 + B + n_req + 1);
+        launch_foldin_tiled<T>(a, blocks, n_req, st);
+        std::vector<T> rows((size_t)n_req * K);
+        TFS_CUDA(cudaMemcpyAsync(status, a.req_status, (size_t)n_req * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaMemcpyAsync(rows.data(), f_out.p, rows.size() * sizeof(T),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+        // rows of requests that failed stay untouched
+        for (int r = 0; r < n_req; ++r)
+            if (status[r] == 0) std::copy(rows.begin() + (size_t)r * K, rows.begin() + (size_t)(r + 1) * K,
+                                          out + (size_t)r * K);
+    }
+
     void foldin(int md, const int32_t *other, const T *vals, int64_t m, double lambda, T *out) {
+        if (m < 0) throw ApiError{TF_EINVAL, "m must be >= 0"};
+        if (!foldin_tiled_ok(K) || m == 0) {
+            foldin_one(md, other, vals, m, lambda, out);
+            return;
+        }
+        const int64_t offs[2] = {0, m};
+        int32_t status = 0;
+        foldin_batch(md, 1, offs, other, vals, lambda, out, &status);
+        if (status & 1) throw ApiError{TF_ERANGE, "fold-in index out of range"};
+        if (status & 2) throw ApiError{TF_EINVAL, "fold-in system is not positive definite"};
+    }
+
+    // one request, one block (any K that fits the block's shared memory)
+    void foldin_one(int md, const int32_t *other, const T *vals, int64_t m, double lambda, T *out) {
         if (md < 0 || md >= N) throw ApiError{TF_EINVAL, "mode out of range"};
         if (m < 0) throw ApiError{TF_EINVAL, "m must be >= 0"};
         if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
@@ -927,14 +1031,7 @@ struct Impl : CtxBase {
         a.lambda = (T)lambda;
         a.out = f_out.p;
         a.stat = stat.p;
-        const int fb = foldin_blocks(K, m, num_sms);
-        if (fb > 0) {
-            f_part.ensure(foldin_part_elems(K, fb));
-            a.part = f_part.p;
-            launch_foldin_tiled<T>(a, fb, st);
-        } else {
-            launch_foldin<T>(a, st);
-        }
+        launch_foldin<T>(a, st);
         DeviceStatus s = read_status();
         const int fbits = s.bits & (kStatFoldRange | kStatFoldPivot);
         if (fbits) {
@@ -1190,6 +1287,18 @@ tf_status tf_foldin(tf_ctx *ctx, int mode, const int32_t *other, const void *val
     return dispatch(ctx, [&](auto &c) {
         using T = typename std::remove_reference<decltype(*c.x.p)>::type;
         c.foldin(mode, other, static_cast<const T *>(values), m, lambda, static_cast<T *>(out_row));
+    });
+}
+
+tf_status tf_foldin_batch(tf_ctx *ctx, int mode, int n_req, const int64_t *offsets,
+                          const int32_t *other, const void *values, double lambda, void *out_rows,
+                          int32_t *status) {
+    if (n_req < 0 || (n_req > 0 && (!offsets || !out_rows || !status))) return TF_EINVAL;
+    if (n_req > 0 && offsets[n_req] > 0 && (!other || !values)) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        using T = typename std::remove_reference<decltype(*c.x.p)>::type;
+        c.foldin_batch(mode, n_req, offsets, other, static_cast<const T *>(values), lambda,
+                       static_cast<T *>(out_rows), status);
     });
 }
 

@@ -121,17 +121,19 @@ __global__ void __launch_bounds__(kFoldThreads) k_foldin(const FoldArgs<T> a) {
         for (int q = tid; q < K; q += blockDim.x) a.out[q] = cv[q];
 }
 
-// Tiled fold-in for K < 128 (several blocks per request): block b takes entries
-// [b E, (b + 1) E); tiles of 32 entries build H' = [H | x] in shared memory (8 threads
-// per entry, columns strided by 8, one round of independent row loads), and a 16 x 16
-// grid of register tiles accumulates the lower triangle of H'^T H' (B and, in row K,
-// c).  Each block writes its partial; k_fold_solve sums them in block order and solves
-// with one warp.
+// Tiled fold-in for K < 128, any number of requests in one launch: block b takes the
+// entries blk_range[2b] .. blk_range[2b + 1] of request blk_req[b] (at most 256); tiles
+// of 32 entries build H' = [H | x] in shared memory (8 threads per entry, columns
+// strided by 8, one round of independent row loads), and a 16 x 16 grid of register
+// tiles accumulates the lower triangle of H'^T H' (B and, in row K, c).  Each block
+// writes its partial; k_fold_solve (one warp per request) sums the request's partials
+// in block order and solves.  Bad indices and non-positive pivots are flagged per
+// request in req_status (1 and 2).
 constexpr int kFoldTile = 32;
 constexpr int kFoldGramThreads = 256;
 
 template <class T, int CW>
-__global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T> a, int64_t E) {
+__global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T> a) {
     constexpr int R = CW / 16, HS = CW + 4;
     __shared__ __align__(16) T H[kFoldTile * HS];
     __shared__ int bad;
@@ -144,8 +146,7 @@ __global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T
     for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[i][j] = T(0);
-    const int64_t b0 = (int64_t)blockIdx.x * E;
-    const int64_t b1 = b0 + E < a.m ? b0 + E : a.m;
+    const int64_t b0 = a.blk_range[2 * blockIdx.x], b1 = a.blk_range[2 * blockIdx.x + 1];
     for (int64_t e0 = b0; e0 < b1; e0 += kFoldTile) {
         const int ne = (int)(b1 - e0 < kFoldTile ? b1 - e0 : kFoldTile);
         __syncthreads();
@@ -164,7 +165,9 @@ __global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T
                 rows[t++] = a.A[l] + (int64_t)(in ? idx : 0) * K;
             }
             if (valid && !ok) bad = 1;
-            for (int c = g; c < CW; c += 8) {
+#pragma unroll
+            for (int k = 0; k < CW / 8; ++k) {
+                const int c = g + 8 * k;
                 T hv = T(0);
                 if (ok && c < K) {
                     hv = T(1);
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T
         }
     }
     __syncthreads();
-    if (tid == 0 && bad) atomicOr(&a.stat->bits, kStatFoldRange);
+    if (tid == 0 && bad) atomicOr(&a.req_status[a.blk_req[blockIdx.x]], 1);
     const int NT = K * (K + 1) / 2;
     T *p = a.part + (int64_t)blockIdx.x * (NT + K);
     if (active) {
@@ -209,32 +212,46 @@ __global__ void __launch_bounds__(kFoldGramThreads) k_fold_gram(const FoldArgs<T
 }
 
 template <class T>
-__global__ void __launch_bounds__(32) k_fold_solve(const FoldArgs<T> a, int blocks) {
+__global__ void __launch_bounds__(32) k_fold_solve(const FoldArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int K = a.K, lane = threadIdx.x;
+    const int K = a.K, lane = threadIdx.x, r = blockIdx.x;
     const int NT = K * (K + 1) / 2, NB = NT + K;
     T *P = reinterpret_cast<T *>(smem_raw);
     T *cv = P + NT;
+    const int bb = a.req_blk[r], be = a.req_blk[r + 1];
     for (int q = lane; q < NB; q += 32) {
         T s = T(0);
-        for (int b = 0; b < blocks; ++b) s += a.part[(int64_t)b * NB + q];
+        for (int b = bb; b < be; ++b) s += a.part[(int64_t)b * NB + q];
         P[q] = s;  // cv follows P: q >= NT lands in cv[q - NT]
     }
     __syncwarp();
     const bool ok = warp_chol_solve<T>(P, cv, K, a.lambda, lane);
     if (!ok) {
-        if (lane == 0) atomicOr(&a.stat->bits, kStatFoldPivot);
+        if (lane == 0) atomicOr(&a.req_status[r], 2);
         return;
     }
-    for (int q = lane; q < K; q += 32) a.out[q] = cv[q];
+    for (int q = lane; q < K; q += 32) a.out[(int64_t)r * K + q] = cv[q];
 }
 
 }  // namespace
 
-int foldin_blocks(int K, int64_t m, int num_sms) {
-    if (K + 1 > 128 || m <= 0) return 0;
-    const int64_t b = (m + 255) / 256;
-    return (int)std::min<int64_t>(b, 2 * (int64_t)num_sms);
+bool foldin_tiled_ok(int K) { return K + 1 <= 128; }
+
+int foldin_plan_blocks(const int64_t *offsets, int n_req, std::vector<int64_t> &blk_range,
+                       std::vector<int32_t> &blk_req, std::vector<int32_t> &req_blk) {
+    blk_range.clear();
+    blk_req.clear();
+    req_blk.assign((size_t)n_req + 1, 0);
+    for (int r = 0; r < n_req; ++r) {
+        req_blk[r] = (int32_t)blk_req.size();
+        for (int64_t b = offsets[r]; b < offsets[r + 1]; b += 256) {
+            blk_range.push_back(b);
+            blk_range.push_back(std::min<int64_t>(b + 256, offsets[r + 1]));
+            blk_req.push_back(r);
+        }
+    }
+    req_blk[n_req] = (int32_t)blk_req.size();
+    return (int)blk_req.size();
 }
 
 size_t foldin_part_elems(int K, int blocks) {
@@ -242,20 +259,21 @@ size_t foldin_part_elems(int K, int blocks) {
 }
 
 template <class T>
-void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, cudaStream_t st) {
-    const int64_t E = (a.m + blocks - 1) / blocks;
+void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream_t st) {
     const int cw = a.K + 1 <= 32 ? 32 : (a.K + 1 <= 64 ? 64 : 128);
-    if (cw == 32)
-        k_fold_gram<T, 32><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
-    else if (cw == 64)
-        k_fold_gram<T, 64><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
-    else
-        k_fold_gram<T, 128><<<blocks, kFoldGramThreads, 0, st>>>(a, E);
-    TFS_CUDA(cudaGetLastError());
+    if (blocks > 0) {
+        if (cw == 32)
+            k_fold_gram<T, 32><<<blocks, kFoldGramThreads, 0, st>>>(a);
+        else if (cw == 64)
+            k_fold_gram<T, 64><<<blocks, kFoldGramThreads, 0, st>>>(a);
+        else
+            k_fold_gram<T, 128><<<blocks, kFoldGramThreads, 0, st>>>(a);
+        TFS_CUDA(cudaGetLastError());
+    }
     const size_t smem = sizeof(T) * ((size_t)a.K * (a.K + 1) / 2 + a.K);
     TFS_CUDA(cudaFuncSetAttribute(k_fold_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    k_fold_solve<T><<<1, 32, smem, st>>>(a, blocks);
+    k_fold_solve<T><<<n_req, 32, smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }
 
@@ -277,7 +295,7 @@ template size_t foldin_smem_bytes<float>(int);
 template size_t foldin_smem_bytes<double>(int);
 template void launch_foldin<float>(const FoldArgs<float> &, cudaStream_t);
 template void launch_foldin<double>(const FoldArgs<double> &, cudaStream_t);
-template void launch_foldin_tiled<float>(const FoldArgs<float> &, int, cudaStream_t);
-template void launch_foldin_tiled<double>(const FoldArgs<double> &, int, cudaStream_t);
+template void launch_foldin_tiled<float>(const FoldArgs<float> &, int, int, cudaStream_t);
+template void launch_foldin_tiled<double>(const FoldArgs<double> &, int, int, cudaStream_t);
 
 }  // namespace tfs

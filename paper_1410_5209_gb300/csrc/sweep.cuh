@@ -1,6 +1,8 @@
 // Kernel interfaces of one SALS sweep (sweep.cu) and of the fold-in (foldin.cu).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace tfs {
@@ -108,6 +110,13 @@ struct FoldArgs {
     T *out;
     DeviceStatus *stat;
     T *part;      // [blocks][K (K + 1) / 2 + K] partial Gram / rhs of the tiled fold-in
+    // tiled fold-in of a batch: per block its entry range and request, per request its
+    // first block (n_req + 1), per request a status word (1 bad index, 2 bad pivot);
+    // out is then [n_req][K]
+    const int64_t *blk_range;
+    const int32_t *blk_req;
+    const int32_t *req_blk;
+    int32_t *req_status;
 };
 
 constexpr int kPassThreads = 128;
@@ -200,12 +209,14 @@ struct PredictArgs {
 };
 template <class T>
 void launch_predict(const PredictArgs<T> &a, cudaStream_t st);
-// Blocks of the tiled fold-in for a request of m entries (0: the one-block kernel),
-// and its partial buffer length in elements.
-int foldin_blocks(int K, int64_t m, int num_sms);
+// Tiled fold-in (K < 128): block table of a batch of requests (offsets[n_req + 1] into
+// the concatenated entries; 256 entries per block), partial buffer length, launch.
+bool foldin_tiled_ok(int K);
+int foldin_plan_blocks(const int64_t *offsets, int n_req, std::vector<int64_t> &blk_range,
+                       std::vector<int32_t> &blk_req, std::vector<int32_t> &req_blk);
 size_t foldin_part_elems(int K, int blocks);
 template <class T>
-void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, cudaStream_t st);
+void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream_t st);
 template <class T>
 size_t foldin_smem_bytes(int K);
 

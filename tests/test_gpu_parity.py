@@ -540,3 +540,36 @@ def test_predict_matches_model(dtype, tol):
         f.predict(bad)
     assert e.value.status == tf.ERANGE
     assert np.allclose(f.predict(held), got)
+
+
+@pytest.mark.parametrize("dtype,tol", [(tf.F64, 1e-9), (tf.F32, 1e-4)])
+def test_foldin_batch(dtype, tol):
+    """A batch of requests of mixed sizes in one launch: each row equals the single
+    request's (bit for bit: same blocks, same order) and the oracle's; a request with a
+    bad index or a singular system is flagged alone and its row left untouched."""
+    p = synth.small(44, (60, 2000, 300), 40_000, 6, 100)
+    f, t, A = make(p, dtype)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for m in (1, 300, 0, 5_000, 17, 2_600):
+        other = np.stack([rng.integers(0, 2000, m), rng.integers(0, 300, m)], 1).astype(np.int32)
+        x = rng.standard_normal(m)
+        if dtype == tf.F32:
+            x = x.astype(np.float32).astype(np.float64)
+        reqs.append((other, x))
+    bad = reqs[1][0].copy()
+    bad[5, 0] = 2000
+    reqs.append((bad, reqs[1][1]))
+    rows, status = f.foldin_batch(0, reqs, 0.7)
+    assert list(status) == [0, 0, 0, 0, 0, 0, 1]
+    assert not rows[-1].any()
+    for r, (other, x) in enumerate(reqs[:-1]):
+        ref, st = oracle.foldin(A, 0, other, x, 0.7)
+        assert st == 0
+        assert rel(rows[r].astype(np.float64), ref) < tol or np.linalg.norm(ref) < 1e-12
+        assert np.array_equal(rows[r], f.foldin(0, other, x, 0.7))
+    # lambda = 0: the empty request is singular, the 5,000-entry one is not
+    rows0, status0 = f.foldin_batch(0, [reqs[2], reqs[3]], 0.0)
+    assert list(status0) == [2, 0]
+    ref, st = oracle.foldin(A, 0, reqs[3][0], reqs[3][1], 0.0)
+    assert st == 0 and rel(rows0[1].astype(np.float64), ref) < 100 * tol
