@@ -217,8 +217,11 @@ def study(args, rank, world):
                           "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
                           "pass_path": f.counters()["pass_path"]}), flush=True)
     C = WORKLOAD["C"]
+    policies = [q for q in args.study_policies.split(",") if q]
     for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),
                       ("seq", tf.SCHED_SEQ), ("ran", tf.SCHED_RAN)):
+        if name.split("_")[0] not in policies:
+            continue
         f.set_schedule(pol, 0)
         run(C, 1)
         times, rmses, tests = run(C, args.study_sweeps)
@@ -251,6 +254,7 @@ def main():
                     help="C-sweep and row-assignment policy study instead of the benchmark")
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
     ap.add_argument("--study-sweeps", type=int, default=3)
+    ap.add_argument("--study-policies", default="lpt,greedy,seq,ran")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.study:
