@@ -300,6 +300,47 @@ def foldin_requests(p, count, seed, mode=0, m_min=10, m_max=10_000, noise_std=0.
     return out
 
 
+def concat_block_diagonal(problems, K, seed):
+    """Independent tensors (same N) as one block-diagonal tensor: tensor b's indices of
+    mode n are shifted by the summed mode-n lengths of the tensors before it, so no
+    entry couples two tensors.  Returns (Problem, row_offsets [count + 1][N],
+    entry_offsets [count + 1])."""
+    N = problems[0].N
+    count = len(problems)
+    row_off = np.zeros((count + 1, N), np.int64)
+    ent_off = np.zeros(count + 1, np.int64)
+    for b, q in enumerate(problems):
+        row_off[b + 1] = row_off[b] + np.asarray(q.dims, np.int64)
+        ent_off[b + 1] = ent_off[b] + q.nnz
+    dev = problems[0].coords.device
+    shift = torch.from_numpy(row_off[:-1].astype(np.int32)).to(dev)
+    coords = torch.cat([q.coords + shift[b] for b, q in enumerate(problems)])
+    x = torch.cat([q.x for q in problems])
+    truth = None
+    if all(q.truth is not None for q in problems) and \
+            len({q.truth[0].shape[1] for q in problems}) == 1:
+        truth = [torch.cat([q.truth[n] for q in problems]) for n in range(N)]
+    p = Problem([int(d) for d in row_off[-1]], coords, x, K, seed, truth)
+    return p, row_off, ent_off
+
+
+def batched(count, seed=4, dims_range=(50, 5000), nnz_range=(1_000, 1_000_000), rank=16,
+            K=16, dtype=torch.float32, device="cpu"):
+    """Many small 3-way tensors: per tensor, mode lengths and entry counts log-uniform in
+    the given ranges (entries capped at half the cells), rank-`rank` ground truth with
+    unit signal variance plus N(0, 0.1^2) noise; concatenated block-diagonally."""
+    u = uniform01(seed, 800, 0, 4 * count).reshape(count, 4)
+    lo_d, hi_d = math.log(dims_range[0]), math.log(dims_range[1])
+    lo_n, hi_n = math.log(nnz_range[0]), math.log(nnz_range[1])
+    probs = []
+    for b in range(count):
+        dims = [int(math.exp(lo_d + float(u[b, n]) * (hi_d - lo_d))) for n in range(3)]
+        nnz = int(math.exp(lo_n + float(u[b, 3]) * (hi_n - lo_n)))
+        probs.append(make_problem(dims, nnz, rank, K, seed * 100_003 + b, dtype=dtype,
+                                  device=device))
+    return concat_block_diagonal(probs, K, seed)
+
+
 def small(seed, dims, nnz, rank, K, noise_std=0.1, modes=None, dtype=torch.float64,
           device="cpu"):
     """Small tensors for tests (any shape)."""
