@@ -573,3 +573,54 @@ def test_foldin_batch(dtype, tol):
     assert list(status0) == [2, 0]
     ref, st = oracle.foldin(A, 0, reqs[3][0], reqs[3][1], 0.0)
     assert st == 0 and rel(rows0[1].astype(np.float64), ref) < 100 * tol
+
+
+# --------------------------------------------------------------------------- more shapes
+
+
+@pytest.mark.parametrize("N,C,K", [(2, 20, 24), (4, 18, 18), (5, 33, 40), (5, 3, 7)])
+def test_wide_and_narrow_other_orders(N, C, K):
+    """Tensor orders 2, 4 and 5 on the wide path (C > 16; the generic mode loop) and on the
+    narrow path with N = 5, FP64 against the oracle over two sweeps with T_in = 2."""
+    dims = {2: (300, 250), 4: (40, 30, 20, 25), 5: (12, 9, 11, 8, 10)}[N]
+    p = synth.small(120 + N + C, dims, 6_000, 2, K)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.4, 2, order)
+        oracle.sals_sweep(t, A, r, C, 0.4, 2, order)
+    for n in range(N):
+        assert rel(f.factors(n), A[n]) < 1e-9
+    assert rel(f.residual(), r) < 1e-9
+
+
+def test_wide_empty_tensor_and_predict_order_four():
+    f = tf.Factorization(np.zeros((0, 3), np.int32), np.zeros(0), [5, 4, 3], 40, dtype=tf.F64)
+    f.sweep(20, 1.0, 1)
+    assert np.all(f.factors(1) == 0)
+    assert f.loss(1.0) == (0.0, 0.0)
+    p = synth.small(130, (40, 30, 20, 25), 5_000, 2, 6)
+    g, t, A = make(p, tf.F64)
+    g.sweep(3, 0.4, 1, p.column_order(0, 3))
+    A_dev = [g.factors(n) for n in range(4)]
+    ref = -oracle.residual(oracle.Tensor(t.coords[:100], np.zeros(100), p.dims), A_dev)
+    assert np.max(np.abs(g.predict(t.coords[:100]) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_foldin_wide_k_single_block():
+    """K >= 128 takes the one-block fold-in (single request and in a batch)."""
+    p = synth.small(131, (30, 400, 300), 20_000, 4, 130)
+    f, t, A = make(p, tf.F64)
+    rng = np.random.default_rng(4)
+    reqs = []
+    for m in (200, 0, 1_000):
+        other = np.stack([rng.integers(0, 400, m), rng.integers(0, 300, m)], 1).astype(np.int32)
+        reqs.append((other, rng.standard_normal(m)))
+    rows, status = f.foldin_batch(0, reqs, 0.9)
+    assert list(status) == [0, 0, 0]
+    for r, (other, x) in enumerate(reqs):
+        ref, st = oracle.foldin(A, 0, other, x, 0.9)
+        assert st == 0
+        assert rel(rows[r], ref) < 1e-9 or np.linalg.norm(ref) < 1e-12
+        assert rel(f.foldin(0, other, x, 0.9), ref) < 1e-9 or np.linalg.norm(ref) < 1e-12
