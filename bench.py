@@ -210,13 +210,17 @@ def study(args, rank, world):
         return times, rmses, tests
 
     for C in [int(c) for c in args.study_c.split(",")]:
-        run(C, 1)  # warm-up (kernel selection, buffers)
-        times, rmses, tests = run(C, args.study_sweeps)
-        ms = float(np.median(times))
-        print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz, "ms_per_sweep": ms,
-                          "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
-                          "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
-                          "pass_path": f.counters()["pass_path"]}), flush=True)
+        for prec in ((0, 1) if C > 16 else (0,)):
+            f.set_precision(prec)
+            run(C, 1)  # warm-up (kernel selection, buffers)
+            times, rmses, tests = run(C, args.study_sweeps)
+            ms = float(np.median(times))
+            print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz, "ms_per_sweep": ms,
+                              "precision": ["fp32", "tf32x1"][prec],
+                              "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
+                              "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
+                              "pass_path": f.counters()["pass_path"]}), flush=True)
+        f.set_precision(0)
     C = WORKLOAD["C"]
     policies = [q for q in args.study_policies.split(",") if q]
     for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),

@@ -241,6 +241,15 @@ tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
  * results; the tensor-core Gram agrees with the SIMT one to FP32 rounding. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
+/* Precision of the Gram matrix of wide subsets (16 < C < 128) in float contexts:
+ * 0 = FP32-level (default; on the tensor cores three TF32 products per term), 1 = the
+ * reduced-precision form, one TF32 product per term on the tensor cores for every wide
+ * C (B and c carry about 1e-3 relative error, so a row update differs from the FP32
+ * one by about cond(B + lambda I) * 1e-3; the training RMSE after a few sweeps stays
+ * within 1e-3 of the FP64 oracle's on the tested workloads).  C <= 16 is unaffected.
+ * TF_EINVAL for mode 1 on a double context. */
+tf_status tf_set_precision(tf_ctx *ctx, int mode);
+
 /* ------------------------------------------------------------------ timing */
 
 /* Kernel kinds reported by tf_get_profile. */

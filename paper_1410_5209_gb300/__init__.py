@@ -79,6 +79,7 @@ def load():
         "tf_get_counters": [P, P],
         "tf_set_schedule": [P, i32, i32],
         "tf_set_kernel_path": [P, i32],
+        "tf_set_precision": [P, i32],
         "tf_profile": [P, i32],
         "tf_get_profile": [P, P, P],
         "tf_get_launch_trace": [P, i64, P, P, P, P],
@@ -285,6 +286,10 @@ class Factorization:
 
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
+
+    def set_precision(self, mode):
+        """0: FP32-level Gram; 1: single-TF32 tensor-core Gram for wide subsets."""
+        self._check(self._lib.tf_set_precision(self._ctx, int(mode)))
 
     def set_schedule(self, policy=SCHED_LPT, P=0):
         self._check(self._lib.tf_set_schedule(self._ctx, int(policy), int(P)))

@@ -114,6 +114,7 @@ struct Impl : CtxBase {
     double prof_ms[TF_KIND_COUNT] = {0};
 
     int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported
+    int precision = 0;             // 0 FP32-level Gram, 1 single-TF32 tensor-core Gram (wide C)
     CUtensorMap tmaps[kMaxModes][3];  // per mode: slice maps with boxes 8, 24, 40 floats
     const void *tmaps_for_Z[kMaxModes] = {nullptr};
     int Cq = 0, CM_last = 1;       // columns Q held by the copies' R-hat; register width
@@ -580,12 +581,13 @@ struct Impl : CtxBase {
                         // float: the tensor-core Gram where it measures faster (the
                         // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
                         const bool tc = sizeof(T) == 4 && path != 1 &&
-                                        (path == 2 || wide_split_width(Cs, CM) == 128);
+                                        (path == 2 || precision == 1 ||
+                                         wide_split_width(Cs, CM) == 128);
                         const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
                         // every block takes one ticket past the last bin
                         ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
                         timed(TF_KIND_MODE_PASS,
-                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, st); });
+                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, precision == 0, st); });
                         last_path |= tc ? 4 : 1;
                         ++launches;
                         if (L.n_single > 0) {
@@ -1340,6 +1342,15 @@ tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kin
                               int32_t *modes, float *ms) {
     if (!n || cap < 0) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) { c.launch_trace(cap, n, kinds, modes, ms); });
+}
+
+tf_status tf_set_precision(tf_ctx *ctx, int mode) {
+    if (mode < 0 || mode > 1) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        if (mode == 1 && sizeof(*c.x.p) != 4)
+            throw tfs::ApiError{TF_EINVAL, "the reduced-precision Gram needs a float context"};
+        c.precision = mode;
+    });
 }
 
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {

@@ -147,9 +147,10 @@ int wide_tile_width(int C);
 int wide_split_width(int C, int CM);
 template <class T>
 int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first);
-// tensor_cores: float contexts only (tcgen05 3xTF32 Gram); otherwise SIMT FMAs.
+// tensor_cores: float contexts only (tcgen05 Gram; split = three TF32 products per term,
+// else one); otherwise SIMT FMAs.
 template <class T>
-void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores,
+void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores, bool split,
                       cudaStream_t st);
 template <class T>
 void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,

@@ -243,7 +243,9 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int CW, bool FIRST>
+// SPLIT: three TF32 products per term (FP32-level accuracy); without it one TF32
+// product (about 1e-3 relative error in B and c, the reduced-precision form).
+template <int CW, bool FIRST, bool SPLIT>
 __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<float> a, int CM, int W) {
     using T = float;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -338,7 +340,8 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                             const int off = (c >> 3) * kTcSbo + eoff + (c & 7) * 16;
                             const uint32_t hb = tf32_bits(hv);
                             *reinterpret_cast<uint32_t *>(ahi + off) = hb;
-                            *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(hv - __uint_as_float(hb));
+                            if (SPLIT)
+                                *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(hv - __uint_as_float(hb));
                         });
 #pragma unroll
                     for (int o = 4; o > 0; o >>= 1) {
@@ -354,7 +357,8 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                         const int off = (C >> 3) * kTcSbo + eoff + (C & 7) * 16;
                         const uint32_t hb = tf32_bits(v);
                         *reinterpret_cast<uint32_t *>(ahi + off) = hb;
-                        *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(v - __uint_as_float(hb));
+                        if (SPLIT)
+                            *reinterpret_cast<uint32_t *>(alo + off) = tf32_bits(v - __uint_as_float(hb));
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                         const uint64_t dh = tc_desc(ahi + k * 256), dl = tc_desc(alo + k * 256);
                         const uint64_t A[3] = {dh, dh, dl}, B[3] = {dh, dl, dh};
 #pragma unroll
-                        for (int u = 0; u < 3; ++u) {
+                        for (int u = 0; u < (SPLIT ? 3 : 1); ++u) {
                             const uint32_t acc = (first_tile && k == 0 && u == 0) ? 0u : 1u;
                             asm volatile(
                                 "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
@@ -522,13 +526,15 @@ __global__ void __launch_bounds__(kWideThreads) k_res_wide(const ResArgs<T> a, i
 }
 
 template <int CW>
-void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, cudaStream_t st) {
+void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, bool split,
+                            cudaStream_t st) {
     // at least 48 KB of shared memory per block keeps at most four blocks (4 x 128 tensor
     // memory columns) on an SM, so no allocation ever waits
     size_t smem = 2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + kWideTile) +
                   sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
     smem = std::max<size_t>(smem, 48 * 1024);
-    auto kern = a.first ? k_pass_wide_tc<CW, true> : k_pass_wide_tc<CW, false>;
+    auto kern = split ? (a.first ? k_pass_wide_tc<CW, true, true> : k_pass_wide_tc<CW, false, true>)
+                      : (a.first ? k_pass_wide_tc<CW, true, false> : k_pass_wide_tc<CW, false, false>);
     TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
     TFS_CUDA(cudaGetLastError());
@@ -580,19 +586,19 @@ int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool fi
 }
 
 template <class T>
-void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores,
+void launch_pass_wide(const PassArgs<T> &a, int CM, int W, int grid, bool tensor_cores, bool split,
                       cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (tensor_cores) {
             switch (wide_split_width(a.C, CM)) {
                 case 32:
-                    launch_pass_wide_tc_cw<32>(a, CM, W, grid, st);
+                    launch_pass_wide_tc_cw<32>(a, CM, W, grid, split, st);
                     return;
                 case 64:
-                    launch_pass_wide_tc_cw<64>(a, CM, W, grid, st);
+                    launch_pass_wide_tc_cw<64>(a, CM, W, grid, split, st);
                     return;
                 case 128:
-                    launch_pass_wide_tc_cw<128>(a, CM, W, grid, st);
+                    launch_pass_wide_tc_cw<128>(a, CM, W, grid, split, st);
                     return;
                 default:
                     throw ApiError{TF_EINVAL, "C >= 128 is not supported"};
@@ -640,7 +646,8 @@ void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st) {
 
 #define TFS_INST(T)                                                                           \
     template int pass_wide_grid<T>(int, int, int, int, bool, bool);                           \
-    template void launch_pass_wide<T>(const PassArgs<T> &, int, int, int, bool, cudaStream_t); \
+    template void launch_pass_wide<T>(const PassArgs<T> &, int, int, int, bool, bool,          \
+                                      cudaStream_t);                                          \
     template void launch_solve_wide<T>(const PassArgs<T> &, const SplitRow *, int, int, int,  \
                                        cudaStream_t);                                         \
     template void launch_res_wide<T>(const ResArgs<T> &, int, cudaStream_t);

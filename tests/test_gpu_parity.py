@@ -624,3 +624,27 @@ def test_foldin_wide_k_single_block():
         assert st == 0
         assert rel(rows[r], ref) < 1e-9 or np.linalg.norm(ref) < 1e-12
         assert rel(f.foldin(0, other, x, 0.9), ref) < 1e-9 or np.linalg.norm(ref) < 1e-12
+
+
+@pytest.mark.parametrize("C,K", [(20, 40), (70, 100)])
+def test_reduced_precision_gram(C, K):
+    """tf_set_precision(1): one TF32 product per Gram term on the tensor cores.  Stated
+    error: training RMSE after three sweeps within 1e-3 of the FP64 oracle's; factors
+    within 5e-2 normwise (a row moves by about cond(B + lambda I) * 1e-3)."""
+    p = synth.small(140 + C, (301, 157, 97), 15_000, 4, K)
+    f, t, A = make(p, tf.F32)
+    f.set_precision(1)
+    r = oracle.residual(t, A)
+    for s in range(3):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.3, 1, order)
+        oracle.sals_sweep(t, A, r, C, 0.3, 1, order)
+    assert f.counters()["pass_path"] & 4
+    _, rmse = f.loss(0.3)
+    _, rmseo = oracle.loss(t, r, A, 0.3)
+    assert abs(rmse - rmseo) <= 1e-3 * rmseo
+    for n in range(3):
+        assert rel(f.factors(n).astype(np.float64), A[n]) < 5e-2
+    g, _, _ = make(p, tf.F64)
+    with pytest.raises(tf.TFError):
+        g.set_precision(1)
