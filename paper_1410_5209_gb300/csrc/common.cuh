@@ -103,8 +103,6 @@ void launch_transpose_check(const int32_t *coords_rowmajor, int N, int64_t nnz,
 void launch_iota(int32_t *p, int64_t n, cudaStream_t st);
 void launch_gather_keys(const int32_t *col, const int32_t *perm, uint32_t *keys, int64_t n,
                         cudaStream_t st);
-void launch_gather_i32(const int32_t *col, const int32_t *perm, int32_t *out, int64_t n,
-                       cudaStream_t st);
 // out[i] = rank[col[perm[i]]]
 void launch_gather_rank(const int32_t *col, const int32_t *perm, const int32_t *rank, int32_t *out,
                         int64_t n, cudaStream_t st);

@@ -42,11 +42,6 @@ bool tma_pass_supported(int CM, int N) {
     return N == 3 && CM <= 10 && slice_stride_elems(CM, 4) == 32;
 }
 
-int tma_box_for(int CM, bool first, bool before_n) {
-    const int need = !first ? CM : (before_n ? 3 * CM : 2 * CM);
-    return tma_box(need);
-}
-
 namespace {
 
 template <int CM>

@@ -164,12 +164,6 @@ __global__ void k_gather_keys(const int32_t *__restrict__ col, const int32_t *__
     if (i < n) keys[i] = (uint32_t)col[perm[i]];
 }
 
-__global__ void k_gather_i32(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
-                             int32_t *__restrict__ out, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = col[perm[i]];
-}
-
 __global__ void k_gather_rank(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
                               const int32_t *__restrict__ rank, int32_t *__restrict__ out,
                               int64_t n) {
@@ -306,13 +300,6 @@ void launch_gather_keys(const int32_t *col, const int32_t *perm, uint32_t *keys,
                         cudaStream_t st) {
     if (n <= 0) return;
     k_gather_keys<<<grid_for(n, 256), 256, 0, st>>>(col, perm, keys, n);
-    TFS_CUDA(cudaGetLastError());
-}
-
-void launch_gather_i32(const int32_t *col, const int32_t *perm, int32_t *out, int64_t n,
-                       cudaStream_t st) {
-    if (n <= 0) return;
-    k_gather_i32<<<grid_for(n, 256), 256, 0, st>>>(col, perm, out, n);
     TFS_CUDA(cudaGetLastError());
 }
 

@@ -121,7 +121,6 @@ struct FoldArgs {
 
 constexpr int kPassThreads = 128;
 constexpr int kCombineThreads = 512;
-constexpr int kMaxCSimt = 16;
 
 int pick_cm(int C);  // smallest instantiated register width >= C (0 if none); C > 16
                      // takes the wide path (wide.cu) with CM = C rounded up to 4
@@ -221,13 +220,11 @@ void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream
 template <class T>
 size_t foldin_smem_bytes(int K);
 
-inline int pass_blocks(int P) { return (P * kWarp + kPassThreads - 1) / kPassThreads; }
 
 // TMA-fed mode pass (float, N = 3, CM <= 10; tma_pass.cuh).  A plan fixes the gather
 // box width per other mode, the rows of each other mode's slice held in the block's
 // shared-memory cache, and the warps per block (one block per SM).
 bool tma_pass_supported(int CM, int N);
-int tma_box_for(int CM, bool first, bool before_n);
 struct TmaPlan {
     int warps = 0, grid = 0;
     int box[2] = {0, 0};
