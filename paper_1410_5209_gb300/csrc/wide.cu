@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *H = reinterpret_cast<T *>(smem_raw);           // [kWideTile][HS]
     T *own = H + kWideTile * HS;                       // prev | old of the own row (2 CM)
-    T *s_res = own + 2 * CM;                           // [kWideTile]
-    int32_t *s_idx = reinterpret_cast<int32_t *>(s_res + kWideTile);  // [no][kWideTile]
+    T *s_res2 = own + 2 * CM;                          // [2][kWideTile]
+    int32_t *s_idx2 = reinterpret_cast<int32_t *>(s_res2 + 2 * kWideTile);  // [2][no][kWideTile]
     __shared__ unsigned long long s_tk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ty = tid >> 4, tx = tid & 15;
@@ -106,20 +106,39 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
                 const T *z = a.Zn + (int64_t)a.rank_n[item.row] * W;
                 for (int q = tid; q < 2 * CM; q += kWideThreads) own[q] = z[CM + q];
             }
+            int buf = 0;
             for (int64_t j0 = item.begin; j0 < item.begin + item.len; j0 += kWideTile) {
                 const int64_t left = item.begin + item.len - j0;
                 const int ne = left < kWideTile ? (int)left : kWideTile;
-                __syncthreads();  // H, the tile's indices and own are free to be rewritten
-                for (int q = tid; q < kWideTile * (no + 1); q += kWideThreads) {
-                    const int t = q / kWideTile, e = q - t * kWideTile;
-                    if (e < ne) {
-                        if (t < no)
-                            s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
-                        else
-                            s_res[e] = a.res[j0 + e];
+                __syncthreads();  // H and own are free; this tile's indices are staged
+                int32_t *s_idx = s_idx2 + buf * (kMaxModes - 1) * kWideTile;
+                T *s_res = s_res2 + buf * kWideTile;
+                if (j0 == item.begin) {  // the item's first tile: its indices now
+                    if (tid < kWideTile * (no + 1)) {
+                        const int t = tid / kWideTile, e = tid - t * kWideTile;
+                        if (e < ne) {
+                            if (t < no)
+                                s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
+                            else
+                                s_res[e] = a.res[j0 + e];
+                        }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
+                // the next tile's indices and residuals: loaded now, stored after this
+                // tile's Gram, so their latency hides behind the work on this tile
+                const int64_t j1 = j0 + kWideTile, left1 = item.begin + item.len - j1;
+                const int ne1 = left1 <= 0 ? 0 : (left1 < kWideTile ? (int)left1 : kWideTile);
+                const int pq_t = tid / kWideTile, pq_e = tid - pq_t * kWideTile;
+                const bool pre = tid < kWideTile * (no + 1) && pq_e < ne1;
+                int32_t pre_i = 0;
+                T pre_r = T(0);
+                if (pre) {
+                    if (pq_t < no)
+                        pre_i = a.oidx[pq_t][j1 + pq_e];
+                    else
+                        pre_r = a.res[j1 + pq_e];
+                }
                 {   // 8 lanes per entry, columns g, g + 8, ...: one round of independent loads
                     const int e = tid >> 3, g = tid & 7;
                     const bool valid = e < ne;
@@ -163,6 +182,13 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide(const PassArgs<T> a,
                             for (int j = 0; j < R; ++j) acc[i][j] += x[i] * y[j];
                     }
                 }
+                if (pre) {
+                    if (pq_t < no)
+                        s_idx2[(buf ^ 1) * (kMaxModes - 1) * kWideTile + pq_t * kWideTile + pq_e] = pre_i;
+                    else
+                        s_res2[(buf ^ 1) * kWideTile + pq_e] = pre_r;
+                }
+                buf ^= 1;
             }
             // item end: lower triangle of B (rows/cols < C) and c = row C of H'^T H'
             T *p = a.partials + (int64_t)item.slot * (CM * (CM + 1) / 2 + CM);
@@ -252,8 +278,8 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
     // kTcStages operand stages (hi and lo copies each)
     unsigned char *stage0 = smem_raw;
     T *own = reinterpret_cast<T *>(smem_raw + 2 * kTcStages * kTcBuf);  // prev | old (2 CM)
-    T *s_res = own + 2 * CM;                                   // [kWideTile]
-    int32_t *s_idx = reinterpret_cast<int32_t *>(s_res + kWideTile);
+    T *s_res2 = own + 2 * CM;                                  // [2][kWideTile]
+    int32_t *s_idx2 = reinterpret_cast<int32_t *>(s_res2 + 2 * kWideTile);  // [2][no][kWideTile]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t s_taddr;
     __shared__ unsigned long long s_tk;
@@ -304,6 +330,7 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                 for (int q = tid; q < 2 * CM; q += kWideThreads) own[q] = z[CM + q];
             }
             bool first_tile = true;
+            int buf = 0;
             for (int64_t j0 = item.begin; j0 < item.begin + item.len; j0 += kWideTile) {
                 const int64_t left = item.begin + item.len - j0;
                 const int ne = left < kWideTile ? (int)left : kWideTile;
@@ -316,16 +343,34 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                     timed_out = true;
                     break;
                 }
-                for (int q = tid; q < kWideTile * (no + 1); q += kWideThreads) {
-                    const int t = q / kWideTile, e = q - t * kWideTile;
-                    if (e < ne) {
-                        if (t < no)
-                            s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
-                        else
-                            s_res[e] = a.res[j0 + e];
+                int32_t *s_idx = s_idx2 + buf * (kMaxModes - 1) * kWideTile;
+                T *s_res = s_res2 + buf * kWideTile;
+                if (j0 == item.begin) {  // the item's first tile: its indices now
+                    if (tid < kWideTile * (no + 1)) {
+                        const int t = tid / kWideTile, e = tid - t * kWideTile;
+                        if (e < ne) {
+                            if (t < no)
+                                s_idx[t * kWideTile + e] = a.oidx[t][j0 + e];
+                            else
+                                s_res[e] = a.res[j0 + e];
+                        }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
+                // the next tile's indices and residuals: loaded now, stored after this
+                // tile's Gram, so their latency hides behind the work on this tile
+                const int64_t j1 = j0 + kWideTile, left1 = item.begin + item.len - j1;
+                const int ne1 = left1 <= 0 ? 0 : (left1 < kWideTile ? (int)left1 : kWideTile);
+                const int pq_t = tid / kWideTile, pq_e = tid - pq_t * kWideTile;
+                const bool pre = tid < kWideTile * (no + 1) && pq_e < ne1;
+                int32_t pre_i = 0;
+                T pre_r = T(0);
+                if (pre) {
+                    if (pq_t < no)
+                        pre_i = a.oidx[pq_t][j1 + pq_e];
+                    else
+                        pre_r = a.res[j1 + pq_e];
+                }
                 {
                     const int e = tid >> 3, g = tid & 7;
                     const bool valid = e < ne;
@@ -384,6 +429,13 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                             tc_saddr(&mbar[st]))
                         : "memory");
                 }
+                if (pre) {
+                    if (pq_t < no)
+                        s_idx2[(buf ^ 1) * (kMaxModes - 1) * kWideTile + pq_t * kWideTile + pq_e] = pre_i;
+                    else
+                        s_res2[(buf ^ 1) * kWideTile + pq_e] = pre_r;
+                }
+                buf ^= 1;
                 pending[st] = true;
                 ++tiles;
                 first_tile = false;
@@ -530,8 +582,8 @@ void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, b
                             cudaStream_t st) {
     // at least 48 KB of shared memory per block keeps at most four blocks (4 x 128 tensor
     // memory columns) on an SM, so no allocation ever waits
-    size_t smem = 2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + kWideTile) +
-                  sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
+    size_t smem = 2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + 2 * kWideTile) +
+                  sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
     smem = std::max<size_t>(smem, 48 * 1024);
     auto kern = split ? (a.first ? k_pass_wide_tc<CW, true, true> : k_pass_wide_tc<CW, false, true>)
                       : (a.first ? k_pass_wide_tc<CW, true, false> : k_pass_wide_tc<CW, false, false>);
@@ -542,8 +594,8 @@ void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, b
 
 template <class T, int CW>
 void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStream_t st) {
-    const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM + kWideTile) +
-                        sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
+    const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM + 2 * kWideTile) +
+                        sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
     auto kern = a.first ? k_pass_wide<T, CW, true> : k_pass_wide<T, CW, false>;
     TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
@@ -569,8 +621,8 @@ int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool fi
     int per_sm = 4;
     if (!(sizeof(T) == 4 && tensor_cores)) {
         const int cw = wide_split_width(C, CM);
-        const size_t smem = sizeof(T) * ((size_t)kWideTile * (cw + 4) + 2 * (size_t)CM + kWideTile) +
-                            sizeof(int32_t) * (size_t)kWideTile * (kMaxModes - 1);
+        const size_t smem = sizeof(T) * ((size_t)kWideTile * (cw + 4) + 2 * (size_t)CM + 2 * kWideTile) +
+                            sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
         const void *kern = nullptr;
         if (cw == 32)
             kern = first ? (const void *)k_pass_wide<T, 32, true> : (const void *)k_pass_wide<T, 32, false>;
