@@ -45,13 +45,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     constexpr int kWarps = kSortThreads / kWarp;
     __shared__ uint32_t wcnt[kWarps][kDigits];
     __shared__ uint32_t gbase[kDigits];
+    __shared__ uint32_t tstart[kDigits];   // tile-local start of each digit's run
+    __shared__ uint32_t wsum[kWarps];
+    __shared__ uint32_t skey[kTile];
+    __shared__ int32_t sval[kTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
     gbase[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
 
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * (kTile / kWarps);
+    const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    const int64_t base = tile0 + (int64_t)warp * (kTile / kWarps);
     uint32_t key[kSortItems], loc[kSortItems];
     int32_t val[kSortItems];
 #pragma unroll
@@ -69,6 +74,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
+    uint32_t total;
     {  // exclusive prefix over warps, per digit (thread = digit)
         uint32_t run = 0;
         for (int w = 0; w < kWarps; ++w) {
@@ -76,17 +82,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             wcnt[w][threadIdx.x] = run;
             run += t;
         }
+        total = run;
+    }
+    {  // exclusive prefix over digits of the tile's counts
+        uint32_t incl = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        tstart[threadIdx.x] = before + incl - total;
     }
     __syncthreads();
+    // local order: keys grouped by digit inside the tile (stable), then written out in
+    // that order, so consecutive threads write consecutive positions of a digit's run
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t idx = base + r * kWarp + lane;
         if (idx < n) {
             const uint32_t d = (key[r] >> shift) & (kDigits - 1);
-            const uint32_t dst = gbase[d] + wcnt[warp][d] + loc[r];
-            kout[dst] = key[r];
-            vout[dst] = val[r];
+            const uint32_t lp = tstart[d] + wcnt[warp][d] + loc[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
+    }
+    __syncthreads();
+    const int tile_n = (int)(n - tile0 < kTile ? n - tile0 : kTile);
+    for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+        const uint32_t k = skey[i];
+        const uint32_t d = (k >> shift) & (kDigits - 1);
+        const uint32_t dst = gbase[d] + (uint32_t)i - tstart[d];
+        kout[dst] = k;
+        vout[dst] = sval[i];
     }
 }
 
