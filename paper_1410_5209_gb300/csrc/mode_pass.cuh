@@ -845,9 +845,13 @@ inline int best_warps_per_block(size_t warp_bytes) {
     return best;
 }
 
+// Three- and five-way tensors get the number of other modes as a compile-time constant
+// (fully unrolled mode loops); other orders run the generic kernel.
 template <class T, int CM>
 auto mode_pass_kernel(int N, bool first) {
     if (N == 3) return first ? k_mode_pass<T, CM, 2, true> : k_mode_pass<T, CM, 2, false>;
+    if constexpr (sizeof(T) == 4)
+        if (N == 5) return first ? k_mode_pass<T, CM, 4, true> : k_mode_pass<T, CM, 4, false>;
     return first ? k_mode_pass<T, CM, 0, true> : k_mode_pass<T, CM, 0, false>;
 }
 

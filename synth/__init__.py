@@ -131,10 +131,20 @@ def distinct_coords(dims, nnz, seed, modes=None, zipf_s=1.1, stream=100, device=
     modes = modes or ["uniform"] * N
     samplers = [Zipf(int(dims[n]), zipf_s, seed, stream + n, device)
                 if modes[n] == "zipf" else None for n in range(N)]
+    # modes grouped so that each group's packed index fits in 62 bits (one group unless
+    # the tensor has more than 2^62 cells)
+    groups, cur, prod = [], [], 1
+    for n in range(N):
+        if cur and prod * int(dims[n]) >= 2 ** 62:
+            groups.append(cur)
+            cur, prod = [], 1
+        cur.append(n)
+        prod *= int(dims[n])
+    groups.append(cur)
     mult = [1] * N
-    for n in range(N - 2, -1, -1):
-        mult[n] = mult[n + 1] * int(dims[n + 1])
-    assert float(np.prod(np.array(dims, dtype=np.float64))) < 2.0 ** 62
+    for g in groups:
+        for k in range(len(g) - 2, -1, -1):
+            mult[g[k]] = mult[g[k + 1]] * int(dims[g[k + 1]])
 
     def draw(start, n):
         cols = []
@@ -146,9 +156,9 @@ def distinct_coords(dims, nnz, seed, modes=None, zipf_s=1.1, stream=100, device=
                                                          device)))
         return torch.stack(cols, dim=1).to(torch.int32)
 
-    def keys(c):
+    def keys(c, g):
         k = torch.zeros(c.shape[0], dtype=torch.int64, device=device)
-        for m in range(N):
+        for m in g:
             k += c[:, m].long() * mult[m]
         return k
 
@@ -159,9 +169,22 @@ def distinct_coords(dims, nnz, seed, modes=None, zipf_s=1.1, stream=100, device=
         c = draw(start, n_draw)
         start += n_draw
         allc = torch.cat([have, c]) if have.shape[0] else c
-        ks, idx = torch.sort(keys(allc), stable=True)
-        first = torch.ones_like(ks, dtype=torch.bool)
-        first[1:] = ks[1:] != ks[:-1]
+        if len(groups) == 1:
+            ks, idx = torch.sort(keys(allc, groups[0]), stable=True)
+            first = torch.ones_like(ks, dtype=torch.bool)
+            first[1:] = ks[1:] != ks[:-1]
+        else:  # stable sorts from the least significant group; equal tuples stay in draw order
+            idx = torch.arange(allc.shape[0], device=device)
+            for g in reversed(groups):
+                _, o = torch.sort(keys(allc, g)[idx], stable=True)
+                idx = idx[o]
+            first = torch.ones(idx.shape[0], dtype=torch.bool, device=device)
+            same = torch.ones(idx.shape[0] - 1, dtype=torch.bool, device=device)
+            for g in groups:
+                kg = keys(allc, g)[idx]
+                same &= kg[1:] == kg[:-1]
+            first[1:] = ~same
+            ks = None
         keep = torch.sort(idx[first]).values
         del ks, idx, first
         if keep.numel() >= nnz:
