@@ -274,6 +274,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 template <int CW, bool FIRST, bool SPLIT>
 __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<float> a, int CM, int W) {
     using T = float;
+    constexpr int kTcCols = CW;  // tensor-memory columns: the accumulator is 128 x CW fp32
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // kTcStages operand stages (hi and lo copies each)
     unsigned char *stage0 = smem_raw;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          tc_saddr(&s_taddr)),
-                     "r"(128)
+                     "r"(kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(128)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols)
                      : "memory");
 }
 
@@ -577,14 +578,21 @@ __global__ void __launch_bounds__(kWideThreads) k_res_wide(const ResArgs<T> a, i
     }
 }
 
+// Shared memory per tensor-core block that keeps residency at most 512 / CW blocks per SM
+// (the SM's shared memory, 228 KB, over one more block than that, plus a margin).
+size_t tc_min_smem(int CW) {
+    const int max_blocks = 512 / CW;
+    return (size_t)(228 * 1024) / (size_t)(max_blocks + 1) + 1024;
+}
+
 template <int CW>
 void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, bool split,
                             cudaStream_t st) {
-    // at least 48 KB of shared memory per block keeps at most four blocks (4 x 128 tensor
-    // memory columns) on an SM, so no allocation ever waits
+    // enough shared memory per block that at most 512 / CW blocks (each holding CW of the
+    // SM's 512 tensor-memory columns) fit on an SM, so no allocation ever waits
     size_t smem = 2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + 2 * kWideTile) +
                   sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
-    smem = std::max<size_t>(smem, 48 * 1024);
+    smem = std::max<size_t>(smem, tc_min_smem(CW));
     auto kern = split ? (a.first ? k_pass_wide_tc<CW, true, true> : k_pass_wide_tc<CW, false, true>)
                       : (a.first ? k_pass_wide_tc<CW, true, false> : k_pass_wide_tc<CW, false, false>);
     TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -619,7 +627,14 @@ int wide_split_width(int C, int CM) {
 template <class T>
 int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool first) {
     int per_sm = 4;
-    if (!(sizeof(T) == 4 && tensor_cores)) {
+    if (sizeof(T) == 4 && tensor_cores) {
+        const int cw = wide_split_width(C, CM);
+        const size_t smem = std::max<size_t>(
+            2 * kTcStages * (size_t)kTcBuf + sizeof(float) * (2 * (size_t)CM + 2 * kWideTile) +
+                sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1),
+            tc_min_smem(cw));
+        per_sm = std::max(1, std::min(512 / cw, (int)((228 * 1024) / (smem + 1024))));
+    } else {
         const int cw = wide_split_width(C, CM);
         const size_t smem = sizeof(T) * ((size_t)kWideTile * (cw + 4) + 2 * (size_t)CM + 2 * kWideTile) +
                             sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
