@@ -37,7 +37,7 @@ WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=
 # reports traffic as null once the sources differ or the entry count is not 1e8.
 NCU_TRAFFIC = 1.807e9
 NCU_TRAFFIC_NNZ = 100_000_000
-NCU_SOURCE_HASH = "e2796299e8e8fb30"
+NCU_SOURCE_HASH = "d797491fea4f39c1"
 
 
 def kernel_source_hash():

@@ -48,6 +48,16 @@ def test_noalloc_loss_matches_tf_loss(dtype, weighted):
         assert got[1] > 0
 
 
+def test_noalloc_loss_wide_subsets():
+    """After a sweep with C > 16 the loss reduction runs the wide residual kernel; its block
+    partials also fit the static array."""
+    p = synth.small(45, (300, 200, 50), 30_000, 3, 40)
+    f = factorization(p, tf.F32)
+    for call in range(2):
+        f.sweep(20, 0.3, 1, p.column_order(call, 20))
+        assert close(f.loss_noalloc(0.3), f.loss(0.3))
+
+
 def test_noalloc_loss_across_contexts():
     """Contexts of different shapes (N = 4, then N = 3, other block counts) share the
     array; stale partial sums of the larger reduction never reach the smaller one."""
