@@ -666,3 +666,39 @@ def test_five_way_float(C):
     assert abs(rmse - rmseo) <= 1e-3 * rmseo
     for n in range(5):
         assert rel(f.factors(n).astype(np.float64), A[n]) < 1e-3
+
+
+# --------------------------------------------------------------------------- edge cases
+
+
+@pytest.mark.parametrize("dims,nnz,K,C", [((1, 1, 1), 1, 1, 1), ((5, 7), 1, 3, 3),
+                                          ((3, 4, 2, 2, 3, 2, 2, 3), 400, 4, 2),
+                                          ((3, 4, 2, 2, 3, 2, 2, 3), 400, 20, 17)])
+def test_edge_shapes(dims, nnz, K, C):
+    """A single entry, a one-cell tensor, and eight modes (the maximum) on the narrow and
+    the wide path, FP64 against the oracle."""
+    p = synth.small(160 + len(dims) + K, dims, nnz, 1, K)
+    f, t, A = make(p, tf.F64)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.5, 1, order)
+        bad_o = oracle.sals_sweep(t, A, r, C, 0.5, 1, order)
+        assert bad_o == 0
+    for n in range(len(dims)):
+        assert rel(f.factors(n), A[n]) < 1e-9 or np.linalg.norm(A[n]) < 1e-12
+    L, _ = f.loss(0.5)
+    Lo, _ = oracle.loss(t, r, A, 0.5)
+    assert abs(L - Lo) <= 1e-9 * max(Lo, 1e-300)
+
+
+def test_rejects_bad_sweep_arguments():
+    p = synth.small(170, (20, 10, 5), 300, 2, 6)
+    f, _, _ = make(p, tf.F64)
+    for C, lam, T_in in ((0, 0.1, 1), (7, 0.1, 1), (2, -1.0, 1), (2, 0.1, 0)):
+        with pytest.raises(tf.TFError) as e:
+            f.sweep(C, lam, T_in)
+        assert e.value.status == tf.EINVAL
+    with pytest.raises(tf.TFError):
+        f.sweep(2, 0.1, 1, np.array([0, 0, 1, 2, 3, 4], np.int32))   # not a permutation
+    f.sweep(2, 0.1, 1)   # still usable
