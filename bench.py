@@ -298,6 +298,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-batch", type=int, default=256)
+    ap.add_argument("--serve-mix-nnz", type=int, default=20_000_000)
     ap.add_argument("--study", action="store_true",
                     help="C-sweep and row-assignment policy study instead of the benchmark")
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
@@ -437,26 +438,62 @@ def main():
         f.foldin_batch(0, reqs[:8], lam)   # warm-up
         rng = np.random.default_rng(args.seed + 31)
         arrive = np.cumsum(rng.exponential(1.0 / args.serve_rate, len(reqs)))
-        clock, nxt, lat, batches = 0.0, 0, np.zeros(len(reqs)), []
-        while nxt < len(reqs):
-            clock = max(clock, arrive[nxt])
-            end = nxt
-            while end < len(reqs) and arrive[end] <= clock and end - nxt < args.serve_batch:
-                end += 1
-            t0 = time.perf_counter()
-            _, status = f.foldin_batch(0, reqs[nxt:end], lam)
-            clock += time.perf_counter() - t0
-            assert not status.any()
-            lat[nxt:end] = clock - arrive[nxt:end]
-            batches.append(end - nxt)
-            nxt = end
-        out["serving"] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
-                          "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                          "req_per_s": len(reqs) / clock, "offered_req_per_s": args.serve_rate,
-                          "requests": len(reqs), "mean_batch": float(np.mean(batches)),
-                          "max_batch": args.serve_batch,
-                          "what": "Poisson fold-in arrivals, continuous batching through "
-                                  "tf_foldin_batch (latency = arrival -> rows on host)"}
+
+        def serve():
+            clock, nxt, lat, batches = 0.0, 0, np.zeros(len(reqs)), []
+            while nxt < len(reqs):
+                clock = max(clock, arrive[nxt])
+                end = nxt
+                while end < len(reqs) and arrive[end] <= clock and end - nxt < args.serve_batch:
+                    end += 1
+                t0 = time.perf_counter()
+                _, status = f.foldin_batch(0, reqs[nxt:end], lam)
+                clock += time.perf_counter() - t0
+                assert not status.any()
+                lat[nxt:end] = clock - arrive[nxt:end]
+                batches.append(end - nxt)
+                nxt = end
+            return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "req_per_s": len(reqs) / clock, "offered_req_per_s": args.serve_rate,
+                    "requests": len(reqs), "mean_batch": float(np.mean(batches)),
+                    "max_batch": args.serve_batch}
+
+        out["serving"] = {**serve(), "what": "Poisson fold-in arrivals, continuous batching "
+                          "through tf_foldin_batch (latency = arrival -> rows on host)"}
+        if args.serve_mix_nnz > 0:
+            # the same arrivals while a factorisation job sweeps on a second stream from its
+            # own host thread: its kernels and the fold-ins share the GPU
+            import threading
+            q = synth.skewed_3way(seed=args.seed + 41, nnz=args.serve_mix_nnz, device="cuda")
+            s2 = torch.cuda.Stream()
+            g = tf.Factorization(q.coords, q.x, q.dims, K, seed=args.seed + 41, dtype=tf.F32,
+                                 stream=s2.cuda_stream, device_input=True)
+            stop, done = threading.Event(), [0]
+
+            def job():
+                while not stop.is_set():
+                    g.sweep(C, lam, T_in)
+                    done[0] += 1
+
+            # the serving context moves to a high-priority stream: its fold-in kernels are
+            # started as soon as the background job's blocks free an SM
+            hi = torch.cuda.Stream(priority=-1)
+            f.set_stream(hi)
+            th = threading.Thread(target=job)
+            th.start()
+            time.sleep(0.2)
+            mixed = serve()
+            stop.set()
+            th.join()
+            torch.cuda.synchronize()
+            f.set_stream(stream)
+            out["serving_mixed"] = {**mixed, "background_sweeps": done[0],
+                                    "what": "as serving (on a high-priority stream), with "
+                                            f"sweeps of a {q.nnz}-entry skewed tensor (K={K}, "
+                                            f"C={C}) running on a second stream meanwhile"}
+            g.close()
+            del q
     f.close()
     del f
 

@@ -17,7 +17,10 @@
  *     most recent failure in words.
  *   - Inputs are copied: the caller keeps ownership of every buffer it passes, and
  *     owns every output buffer.  All device memory belongs to the context and is
- *     released by tf_destroy.
+ *     released by tf_destroy.  The tensor's layout is allocated by tf_create; scratch
+ *     that grows with later calls (Gram partials, loss reduction, fold-in and predict
+ *     staging) is allocated in stream order on the context's stream, so that growing
+ *     it waits for no other stream of the device.
  *   - Calls on one context are ordered on the context's CUDA stream.  A context is
  *     not thread-safe; distinct contexts are independent.
  *   - Host-only entry points (tf_assign_rows, tf_plan_mode, tf_version) need no GPU.
@@ -102,6 +105,12 @@ const char *tf_last_error(const tf_ctx *ctx);
 
 /* Waits for the context's stream and reports any device-side error. */
 tf_status tf_sync(tf_ctx *ctx);
+
+/* Orders all later work of ctx on `stream` (a cudaStream_t of the same device; NULL = the
+ * legacy default stream), after waiting for the work already queued on the old one.  A
+ * serving context can so move to a high-priority stream, whose kernels the GPU starts
+ * first when other contexts' kernels share it. */
+tf_status tf_set_stream(tf_ctx *ctx, void *stream);
 
 /* ------------------------------------------------------------------ factors */
 

@@ -80,6 +80,7 @@ def load():
         "tf_set_schedule": [P, i32, i32],
         "tf_set_kernel_path": [P, i32],
         "tf_set_precision": [P, i32],
+        "tf_set_stream": [P, P],
         "tf_profile": [P, i32],
         "tf_get_profile": [P, P, P],
         "tf_get_launch_trace": [P, i64, P, P, P, P],
@@ -286,6 +287,11 @@ class Factorization:
 
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
+
+    def set_stream(self, stream):
+        """Queue later work on `stream` (a cudaStream_t handle as int, or a torch stream)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.tf_set_stream(self._ctx, ctypes.c_void_p(handle or 0)))
 
     def set_precision(self, mode):
         """0: FP32-level Gram; 1: single-TF32 tensor-core Gram for wide subsets."""

@@ -48,6 +48,37 @@ struct Buf {  // owning device buffer
     }
 };
 
+// Growable scratch allocated in stream order (cudaMallocAsync / cudaFreeAsync): growing it
+// waits for nothing but the context's own stream, where cudaFree would wait for the whole
+// device -- so a serving context growing its fold-in staging never waits for the kernels
+// of another context on the same GPU.  Capacity grows by at least half each time.
+template <class T>
+struct StreamBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    StreamBuf() = default;
+    StreamBuf(const StreamBuf &) = delete;
+    StreamBuf &operator=(const StreamBuf &) = delete;
+    void ensure(size_t count, cudaStream_t st) {
+        if (count <= n) return;
+        const size_t want = std::max(count, n + n / 2);
+        release(st);
+        cudaError_t e = cudaMallocAsync(&p, want * sizeof(T), st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            throw ApiError{TF_ENOMEM, "device allocation of " + std::to_string(want * sizeof(T)) +
+                                          " bytes failed"};
+        }
+        n = want;
+    }
+    void release(cudaStream_t st) {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        n = 0;
+    }
+};
+
 struct ModeLayout {
     int64_t I = 0;
     Buf<int64_t> off;       // [I + 1]
@@ -88,18 +119,18 @@ struct Impl : CtxBase {
     Buf<T> res[kMaxModes];         // residual copies, mode-n order
     Buf<T> Z[kMaxModes];           // packed slices
     ModeLayout mode[kMaxModes];
-    Buf<T> partials;
+    StreamBuf<T> partials;
     Buf<int32_t> d_order, d_Q;
     Buf<DeviceStatus> stat;
     Buf<unsigned long long> ticket;  // bin counter of the mode passes
     unsigned long long ticket_base = 0;
-    Buf<double> red;               // reduction scratch
+    StreamBuf<double> red;         // reduction scratch
     Buf<int64_t> d_dims;
-    Buf<int32_t> f_other;          // fold-in scratch
-    Buf<T> f_x, f_out, f_part;
-    Buf<int64_t> f_meta;           // tiled fold-in block table / request offsets / status
-    Buf<int32_t> p_coords;         // tf_predict staging
-    Buf<T> p_out;
+    StreamBuf<int32_t> f_other;    // fold-in scratch
+    StreamBuf<T> f_x, f_out, f_part;
+    StreamBuf<int64_t> f_meta;     // tiled fold-in block table / request offsets / status
+    StreamBuf<int32_t> p_coords;   // tf_predict staging
+    StreamBuf<T> p_out;
     int32_t *h_order = nullptr;    // pinned staging of the column order
     cudaEvent_t order_ev = nullptr;
     bool order_pending = false;
@@ -126,6 +157,12 @@ struct Impl : CtxBase {
     int64_t launches = 0;
 
     ~Impl() override {
+        // the stream-ordered scratch goes back to the pool behind the last work on st
+        for (auto *b : {&f_other, &p_coords}) b->release(st);
+        for (auto *b : {&f_x, &f_out, &f_part, &p_out, &partials}) b->release(st);
+        f_meta.release(st);
+        red.release(st);
+        cudaStreamSynchronize(st);
         if (h_order) cudaFreeHost(h_order);
         if (order_ev) cudaEventDestroy(order_ev);
         for (auto &pr : prof_pending) {
@@ -213,7 +250,7 @@ struct Impl : CtxBase {
         ticket.alloc(1);
         TFS_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned long long), st));
         ticket_base = 0;
-        red.alloc(4096);
+        red.ensure(4096, st);
         d_dims.alloc(N);
         TFS_CUDA(cudaMemcpyAsync(d_dims.p, dims.data(), N * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st));
@@ -508,7 +545,7 @@ struct Impl : CtxBase {
             }
             max_slots = std::max(max_slots, mode[n].n_slots);
         }
-        partials.ensure((size_t)std::max<int64_t>(max_slots, 1) * partial_stride(CM));
+        partials.ensure((size_t)std::max<int64_t>(max_slots, 1) * partial_stride(CM), st);
 
         bool use_tma = false;
         if constexpr (sizeof(T) == 4) {
@@ -716,7 +753,7 @@ struct Impl : CtxBase {
         const ModeLayout &L = mode[0];
         const int blocks = res_grid<T>(CM_last, L.P, N);
         const int reg_blocks = 256;
-        red.ensure((size_t)blocks + (size_t)N * reg_blocks + 4);
+        red.ensure((size_t)blocks + (size_t)N * reg_blocks + 4, st);
         ResArgs<T> a{};
         a.items = L.items.p;
         a.bin_ptr = L.bin_ptr.p;
@@ -867,8 +904,8 @@ struct Impl : CtxBase {
         const int32_t *dc = coords;
         T *dout = out;
         if (!dev) {
-            p_coords.ensure((size_t)m * N);
-            p_out.ensure((size_t)m);
+            p_coords.ensure((size_t)m * N, st);
+            p_out.ensure((size_t)m, st);
             TFS_CUDA(cudaMemcpyAsync(p_coords.p, coords, (size_t)m * N * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, st));
             dc = p_coords.p;
@@ -930,16 +967,16 @@ struct Impl : CtxBase {
         std::vector<int64_t> blk_range;
         std::vector<int32_t> blk_req, req_blk;
         const int blocks = foldin_plan_blocks(offsets, n_req, blk_range, blk_req, req_blk);
-        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1));
-        f_x.ensure((size_t)std::max<int64_t>(m, 1));
-        f_out.ensure((size_t)n_req * K);
-        f_part.ensure(foldin_part_elems(K, blocks));
+        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1), st);
+        f_x.ensure((size_t)std::max<int64_t>(m, 1), st);
+        f_out.ensure((size_t)n_req * K, st);
+        f_part.ensure(foldin_part_elems(K, blocks), st);
         // one int64 staging buffer: block entry ranges [2B], then as int32 the blocks'
         // requests [B], the requests' first blocks [n_req + 1] and their status [n_req]
         const size_t B = (size_t)std::max(blocks, 1);
         const size_t n32 = B + 2 * (size_t)n_req + 1;
         const size_t n64 = 2 * B + (n32 + 1) / 2;
-        f_meta.ensure(n64);
+        f_meta.ensure(n64, st);
         std::vector<int64_t> meta(n64, 0);
         std::copy(blk_range.begin(), blk_range.end(), meta.begin());
         int32_t *m32 = reinterpret_cast<int32_t *>(meta.data() + 2 * B);
@@ -1011,9 +1048,9 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         if (foldin_smem_bytes<T>(K) + 1024 > (size_t)maxsm)
             throw ApiError{TF_EINVAL, "K too large for the fold-in kernel"};
-        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1));
-        f_x.ensure((size_t)std::max<int64_t>(m, 1));
-        f_out.ensure((size_t)K);
+        f_other.ensure((size_t)std::max<int64_t>(m, 1) * std::max(N - 1, 1), st);
+        f_x.ensure((size_t)std::max<int64_t>(m, 1), st);
+        f_out.ensure((size_t)K, st);
         if (m > 0) {
             TFS_CUDA(cudaMemcpyAsync(f_other.p, other, (size_t)m * (N - 1) * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, st));
@@ -1342,6 +1379,13 @@ tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kin
                               int32_t *modes, float *ms) {
     if (!n || cap < 0) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) { c.launch_trace(cap, n, kinds, modes, ms); });
+}
+
+tf_status tf_set_stream(tf_ctx *ctx, void *stream) {
+    return dispatch(ctx, [&](auto &c) {
+        TFS_CUDA(cudaStreamSynchronize(c.st));
+        c.st = (cudaStream_t)stream;
+    });
 }
 
 tf_status tf_set_precision(tf_ctx *ctx, int mode) {

@@ -702,3 +702,71 @@ def test_rejects_bad_sweep_arguments():
     with pytest.raises(tf.TFError):
         f.sweep(2, 0.1, 1, np.array([0, 0, 1, 2, 3, 4], np.int32))   # not a permutation
     f.sweep(2, 0.1, 1)   # still usable
+
+
+# --------------------------------------------------------------------------- concurrency
+
+
+def test_jobs_on_two_streams_match_solo_runs():
+    """Two factorisation jobs on their own CUDA streams, their sweeps and fold-ins queued
+    alternately so that their kernels overlap on the device, give bit for bit the results
+    each gives alone (contexts share no device state)."""
+    import torch
+    pa = synth.small(180, (300, 200, 50), 30_000, 4, 24)
+    pb = synth.small(181, (150, 400, 60), 25_000, 3, 24)
+
+    def run(p, stream, C):
+        c, x = p.numpy()
+        f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32,
+                             stream=stream.cuda_stream if stream is not None else None)
+        return f
+
+    def finish(f, p, C):
+        rows = f.foldin(0, np.stack([np.arange(50) % p.dims[1], np.arange(50) % p.dims[2]], 1),
+                        np.linspace(-1, 1, 50), 0.3)
+        return [f.factors(n) for n in range(3)], f.loss(0.3), rows
+
+    solo = []
+    for p, C in ((pa, 8), (pb, 20)):
+        f = run(p, None, C)
+        for s in range(3):
+            f.sweep(C, 0.3, 1, p.column_order(s, C))
+        solo.append(finish(f, p, C))
+        f.close()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    fa, fb = run(pa, sa, 8), run(pb, sb, 20)
+    for s in range(3):   # queued back to back, no synchronisation between the two jobs
+        fa.sweep(8, 0.3, 1, pa.column_order(s, 8))
+        fb.sweep(20, 0.3, 1, pb.column_order(s, 20))
+    mixed = [finish(fa, pa, 8), finish(fb, pb, 20)]
+    for (fs, ls, rs), (fm, lm, rm) in zip(solo, mixed):
+        for n in range(3):
+            assert np.array_equal(fs[n], fm[n])
+        assert ls == lm
+        assert np.array_equal(rs, rm)
+
+
+def test_set_stream_moves_later_work():
+    """A context moved to another stream (here a high-priority one) between sweeps
+    continues the same job: the sweeps split across the two streams give bit for bit
+    the factors and loss of the same sweeps on one stream."""
+    import torch
+    p = synth.small(182, (300, 200, 50), 30_000, 3, 12)
+    c, x = p.numpy()
+    ref = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
+    for s in range(4):
+        ref.sweep(6, 0.3, 1, p.column_order(s, 6))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream(priority=-1)
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32,
+                         stream=s1.cuda_stream)
+    for s in range(4):
+        if s == 2:
+            f.set_stream(s2)
+        f.sweep(6, 0.3, 1, p.column_order(s, 6))
+    for n in range(3):
+        assert np.array_equal(f.factors(n), ref.factors(n))
+    assert f.loss(0.3) == ref.loss(0.3)
+    f.set_stream(None)   # the legacy default stream
+    f.sweep(6, 0.3, 1, p.column_order(4, 6))
+    ref.sweep(6, 0.3, 1, p.column_order(4, 6))
+    assert np.array_equal(f.factors(0), ref.factors(0))
