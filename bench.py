@@ -392,6 +392,12 @@ def main():
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": mp_avg_ms}
+    # the same launch with the factor-row gathers counted as bytes: C values of each other
+    # mode's row per entry (the slices fit L2, so these are L2/L1 bytes, not HBM bytes)
+    gather_bytes = nnz * (N - 1) * 4.0 * C
+    with_g = (bytes_per_launch + gather_bytes) / (mp_avg_ms / 1e3) / 1e9
+    roofline["with_gathers"] = {"achieved": with_g, "frac": with_g / hbm,
+                                "gather_bytes_per_launch": gather_bytes}
     nsplit = math.ceil(K / C)
     sweep_bytes = nnz * (T_in * N * (4 * (N - 1) + 4) + 4) * nsplit
     sweep_ms = sum(v[1] for k, v in prof.items()

@@ -23,7 +23,8 @@
  *     it waits for no other stream of the device.
  *   - Calls on one context are ordered on the context's CUDA stream.  A context is
  *     not thread-safe; distinct contexts are independent.
- *   - Host-only entry points (tf_assign_rows, tf_plan_mode, tf_version) need no GPU.
+ *   - Host-only entry points (tf_assign_rows, tf_plan_mode, tf_version, and
+ *     tf_estimate_bytes given num_sms > 0) need no GPU.
  */
 #ifndef TF_SALS_H
 #define TF_SALS_H
@@ -105,6 +106,12 @@ const char *tf_last_error(const tf_ctx *ctx);
 
 /* Waits for the context's stream and reports any device-side error. */
 tf_status tf_sync(tf_ctx *ctx);
+
+/* The context's mode count, rank and dtype (any output may be NULL). */
+tf_status tf_get_shape(tf_ctx *ctx, int *N, int *K, tf_dtype *dtype);
+
+/* The stream the context's work is ordered on. */
+tf_status tf_get_stream(tf_ctx *ctx, void **stream);
 
 /* Orders all later work of ctx on `stream` (a cudaStream_t of the same device; NULL = the
  * legacy default stream), after waiting for the work already queued on the old one.  A
@@ -308,6 +315,25 @@ tf_status tf_plan_mode(const int64_t *off, int64_t I, int P, int64_t cap,
                        tf_sched_policy policy, uint64_t seed, tf_item *items,
                        int64_t max_items, int64_t *n_items, int64_t *n_slots,
                        int64_t *bin_ptr);
+
+/* ------------------------------------------------------------------ memory */
+
+/* Upper bound, in bytes, of the device memory a context holds at any time from tf_create
+ * through sweeps with C <= C_max and tf_loss (the peak of the layout build or of the
+ * sweeps, whichever is larger), counting the stream-ordered pool's rounding.  Fold-in and
+ * predict staging are not included (they grow with the requests).  No counterpart in the
+ * paper: a serving process admits jobs against free device memory with it.
+ *   dims [N], N, nnz, K, dtype, flags   as for tf_create (flags: TF_INPUT_DEVICE or 0)
+ *   C_max    largest C of the sweeps to come, 1..min(K, 127)
+ *   num_sms  the device's SM count (> 0: no device needed), <= 0: asked of the device
+ * TF_EINVAL for arguments tf_create or tf_sals_sweep would refuse. */
+tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int C_max,
+                            tf_dtype dtype, uint32_t flags, int num_sms, int64_t *bytes);
+
+/* Bytes in use, and the high-water mark, of the current device's default stream-ordered
+ * memory pool, which holds every context's device memory; reset_high != 0 restarts the
+ * high-water mark at the current use.  Any output pointer may be NULL. */
+tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int reset_high);
 
 /* Library version string. */
 const char *tf_version(void);

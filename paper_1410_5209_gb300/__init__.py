@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtfsals.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "tf_sals.h")
+SERVER_HEADER = os.path.join(os.path.dirname(_HERE), "include", "tf_server.h")
 
 OK, EINVAL, ERANGE, EDUP, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(8)
 STATUS_NAMES = ["TF_OK", "TF_EINVAL", "TF_ERANGE", "TF_EDUP", "TF_ENOMEM", "TF_ECUDA",
@@ -87,6 +88,22 @@ def load():
         "tf_assign_rows": [i32, i32, P, P, i32, u64, P],
         "tf_plan_mode": [P, i64, i32, i64, i32, u64, P, i64, P, P, P],
         "tf_version": [],
+        "tf_get_shape": [P, P, P, P],
+        "tf_get_stream": [P, P],
+        "tf_estimate_bytes": [P, i32, i64, i32, i32, i32, u32, i32, P],
+        "tf_pool_usage": [P, P, i32],
+        "tf_server_create": [P, P, P],
+        "tf_server_destroy": [P],
+        "tf_server_last_error": [P],
+        "tf_server_submit_job": [P, P, P],
+        "tf_server_job_info": [P, i64, P],
+        "tf_server_wait_job": [P, i64, f64, P],
+        "tf_server_job_factors": [P, i64, i32, P],
+        "tf_server_release_job": [P, i64],
+        "tf_server_submit_foldin": [P, i32, P, P, i64, f64, P],
+        "tf_server_wait_foldin": [P, i64, f64, P, P, P],
+        "tf_server_get_stats": [P, P],
+        "tf_server_plan_admission": [i32, P, P, i64, i64, i32, i32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -95,15 +112,19 @@ def load():
     lib.tf_destroy.restype = None
     lib.tf_last_error.restype = ctypes.c_char_p
     lib.tf_version.restype = ctypes.c_char_p
+    lib.tf_server_destroy.restype = None
+    lib.tf_server_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
 
-def declared_symbols(header: str = HEADER):
-    """Names of the functions declared in the public header."""
-    txt = open(header).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(tf_[a-z_0-9]+)\s*\(", txt)))
+def declared_symbols(headers=(HEADER, SERVER_HEADER)):
+    """Names of the functions declared in the public headers."""
+    names = set()
+    for h in ([headers] if isinstance(headers, str) else headers):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(tf_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 def _ptr(a):
@@ -367,3 +388,174 @@ def plan_mode(off, P, cap=0, policy=SCHED_LPT, seed=0):
 
 def version():
     return load().tf_version().decode()
+
+
+def estimate_bytes(dims, nnz, K, C_max, dtype=F32, device_input=False, num_sms=0):
+    """Upper bound of a context's device memory from tf_create through sweeps with
+    C <= C_max (tf_estimate_bytes); num_sms > 0 needs no GPU."""
+    lib = load()
+    d = np.ascontiguousarray(dims, np.int64)
+    out = ctypes.c_int64()
+    st = lib.tf_estimate_bytes(_ptr(d), len(d), int(nnz), int(K), int(C_max), int(dtype),
+                               INPUT_DEVICE if device_input else 0, int(num_sms),
+                               ctypes.byref(out))
+    if st != OK:
+        raise TFError(st, "tf_estimate_bytes refused the shape")
+    return out.value
+
+
+def pool_usage(reset_high=False):
+    """(bytes in use, high-water mark) of the device's stream-ordered pool."""
+    used, high = ctypes.c_int64(), ctypes.c_int64()
+    st = load().tf_pool_usage(ctypes.byref(used), ctypes.byref(high), 1 if reset_high else 0)
+    if st != OK:
+        raise TFError(st, "tf_pool_usage failed")
+    return used.value, high.value
+
+
+# ---------------------------------------------------------------- serving (tf_server.h)
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("hbm_reserve", ctypes.c_int64),
+                ("max_running", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("max_bypass", ctypes.c_int)]
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("coords", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("dims", ctypes.c_void_p), ("N", ctypes.c_int), ("nnz", ctypes.c_int64),
+                ("K", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("C", ctypes.c_int), ("lam", ctypes.c_double), ("T_in", ctypes.c_int),
+                ("sweeps", ctypes.c_int), ("sweep_flags", ctypes.c_uint32),
+                ("col_orders", ctypes.c_void_p)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int),
+                ("sweeps_done", ctypes.c_int), ("loss", ctypes.c_double),
+                ("rmse", ctypes.c_double), ("bytes", ctypes.c_int64),
+                ("queued_s", ctypes.c_double), ("started_s", ctypes.c_double),
+                ("finished_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "jobs_queued", "jobs_running", "jobs_done", "jobs_failed", "foldins_done",
+        "foldin_batches", "foldin_max_batch", "bytes_admitted", "bytes_admitted_peak",
+        "running_peak")]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = range(4)
+
+
+def _struct_dict(s):
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+class Server:
+    """Serving loop (include/tf_server.h): factorisation jobs admitted against free device
+    memory, each on its own stream and host thread, and continuously batched fold-in
+    requests against `model` (a Factorization, owned by the server until close())."""
+
+    def __init__(self, model=None, hbm_budget=0, hbm_reserve=0, max_running=0, max_batch=0,
+                 max_bypass=0):
+        self._lib = load()
+        cfg = ServerConfig(int(hbm_budget), int(hbm_reserve), int(max_running),
+                           int(max_batch), int(max_bypass))
+        self._srv = ctypes.c_void_p()
+        self.model = model
+        st = self._lib.tf_server_create(ctypes.byref(cfg), model._ctx if model else None,
+                                        ctypes.byref(self._srv))
+        if st != OK:
+            raise TFError(st, self._lib.tf_server_last_error(None).decode())
+        self._dtype = model.dtype if model else F32
+        self._K = model.K if model else 0
+        self._keep = {}
+
+    def _check(self, st, what):
+        if st != OK:
+            raise TFError(st, f"{what}: {self._lib.tf_server_last_error(self._srv).decode()}")
+
+    def close(self):
+        if self._srv:
+            self._lib.tf_server_destroy(self._srv)
+            self._srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_job(self, coords, values, dims, K, C, lam, sweeps, T_in=1, seed=0, dtype=F32,
+                   orders=None, weighted=False):
+        c = np.ascontiguousarray(coords, np.int32)
+        x = np.ascontiguousarray(values, _np_dtype(dtype))
+        d = np.ascontiguousarray(dims, np.int64)
+        o = None if orders is None else np.ascontiguousarray(orders, np.int32)
+        desc = JobDesc(c.ctypes.data, x.ctypes.data, d.ctypes.data, len(d), len(x), int(K),
+                       int(dtype), ctypes.c_uint64(seed).value, int(C), float(lam), int(T_in),
+                       int(sweeps), WEIGHTED_LAMBDA if weighted else 0,
+                       o.ctypes.data if o is not None else None)
+        jid = ctypes.c_int64()
+        self._check(self._lib.tf_server_submit_job(self._srv, ctypes.byref(desc),
+                                                   ctypes.byref(jid)), "submit_job")
+        self._keep[jid.value] = (tuple(int(v) for v in d), int(K), dtype)
+        return jid.value
+
+    def job_info(self, jid):
+        info = JobInfo()
+        self._check(self._lib.tf_server_job_info(self._srv, int(jid), ctypes.byref(info)),
+                    "job_info")
+        return _struct_dict(info)
+
+    def wait_job(self, jid, timeout=600.0):
+        """Job info once done or failed; raises TFError(ETIMEOUT) if still running."""
+        info = JobInfo()
+        self._check(self._lib.tf_server_wait_job(self._srv, int(jid), float(timeout),
+                                                 ctypes.byref(info)), "wait_job")
+        return _struct_dict(info)
+
+    def job_factors(self, jid, n):
+        dims, K, dtype = self._keep[jid]
+        out = np.empty((dims[n], K), _np_dtype(dtype))
+        self._check(self._lib.tf_server_job_factors(self._srv, int(jid), int(n), _ptr(out)),
+                    "job_factors")
+        return out
+
+    def release_job(self, jid):
+        self._check(self._lib.tf_server_release_job(self._srv, int(jid)), "release_job")
+        self._keep.pop(jid, None)
+
+    def submit_foldin(self, mode, other, values, lam):
+        o = np.ascontiguousarray(other, np.int32)
+        v = np.ascontiguousarray(values, _np_dtype(self._dtype))
+        rid = ctypes.c_int64()
+        self._check(self._lib.tf_server_submit_foldin(self._srv, int(mode), _ptr(o), _ptr(v),
+                                                      len(v), float(lam), ctypes.byref(rid)),
+                    "submit_foldin")
+        return rid.value
+
+    def wait_foldin(self, rid, timeout=60.0):
+        """(row [K], status, latency seconds)."""
+        row = np.empty(self._K, _np_dtype(self._dtype))
+        status, lat = ctypes.c_int32(), ctypes.c_double()
+        self._check(self._lib.tf_server_wait_foldin(self._srv, int(rid), float(timeout),
+                                                    _ptr(row), ctypes.byref(status),
+                                                    ctypes.byref(lat)), "wait_foldin")
+        return row, status.value, lat.value
+
+    def stats(self):
+        s = ServerStats()
+        self._check(self._lib.tf_server_get_stats(self._srv, ctypes.byref(s)), "stats")
+        return _struct_dict(s)
+
+
+def plan_admission(need, bypassed, room, budget_left=-1, slots=1 << 30, max_bypass=8):
+    """The scheduler's admission decision (host only): (admit flags, updated pass counts)."""
+    need = np.ascontiguousarray(need, np.int64)
+    byp = np.array(bypassed, np.int32, copy=True)
+    admit = np.zeros(len(need), np.int32)
+    load().tf_server_plan_admission(len(need), _ptr(need), _ptr(byp), int(room),
+                                    int(budget_left), int(slots), int(max_bypass), _ptr(admit))
+    return admit.astype(bool), byp

@@ -44,7 +44,8 @@ def up_to_date() -> bool:
         return False
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(HERE, "..", "include", "tf_sals.h"))
+    inc = os.path.join(HERE, "..", "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc)]
     return all(os.path.getmtime(d) <= t for d in deps if os.path.exists(d))
 
 
@@ -60,7 +61,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
             if log.strip():
                 print(f"== {s}\n{log}")
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

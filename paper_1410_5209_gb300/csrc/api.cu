@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -18,23 +19,31 @@
 
 namespace tfs {
 
+// Device buffer owned by a context, allocated and freed in the order of the context's
+// stream (cudaMallocAsync / cudaFreeAsync).  cudaFree waits for every stream of the device,
+// so a context built or destroyed beside running work (a serving process admitting and
+// retiring jobs) would stall all other work on the GPU; stream-ordered calls wait for
+// nothing but the context's own stream.  `s` is the stream the buffer is freed on; it
+// follows the context when tf_set_stream moves it.
 template <class T>
-struct Buf {  // owning device buffer
+struct Buf {
     T *p = nullptr;
     size_t n = 0;
+    cudaStream_t s = nullptr;
     Buf() = default;
     Buf(const Buf &) = delete;
     Buf &operator=(const Buf &) = delete;
     ~Buf() { reset(); }
     void reset() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
         p = nullptr;
         n = 0;
     }
-    void alloc(size_t count) {
+    void alloc(size_t count, cudaStream_t st) {
         reset();
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        s = st;
+        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -43,41 +52,55 @@ struct Buf {  // owning device buffer
         }
         n = count;
     }
-    void ensure(size_t count) {
-        if (count > n) alloc(count);
+    // Growable scratch: capacity grows by at least half each time.
+    void ensure(size_t count, cudaStream_t st) {
+        if (count > n) alloc(std::max(count, n + n / 2), st);
     }
 };
 
-// Growable scratch allocated in stream order (cudaMallocAsync / cudaFreeAsync): growing it
-// waits for nothing but the context's own stream, where cudaFree would wait for the whole
-// device -- so a serving context growing its fold-in staging never waits for the kernels
-// of another context on the same GPU.  Capacity grows by at least half each time.
-template <class T>
-struct StreamBuf {
-    T *p = nullptr;
-    size_t n = 0;
-    StreamBuf() = default;
-    StreamBuf(const StreamBuf &) = delete;
-    StreamBuf &operator=(const StreamBuf &) = delete;
-    void ensure(size_t count, cudaStream_t st) {
-        if (count <= n) return;
-        const size_t want = std::max(count, n + n / 2);
-        release(st);
-        cudaError_t e = cudaMallocAsync(&p, want * sizeof(T), st);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            cudaGetLastError();
-            throw ApiError{TF_ENOMEM, "device allocation of " + std::to_string(want * sizeof(T)) +
-                                          " bytes failed"};
+// Page-locked host blocks reused across contexts.  cudaFreeHost waits for the whole
+// device, so a destroyed context returns its staging block to this list instead; blocks
+// live as long as the process.  Sizes are rounded up to powers of two (>= 4 KiB).
+class PinnedCache {
+  public:
+    void *get(size_t bytes) {
+        const size_t sz = round(bytes);
+        {
+            std::lock_guard<std::mutex> g(m_);
+            auto it = free_.find(sz);
+            if (it != free_.end() && !it->second.empty()) {
+                void *q = it->second.back();
+                it->second.pop_back();
+                return q;
+            }
         }
-        n = want;
+        void *q = nullptr;
+        if (cudaMallocHost(&q, sz) != cudaSuccess) {
+            cudaGetLastError();
+            throw ApiError{TF_ENOMEM, "page-locked allocation failed"};
+        }
+        return q;
     }
-    void release(cudaStream_t st) {
-        if (p) cudaFreeAsync(p, st);
-        p = nullptr;
-        n = 0;
+    void put(void *q, size_t bytes) {
+        if (!q) return;
+        std::lock_guard<std::mutex> g(m_);
+        free_[round(bytes)].push_back(q);
     }
+
+  private:
+    static size_t round(size_t b) {
+        size_t sz = 4096;
+        while (sz < b) sz <<= 1;
+        return sz;
+    }
+    std::mutex m_;
+    std::map<size_t, std::vector<void *>> free_;
 };
+
+PinnedCache &pinned_cache() {
+    static PinnedCache c;
+    return c;
+}
 
 struct ModeLayout {
     int64_t I = 0;
@@ -95,6 +118,11 @@ struct ModeLayout {
     Buf<int32_t> id_of;     // degree rank -> row id
     int P = 0;
     int omode[kMaxModes - 1];
+    template <class F>
+    void each_buf(F f) {
+        f(off), f(perm), f(oidx), f(items), f(bin_ptr), f(split), f(single), f(rank_of),
+            f(id_of);
+    }
 };
 
 struct CtxBase {
@@ -119,18 +147,18 @@ struct Impl : CtxBase {
     Buf<T> res[kMaxModes];         // residual copies, mode-n order
     Buf<T> Z[kMaxModes];           // packed slices
     ModeLayout mode[kMaxModes];
-    StreamBuf<T> partials;
+    Buf<T> partials;
     Buf<int32_t> d_order, d_Q;
     Buf<DeviceStatus> stat;
     Buf<unsigned long long> ticket;  // bin counter of the mode passes
     unsigned long long ticket_base = 0;
-    StreamBuf<double> red;         // reduction scratch
+    Buf<double> red;               // reduction scratch
     Buf<int64_t> d_dims;
-    StreamBuf<int32_t> f_other;    // fold-in scratch
-    StreamBuf<T> f_x, f_out, f_part;
-    StreamBuf<int64_t> f_meta;     // tiled fold-in block table / request offsets / status
-    StreamBuf<int32_t> p_coords;   // tf_predict staging
-    StreamBuf<T> p_out;
+    Buf<int32_t> f_other;          // fold-in scratch
+    Buf<T> f_x, f_out, f_part;
+    Buf<int64_t> f_meta;           // tiled fold-in block table / request offsets / status
+    Buf<int32_t> p_coords;         // tf_predict staging
+    Buf<T> p_out;
     int32_t *h_order = nullptr;    // pinned staging of the column order
     cudaEvent_t order_ev = nullptr;
     bool order_pending = false;
@@ -156,14 +184,21 @@ struct Impl : CtxBase {
     int64_t last_path = 0;  // mode-pass paths of the last sweep: bit 0 cp.async, bit 1 TMA
     int64_t launches = 0;
 
+    // Every device buffer of the context (tf_set_stream moves their frees to the new stream).
+    template <class F>
+    void each_buf(F f) {
+        f(x), f(partials), f(d_order), f(d_Q), f(stat), f(ticket), f(red), f(d_dims);
+        f(f_other), f(f_x), f(f_out), f(f_part), f(f_meta), f(p_coords), f(p_out);
+        for (int n = 0; n < kMaxModes; ++n) {
+            f(A[n]), f(res[n]), f(Z[n]);
+            mode[n].each_buf(f);
+        }
+    }
+
     ~Impl() override {
-        // the stream-ordered scratch goes back to the pool behind the last work on st
-        for (auto *b : {&f_other, &p_coords}) b->release(st);
-        for (auto *b : {&f_x, &f_out, &f_part, &p_out, &partials}) b->release(st);
-        f_meta.release(st);
-        red.release(st);
-        cudaStreamSynchronize(st);
-        if (h_order) cudaFreeHost(h_order);
+        // device buffers go back to the pool behind the last work on st (their destructors)
+        if (order_pending) cudaEventSynchronize(order_ev);  // the last copy out of h_order
+        if (h_order) pinned_cache().put(h_order, sizeof(int32_t) * (size_t)K);
         if (order_ev) cudaEventDestroy(order_ev);
         for (auto &pr : prof_pending) {
             cudaEventDestroy(pr.first);
@@ -245,34 +280,34 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaGetDevice(&dev));
         TFS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
         P = num_sms * 32;
-        stat.alloc(1);
+        stat.alloc(1, st);
         TFS_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(DeviceStatus), st));
-        ticket.alloc(1);
+        ticket.alloc(1, st);
         TFS_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned long long), st));
         ticket_base = 0;
         red.ensure(4096, st);
-        d_dims.alloc(N);
+        d_dims.alloc(N, st);
         TFS_CUDA(cudaMemcpyAsync(d_dims.p, dims.data(), N * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st));
-        TFS_CUDA(cudaMallocHost(&h_order, sizeof(int32_t) * (size_t)K));
+        h_order = static_cast<int32_t *>(pinned_cache().get(sizeof(int32_t) * (size_t)K));
         TFS_CUDA(cudaEventCreateWithFlags(&order_ev, cudaEventDisableTiming));
-        d_order.alloc(K);
-        d_Q.alloc(K);
+        d_order.alloc(K, st);
+        d_Q.alloc(K, st);
 
         const bool on_dev = flags & TF_INPUT_DEVICE;
         const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        x.alloc(nnz);
+        x.alloc(nnz, st);
         if (nnz > 0)
             TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), kind, st));
 
         // canonical coordinates -> SoA with range check
         Buf<int32_t> soa;
-        soa.alloc((size_t)N * nnz);
+        soa.alloc((size_t)N * nnz, st);
         {
             Buf<int32_t> rowmajor;
             const int32_t *src = coords;
             if (!on_dev && nnz > 0) {
-                rowmajor.alloc((size_t)N * nnz);
+                rowmajor.alloc((size_t)N * nnz, st);
                 TFS_CUDA(cudaMemcpyAsync(rowmajor.p, coords, (size_t)N * nnz * sizeof(int32_t),
                                          cudaMemcpyHostToDevice, st));
                 src = rowmajor.p;
@@ -286,13 +321,13 @@ struct Impl : CtxBase {
         // per-mode sorted layout
         SortWorkspace ws;
         Buf<uint32_t> keys;
-        keys.alloc(nnz);
+        keys.alloc(nnz, st);
         try {
             for (int n = 0; n < N; ++n) {
                 ModeLayout &L = mode[n];
                 L.I = dims[n];
-                L.perm.alloc(nnz);
-                L.off.alloc(L.I + 1);
+                L.perm.alloc(nnz, st);
+                L.off.alloc(L.I + 1, st);
                 launch_iota(L.perm.p, nnz, st);
                 for (int t = N - 1; t >= 0; --t) {  // least significant mode first
                     const int m = (n + t) % N;
@@ -322,8 +357,8 @@ struct Impl : CtxBase {
                     return off[a_ + 1] - off[a_] > off[b_ + 1] - off[b_];
                 });
                 for (int64_t r = 0; r < L.I; ++r) rank[id[r]] = (int32_t)r;
-                L.id_of.alloc(L.I);
-                L.rank_of.alloc(L.I);
+                L.id_of.alloc(L.I, st);
+                L.rank_of.alloc(L.I, st);
                 TFS_CUDA(cudaMemcpyAsync(L.id_of.p, id.data(), L.I * sizeof(int32_t),
                                          cudaMemcpyHostToDevice, st));
                 TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, rank.data(), L.I * sizeof(int32_t),
@@ -335,7 +370,7 @@ struct Impl : CtxBase {
                 // index arrays start 256-byte aligned and end in 64 padding entries
                 // (bulk copies read fixed windows past a step's last entry)
                 L.ostride = (nnz + 64 + 63) / 64 * 64;
-                L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride);
+                L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride, st);
                 TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0,
                                          (size_t)std::max(N - 1, 1) * L.ostride * sizeof(int32_t), st));
                 int t = 0;
@@ -348,10 +383,10 @@ struct Impl : CtxBase {
                 }
             }
         } catch (...) {
-            ws.release();
+            ws.release(st);
             throw;
         }
-        ws.release();
+        ws.release(st);
         keys.reset();
         soa.reset();
 
@@ -360,12 +395,12 @@ struct Impl : CtxBase {
         // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
         const double std = pow((double)K, -1.0 / (2.0 * N));
         for (int n = 0; n < N; ++n) {
-            A[n].alloc((size_t)dims[n] * K);
+            A[n].alloc((size_t)dims[n] * K, st);
             if (n == 0)
                 TFS_CUDA(cudaMemsetAsync(A[n].p, 0, (size_t)dims[n] * K * sizeof(T), st));
             else
                 launch_init_normal<T>(A[n].p, dims[n] * K, seed, (uint64_t)n, std, st);
-            res[n].alloc(nnz + 64);
+            res[n].alloc(nnz + 64, st);
             TFS_CUDA(cudaMemsetAsync(res[n].p, 0, (nnz + 64) * sizeof(T), st));
         }
         a0_zero = true;
@@ -404,10 +439,10 @@ struct Impl : CtxBase {
         L.n_slots = n_slots;
         L.n_split = (int)split.size();
         L.n_single = (int)single.size();
-        L.items.alloc(items.size());
-        L.bin_ptr.alloc(bin_ptr.size());
-        L.split.alloc(split.size());
-        L.single.alloc(single.size());
+        L.items.alloc(items.size(), st);
+        L.bin_ptr.alloc(bin_ptr.size(), st);
+        L.split.alloc(split.size(), st);
+        L.single.alloc(single.size(), st);
         if (!single.empty())
             TFS_CUDA(cudaMemcpyAsync(L.single.p, single.data(), single.size() * sizeof(SplitRow),
                                      cudaMemcpyHostToDevice, st));
@@ -540,7 +575,7 @@ struct Impl : CtxBase {
         int64_t max_slots = 0;
         for (int n = 0; n < N; ++n) {
             if (Z[n].n < (size_t)dims[n] * W) {
-                Z[n].alloc((size_t)dims[n] * W);
+                Z[n].alloc((size_t)dims[n] * W, st);
                 TFS_CUDA(cudaMemsetAsync(Z[n].p, 0, Z[n].n * sizeof(T), st));
             }
             max_slots = std::max(max_slots, mode[n].n_slots);
@@ -837,7 +872,7 @@ struct Impl : CtxBase {
     void get_residual(T *host_r) {
         if (dirty) rebuild_residuals();
         Buf<T> out;
-        out.alloc(nnz);
+        out.alloc(nnz, st);
         const ModeLayout &L = mode[0];
         ResArgs<T> a{};
         a.items = L.items.p;
@@ -1381,10 +1416,95 @@ tf_status tf_get_launch_trace(tf_ctx *ctx, int64_t cap, int64_t *n, int32_t *kin
     return dispatch(ctx, [&](auto &c) { c.launch_trace(cap, n, kinds, modes, ms); });
 }
 
+tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int C_max,
+                            tf_dtype dtype, uint32_t flags, int num_sms, int64_t *bytes) {
+    if (!dims || !bytes || N < 1 || N > tfs::kMaxModes || nnz < 0 || K < 1 || C_max < 1 ||
+        C_max > K || (dtype != TF_F32 && dtype != TF_F64))
+        return TF_EINVAL;
+    for (int n = 0; n < N; ++n)
+        if (dims[n] < 1) return TF_EINVAL;
+    const int CM = tfs::pick_cm(C_max);
+    if (CM == 0) return TF_EINVAL;
+    if (num_sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return TF_ECUDA;
+        }
+    }
+    // the same sizes tf_create and the sweeps allocate (see Impl::create / Impl::sweep)
+    const double T = dtype == TF_F32 ? 4.0 : 8.0;
+    const double P = (double)num_sms * 32.0;
+    const double e = (double)nnz, ostride = (double)((nnz + 64 + 63) / 64 * 64);
+    const int W = tfs::slice_stride_elems(CM, (int)T);
+    double layout = 0, plan = 0, factors = 0, maxI = 0;
+    for (int n = 0; n < N; ++n) {
+        const double I = (double)dims[n];
+        layout += e * 4 + (I + 1) * 8 + I * 8 + std::max(N - 1, 1) * ostride * 4;
+        plan += (I + P) * sizeof(tf_item) + (P + 1) * 8 + I * sizeof(tfs::SplitRow);
+        factors += I * K * T + (e + 64) * T + I * W * T;
+        maxI = std::max(maxI, I);
+    }
+    const double base = 4096.0 * 8 + 2.0 * K * 4 + N * 8 + 1024;
+    const double x = e * T, soa = (double)N * e * 4;
+    const double host_copy = (flags & TF_INPUT_DEVICE) ? 0.0 : (double)N * e * 4;
+    const double transpose = x + soa + host_copy;
+    const double sorting = x + soa + e * 4 + (double)tfs::sort_workspace_bytes(nnz) + layout;
+    const double partials = (maxI + P) * tfs::partial_stride(CM) * T;
+    const double steady = x + layout + plan + factors + partials;
+    // stream-ordered pool rounding: large buffers round up to the pool's 2 MiB mapping
+    // granularity (at most 2 MiB each), small ones share chunks
+    const double raw = base + std::max(transpose, std::max(sorting, steady));
+    const double mib2 = 2.0 * 1024 * 1024;
+    const double rounding = std::min(0.05 * raw, (16.0 + 12.0 * N) * mib2) + mib2;
+    *bytes = (int64_t)(raw + rounding);
+    return TF_OK;
+}
+
+tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int reset_high) {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TF_ECUDA;
+    }
+    uint64_t a = 0, b = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &a) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &b) != cudaSuccess) {
+        cudaGetLastError();
+        return TF_ECUDA;
+    }
+    if (used) *used = (int64_t)a;
+    if (used_high) *used_high = (int64_t)b;
+    if (reset_high) {
+        uint64_t zero = 0;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) {
+            cudaGetLastError();
+            return TF_ECUDA;
+        }
+    }
+    return TF_OK;
+}
+
+tf_status tf_get_shape(tf_ctx *ctx, int *N, int *K, tf_dtype *dtype) {
+    return dispatch(ctx, [&](auto &c) {
+        if (N) *N = c.N;
+        if (K) *K = c.K;
+        if (dtype) *dtype = sizeof(*c.x.p) == 4 ? TF_F32 : TF_F64;
+    });
+}
+
+tf_status tf_get_stream(tf_ctx *ctx, void **stream) {
+    if (!stream) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { *stream = (void *)c.st; });
+}
+
 tf_status tf_set_stream(tf_ctx *ctx, void *stream) {
     return dispatch(ctx, [&](auto &c) {
         TFS_CUDA(cudaStreamSynchronize(c.st));
         c.st = (cudaStream_t)stream;
+        c.each_buf([&](auto &b) { b.s = c.st; });
     });
 }
 

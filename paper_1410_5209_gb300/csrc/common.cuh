@@ -84,9 +84,17 @@ struct SortWorkspace {
     uint32_t *hist = nullptr;
     uint32_t *scan_tmp = nullptr;
     size_t cap_items = 0, cap_hist = 0, cap_scan = 0;
-    void reserve(int64_t n);
-    void release();
+    void reserve(int64_t n, cudaStream_t st);  // stream-ordered allocations on st
+    void release(cudaStream_t st);
 };
+
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// and never lowers it.  The limit is one per kernel for the whole process, and contexts
+// driven from other host threads may launch the same kernel with other sizes meanwhile:
+// lowering it between another thread's set and launch would fail that launch.
+cudaError_t raise_smem_limit(const void *kern, int bytes);
+
+size_t sort_workspace_bytes(int64_t n);  // device bytes SortWorkspace::reserve(n) holds
 
 void radix_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int bits, SortWorkspace &ws,
                       cudaStream_t st);

@@ -271,8 +271,7 @@ void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream
         TFS_CUDA(cudaGetLastError());
     }
     const size_t smem = sizeof(T) * ((size_t)a.K * (a.K + 1) / 2 + a.K);
-    TFS_CUDA(cudaFuncSetAttribute(k_fold_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)k_fold_solve<T>, (int)smem));
     k_fold_solve<T><<<n_req, 32, smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }
@@ -285,8 +284,7 @@ size_t foldin_smem_bytes(int K) {
 template <class T>
 void launch_foldin(const FoldArgs<T> &a, cudaStream_t st) {
     const size_t smem = foldin_smem_bytes<T>(a.K);
-    TFS_CUDA(cudaFuncSetAttribute(k_foldin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)k_foldin<T>, (int)smem));
     k_foldin<T><<<1, kFoldThreads, smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }

@@ -875,8 +875,7 @@ PassPlan mode_pass_plan_cm(int N, int n, int num_sms, int P) {
 template <class T, int CM>
 void launch_mode_pass_cm(const PassArgs<T> &a, const PassPlan &plan, cudaStream_t st) {
     auto kern = mode_pass_kernel<T, CM>(a.N, a.first != 0);
-    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)plan.smem));
+    TFS_CUDA(raise_smem_limit((const void *)kern, (int)plan.smem));
     kern<<<plan.grid, plan.warps * kWarp, plan.smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }
@@ -905,8 +904,7 @@ template <class T, int CM>
 void launch_res_cm(const ResArgs<T> &a, cudaStream_t st) {
     const int wpb = res_warps<T, CM>(a.N);
     const size_t smem = wpb * res_warp_bytes<T, CM>(a.N);
-    TFS_CUDA(cudaFuncSetAttribute(k_res<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)k_res<T, CM>, (int)smem));
     k_res<T, CM><<<res_blocks(a.P, wpb), wpb * kWarp, smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
 }

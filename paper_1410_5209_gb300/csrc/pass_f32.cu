@@ -130,8 +130,7 @@ namespace {
 template <int CM>
 void tma_launch_cm(const TmaPassArgs &ta, const TmaPlan &plan, bool first, cudaStream_t st) {
     auto kern = tma_kernel<CM>(first);
-    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)plan.smem));
+    TFS_CUDA(raise_smem_limit((const void *)kern, (int)plan.smem));
     kern<<<plan.grid, plan.warps * kWarp, plan.smem, st>>>(ta);
     TFS_CUDA(cudaGetLastError());
 }

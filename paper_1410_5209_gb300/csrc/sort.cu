@@ -250,39 +250,38 @@ void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
     }
 }
 
-void SortWorkspace::reserve(int64_t n) {
+void SortWorkspace::reserve(int64_t n, cudaStream_t st) {
     const size_t items = (size_t)(n > 0 ? n : 1);
     const size_t ntiles = (size_t)ceil_div<int64_t>(n > 0 ? n : 1, kTile);
     const size_t hist = ntiles * kDigits;
     const size_t scan = scan_temp_elems((int64_t)hist);
-    if (items > cap_items) {
-        if (keys_alt) cudaFree(keys_alt);
-        if (vals_alt) cudaFree(vals_alt);
-        keys_alt = nullptr;
-        vals_alt = nullptr;
-        TFS_CUDA(cudaMalloc(&keys_alt, items * sizeof(uint32_t)));
-        TFS_CUDA(cudaMalloc(&vals_alt, items * sizeof(int32_t)));
-        cap_items = items;
-    }
-    if (hist > cap_hist) {
-        if (this->hist) cudaFree(this->hist);
-        this->hist = nullptr;
-        TFS_CUDA(cudaMalloc(&this->hist, hist * sizeof(uint32_t)));
-        cap_hist = hist;
-    }
-    if (scan > cap_scan) {
-        if (scan_tmp) cudaFree(scan_tmp);
-        scan_tmp = nullptr;
-        TFS_CUDA(cudaMalloc(&scan_tmp, scan * sizeof(uint32_t)));
-        cap_scan = scan;
-    }
+    auto regrow = [&](auto *&p, size_t &cap, size_t want) {
+        if (want <= cap) return;
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        cap = 0;
+        TFS_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&p), want * sizeof(*p), st));
+        cap = want;
+    };
+    size_t cap_vals = cap_items;
+    regrow(keys_alt, cap_items, items);
+    regrow(vals_alt, cap_vals, items);
+    regrow(this->hist, cap_hist, hist);
+    regrow(scan_tmp, cap_scan, scan);
 }
 
-void SortWorkspace::release() {
-    if (keys_alt) cudaFree(keys_alt);
-    if (vals_alt) cudaFree(vals_alt);
-    if (hist) cudaFree(hist);
-    if (scan_tmp) cudaFree(scan_tmp);
+size_t sort_workspace_bytes(int64_t n) {
+    const size_t items = (size_t)(n > 0 ? n : 1);
+    const size_t hist = (size_t)ceil_div<int64_t>(n > 0 ? n : 1, kTile) * kDigits;
+    return items * (sizeof(uint32_t) + sizeof(int32_t)) +
+           (hist + scan_temp_elems((int64_t)hist)) * sizeof(uint32_t);
+}
+
+void SortWorkspace::release(cudaStream_t st) {
+    if (keys_alt) cudaFreeAsync(keys_alt, st);
+    if (vals_alt) cudaFreeAsync(vals_alt, st);
+    if (hist) cudaFreeAsync(hist, st);
+    if (scan_tmp) cudaFreeAsync(scan_tmp, st);
     keys_alt = nullptr;
     vals_alt = nullptr;
     hist = nullptr;
@@ -293,7 +292,7 @@ void SortWorkspace::release() {
 void radix_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int bits, SortWorkspace &ws,
                       cudaStream_t st) {
     if (n <= 1 || bits <= 0) return;
-    ws.reserve(n);
+    ws.reserve(n, st);
     const int64_t ntiles = ceil_div<int64_t>(n, kTile);
     uint32_t *kin = keys, *kout = ws.keys_alt;
     int32_t *vin = vals, *vout = ws.vals_alt;

@@ -4,9 +4,26 @@
 // initialisation (Section 3.1) and the default factor initialisation (Algorithm 1).
 #include <math.h>
 
+#include <map>
+#include <mutex>
+
 #include "sweep.cuh"
 
 namespace tfs {
+
+cudaError_t raise_smem_limit(const void *kern, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> limit;  // (device, kernel) -> bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    int &cur = limit[{dev, kern}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 int pick_cm(int C) {
     static const int cms[] = {1, 2, 4, 6, 8, 10, 12, 16};

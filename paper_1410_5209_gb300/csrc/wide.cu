@@ -595,7 +595,7 @@ void launch_pass_wide_tc_cw(const PassArgs<float> &a, int CM, int W, int grid, b
     smem = std::max<size_t>(smem, tc_min_smem(CW));
     auto kern = split ? (a.first ? k_pass_wide_tc<CW, true, true> : k_pass_wide_tc<CW, false, true>)
                       : (a.first ? k_pass_wide_tc<CW, true, false> : k_pass_wide_tc<CW, false, false>);
-    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)kern, (int)smem));
     kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
     TFS_CUDA(cudaGetLastError());
 }
@@ -605,7 +605,7 @@ void launch_pass_wide_cw(const PassArgs<T> &a, int CM, int W, int grid, cudaStre
     const size_t smem = sizeof(T) * ((size_t)kWideTile * (CW + 4) + 2 * (size_t)CM + 2 * kWideTile) +
                         sizeof(int32_t) * 2 * (size_t)kWideTile * (kMaxModes - 1);
     auto kern = a.first ? k_pass_wide<T, CW, true> : k_pass_wide<T, CW, false>;
-    TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)kern, (int)smem));
     kern<<<grid, kWideThreads, smem, st>>>(a, CM, W);
     TFS_CUDA(cudaGetLastError());
 }
@@ -645,7 +645,7 @@ int pass_wide_grid(int num_sms, int P, int C, int CM, bool tensor_cores, bool fi
             kern = first ? (const void *)k_pass_wide<T, 64, true> : (const void *)k_pass_wide<T, 64, false>;
         else
             kern = first ? (const void *)k_pass_wide<T, 128, true> : (const void *)k_pass_wide<T, 128, false>;
-        TFS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TFS_CUDA(raise_smem_limit((const void *)kern, (int)smem));
         TFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWideThreads, smem));
         per_sm = std::max(1, std::min(per_sm, 8));
     }
@@ -697,8 +697,7 @@ void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, i
     const size_t per_warp = sizeof(T) * ((size_t)a.C * (a.C + 1) / 2 + a.C);
     const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kSolveWarps, smem_blk / per_warp));
     const size_t smem = per_warp * wpb;
-    TFS_CUDA(cudaFuncSetAttribute(k_solve_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    TFS_CUDA(raise_smem_limit((const void *)k_solve_wide<T>, (int)smem));
     k_solve_wide<T><<<(n_rows + wpb - 1) / wpb, wpb * 32, smem, st>>>(a, rows, n_rows, CM, W);
     TFS_CUDA(cudaGetLastError());
 }
