@@ -282,6 +282,87 @@ def batched(args, rank, world):
     return 0
 
 
+def serve_with_jobs(args, f, p, lam):
+    """Fold-in requests and factorisation jobs through the serving loop (tf_server.h), in
+    real time: Poisson arrivals of both kinds submitted from this thread; the server
+    admits jobs against free device memory (each on its own stream and host thread) and
+    batches the fold-ins continuously on a high-priority stream against the frozen model
+    `f`.  Fold-in latency is the server's own submission-to-result time."""
+    import numpy as np
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    rng = np.random.default_rng(args.seed + 53)
+    reqs = synth.foldin_requests(p, args.serve_server_requests, args.seed + 59)
+    # jobs shaped like the batched workload's tensors: mode lengths log-uniform in
+    # [50, 5000], entries log-uniform in [1e3, 1e6], rank-16 truth, K = 16, C = 4
+    u = rng.random((args.serve_jobs, 4))
+    jobs = []
+    for b in range(args.serve_jobs):
+        dims = [int(math.exp(math.log(50) + u[b, n] * (math.log(5000) - math.log(50))))
+                for n in range(3)]
+        nnz = int(math.exp(math.log(1e3) + u[b, 3] * (math.log(1e6) - math.log(1e3))))
+        q = synth.make_problem(dims, nnz, 16, 16, args.seed * 7919 + b, dtype=torch.float32,
+                               device="cuda")
+        c, x = q.numpy()
+        jobs.append((c, x.astype(np.float32), q.dims))
+    job_sweeps, job_C = 5, 4
+    srv = tf.Server(f, max_running=8, max_batch=args.serve_batch)
+    # warm-up: one job and a few fold-ins
+    wj = srv.submit_job(*jobs[0], 16, job_C, lam, 1, seed=1)
+    for o, v in reqs[:8]:
+        srv.wait_foldin(srv.submit_foldin(0, o, v, lam))
+    srv.wait_job(wj)
+    srv.release_job(wj)
+    tf_ = np.cumsum(rng.exponential(1.0 / args.serve_server_rate, len(reqs)))
+    tj = np.cumsum(rng.exponential(1.0 / args.serve_job_rate, len(jobs)))
+    fids, jids, lag = [], [], []
+    t0 = time.perf_counter()
+
+    def submit_jobs():   # jobs from a second host thread (the input copy releases the GIL)
+        for i, t in enumerate(tj):
+            while time.perf_counter() - t0 < t:
+                time.sleep(0)
+            c, x, dims = jobs[i]
+            jids.append(srv.submit_job(c, x, dims, 16, job_C, lam, job_sweeps, seed=i))
+
+    th = threading.Thread(target=submit_jobs)
+    th.start()
+    for i, t in enumerate(tf_):
+        while time.perf_counter() - t0 < t:
+            pass
+        lag.append(time.perf_counter() - t0 - t)
+        fids.append(srv.submit_foldin(0, reqs[i][0], reqs[i][1], lam))
+    t_sub = time.perf_counter() - t0
+    lat = np.array([srv.wait_foldin(r)[2] for r in fids])
+    t_f = time.perf_counter() - t0
+    th.join()
+    infos = [srv.wait_job(j) for j in jids]
+    t_all = time.perf_counter() - t0
+    assert all(i["state"] == tf.JOB_DONE for i in infos), infos
+    for j in jids:
+        srv.release_job(j)
+    st = srv.stats()
+    srv.close()
+    jlat = np.array([i["finished_s"] - i["queued_s"] for i in infos])
+    jwait = np.array([i["started_s"] - i["queued_s"] for i in infos])
+    return {"foldin_p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "foldin_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "foldin_req_per_s": len(fids) / t_f, "foldin_offered_req_per_s": args.serve_server_rate,
+            "foldin_requests": len(fids), "foldin_batches": st["foldin_batches"],
+            "foldin_submitted_per_s": len(fids) / t_sub,
+            "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3),
+            "jobs": len(jids), "job_p50_ms": float(np.percentile(jlat, 50) * 1e3),
+            "job_p99_ms": float(np.percentile(jlat, 99) * 1e3),
+            "job_admission_wait_p99_ms": float(np.percentile(jwait, 99) * 1e3),
+            "jobs_per_s": len(jids) / t_all, "job_offered_per_s": args.serve_job_rate,
+            "job_entries": [int(j[1].shape[0]) for j in jobs],
+            "running_peak": st["running_peak"], "bytes_admitted_peak": st["bytes_admitted_peak"],
+            "what": "tf_server: Poisson fold-ins (new mode-1 slices, K=100) and Poisson "
+                    f"factorisation jobs ({job_sweeps} sweeps, K=16, C={job_C}) admitted "
+                    "against free device memory, in real time"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,7 +379,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-batch", type=int, default=256)
-    ap.add_argument("--serve-mix-nnz", type=int, default=20_000_000)
+    ap.add_argument("--serve-jobs", type=int, default=24,
+                    help="factorisation jobs mixed into the server-driven fold-in stream")
+    ap.add_argument("--serve-job-rate", type=float, default=40.0)
+    ap.add_argument("--serve-server-rate", type=float, default=10000.0)
+    ap.add_argument("--serve-server-requests", type=int, default=4000)
     ap.add_argument("--study", action="store_true",
                     help="C-sweep and row-assignment policy study instead of the benchmark")
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
@@ -467,39 +552,8 @@ def main():
 
         out["serving"] = {**serve(), "what": "Poisson fold-in arrivals, continuous batching "
                           "through tf_foldin_batch (latency = arrival -> rows on host)"}
-        if args.serve_mix_nnz > 0:
-            # the same arrivals while a factorisation job sweeps on a second stream from its
-            # own host thread: its kernels and the fold-ins share the GPU
-            import threading
-            q = synth.skewed_3way(seed=args.seed + 41, nnz=args.serve_mix_nnz, device="cuda")
-            s2 = torch.cuda.Stream()
-            g = tf.Factorization(q.coords, q.x, q.dims, K, seed=args.seed + 41, dtype=tf.F32,
-                                 stream=s2.cuda_stream, device_input=True)
-            stop, done = threading.Event(), [0]
-
-            def job():
-                while not stop.is_set():
-                    g.sweep(C, lam, T_in)
-                    done[0] += 1
-
-            # the serving context moves to a high-priority stream: its fold-in kernels are
-            # started as soon as the background job's blocks free an SM
-            hi = torch.cuda.Stream(priority=-1)
-            f.set_stream(hi)
-            th = threading.Thread(target=job)
-            th.start()
-            time.sleep(0.2)
-            mixed = serve()
-            stop.set()
-            th.join()
-            torch.cuda.synchronize()
-            f.set_stream(stream)
-            out["serving_mixed"] = {**mixed, "background_sweeps": done[0],
-                                    "what": "as serving (on a high-priority stream), with "
-                                            f"sweeps of a {q.nnz}-entry skewed tensor (K={K}, "
-                                            f"C={C}) running on a second stream meanwhile"}
-            g.close()
-            del q
+        if args.serve_jobs > 0:
+            out["serving_server"] = serve_with_jobs(args, f, p, lam)
     f.close()
     del f
 
