@@ -256,9 +256,17 @@ def batched(args, rank, world):
     t0 = time.perf_counter()
     p, row_off, ent_off = synth.batched(args.batched, seed=args.seed, K=K, device="cuda")
     gen_s = time.perf_counter() - t0
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()   # a capturable stream: sweeps replay as CUDA graphs
     f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
                          stream=stream.cuda_stream, device_input=True)
+    f.set_graphs(True)
+    tune = None
+    if args.autotune:
+        Cs, Ps = [2, 4, 8, 16], [0, 152 * 32, 152 * 192]
+        bc, bp, tms = f.autotune(Cs, Ps, lam=lam)
+        tune = {"C": Cs, "P": [p_ or "default" for p_ in Ps], "ms": tms.round(3).tolist(),
+                "best_C": bc, "best_P": bp or "default"}
+        f.set_schedule(tf.SCHED_LPT, 0)   # the timed sweeps below keep the default schedule
     for s_ in range(args.warmup):
         f.sweep(C, lam, 1)
     f.loss(lam)
@@ -275,11 +283,50 @@ def batched(args, rank, world):
     print(json.dumps({"metric": "nnz*rank updates/s per SALS sweep (batch of tensors)",
                       "value": p.nnz * K / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms,
                       "tensors": args.batched, "nnz": p.nnz, "dims_total": p.dims, "K": K,
-                      "C": C, "launches_per_sweep": cnt["last_sweep_launches"],
+                      "C": C, "kernels_per_sweep": cnt["last_sweep_launches"],
+                      "graph_launches_per_sweep": 1 if f.graph_info()["replays"] else None,
+                      "autotune": tune,
                       "train_rmse": rmse, "generate_s": gen_s, "dtype": "f32",
                       "data": "synthetic"}), flush=True)
     f.close()
     return 0
+
+
+def small_sweeps(args):
+    """The 1e5-entry FP64 parity workload (1000 x 1000 x 100, K = 10), C = 1 (CDTF) and
+    C = 5: device time per sweep with eager launches and with the sweep replayed as a
+    CUDA graph (tf_set_graphs).  At this size a sweep is launch-bound."""
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    p = synth.parity_3way(seed=1, device="cuda")
+    s = torch.cuda.Stream()
+    out = {}
+    for C in (1, 5):
+        row = {}
+        for graphs in (False, True):
+            f = tf.Factorization(p.coords, p.x, p.dims, p.K, seed=1, dtype=tf.F64,
+                                 stream=s.cuda_stream, device_input=True)
+            f.set_graphs(graphs)
+            for _ in range(3):
+                f.sweep(C, 1.0, 1)
+            f.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(s)
+            for _ in range(reps):
+                f.sweep(C, 1.0, 1)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row["graph_ms" if graphs else "eager_ms"] = ms
+            row["launches_per_sweep"] = f.counters()["last_sweep_launches"]
+            f.close()
+        row["nnz_rank_per_s_graph"] = p.nnz * p.K / (row["graph_ms"] / 1e3)
+        out[f"C={C}"] = row
+    out["what"] = ("1e5-entry FP64 parity workload, K=10: ms per sweep, eager launches vs "
+                   "one CUDA-graph launch per sweep")
+    return out
 
 
 def serve_with_jobs(args, f, p, lam):
@@ -379,6 +426,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-batch", type=int, default=256)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="with --batched: time (C, P) candidates with tf_autotune first")
+    ap.add_argument("--small-sweeps", type=int, default=1,
+                    help="1: time the 1e5-entry parity workload eager vs CUDA graphs")
     ap.add_argument("--serve-jobs", type=int, default=24,
                     help="factorisation jobs mixed into the server-driven fold-in stream")
     ap.add_argument("--serve-job-rate", type=float, default=40.0)
@@ -556,6 +607,8 @@ def main():
             out["serving_server"] = serve_with_jobs(args, f, p, lam)
     f.close()
     del f
+    if args.small_sweeps:
+        out["small_sweeps"] = small_sweeps(args)
 
     # end to end through the C ABI from pinned host buffers: upload + layout + one sweep
     # + loss + factors back, per step

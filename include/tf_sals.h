@@ -107,6 +107,33 @@ const char *tf_last_error(const tf_ctx *ctx);
 /* Waits for the context's stream and reports any device-side error. */
 tf_status tf_sync(tf_ctx *ctx);
 
+/* enable = 1: sweeps run as CUDA graphs.  The launches of a sweep (pack, mode passes,
+ * solves, for every split) depend only on C, T_in, lambda, flags, the columns left from
+ * the previous sweep and the context's settings; the second sweep with a given such key is
+ * captured into a graph and every later one replays it -- one launch per sweep.  Results
+ * are bit-identical to eager sweeps.  Up to 8 graphs are kept per context (least recently
+ * used dropped).  Not used while profiling (tf_profile) or on the legacy default stream.
+ * enable = 0 (the default) drops the graphs.  The paper has no counterpart. */
+tf_status tf_set_graphs(tf_ctx *ctx, int enable);
+
+/* Picks the fastest (P, C) pair for this tensor by measurement: for every bin count
+ * P_list[i] (0 = the default of tf_set_schedule; it sets how many rows' work one warp takes, the
+ * rows-per-CTA knob of the mode passes) and every subset size C_list[j], one sweep
+ * (lambda, T_in, flags as tf_sals_sweep_ex, default column order) is timed on the device
+ * after an untimed sweep from the same state.  The state before the call (factors,
+ * residuals, the previous subset's columns, the sweep counter) is restored bit for bit
+ * after every trial and at the end, so later sweeps give what they would have given
+ * without the call -- on the schedule of *best_P, which the context keeps.  Times go to
+ * ms[i * n_C + j] (may be NULL).  Needs device memory for one copy of the factors and
+ * residuals.  Speed only: a C that converges per sweep more slowly is not penalised.
+ * The paper picks C by hand from its experiments (Section 5); it has no autotuner. */
+tf_status tf_autotune(tf_ctx *ctx, const int32_t *C_list, int n_C, const int32_t *P_list,
+                      int n_P, double lambda, int T_in, uint32_t flags, int32_t *best_C,
+                      int32_t *best_P, float *ms);
+
+/* Sweeps run from a graph so far, and graphs held. */
+tf_status tf_graph_info(tf_ctx *ctx, int64_t *replays, int64_t *cached);
+
 /* The context's mode count, rank and dtype (any output may be NULL). */
 tf_status tf_get_shape(tf_ctx *ctx, int *N, int *K, tf_dtype *dtype);
 
@@ -244,7 +271,10 @@ tf_status tf_get_residual(tf_ctx *ctx, void *host_r);
 tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
 
 /* Re-plans the row schedule of every mode (policy, P bins; P = 0 picks the default
- * for this GPU).  Results do not depend on the schedule. */
+ * for this GPU and tensor: 128 bins per SM, fewer for small tensors so that a bin holds
+ * 64 entries on average, at least 4 per SM).  The schedule changes only the order in which a row's
+ * partial sums are added (heavy rows are split into chunks of at most |Omega| / P
+ * entries), so results agree to rounding. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
 /* Data path of the mode pass: 0 = automatic (C <= 16: the cp.async SIMT pass, whose

@@ -89,6 +89,9 @@ def load():
         "tf_plan_mode": [P, i64, i32, i64, i32, u64, P, i64, P, P, P],
         "tf_version": [],
         "tf_get_shape": [P, P, P, P],
+        "tf_set_graphs": [P, i32],
+        "tf_autotune": [P, P, i32, P, i32, f64, i32, u32, P, P, P],
+        "tf_graph_info": [P, P, P],
         "tf_get_stream": [P, P],
         "tf_estimate_bytes": [P, i32, i64, i32, i32, i32, u32, i32, P],
         "tf_pool_usage": [P, P, i32],
@@ -308,6 +311,28 @@ class Factorization:
 
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
+
+    def set_graphs(self, enable=True):
+        """Run sweeps as CUDA graphs (captured on a shape's second sweep, then replayed)."""
+        self._check(self._lib.tf_set_graphs(self._ctx, 1 if enable else 0))
+
+    def autotune(self, C_list, P_list=(0,), lam=0.1, T_in=1, weighted=False):
+        """Fastest (C, P) by one timed sweep each; state restored, best P kept.
+        Returns (best_C, best_P, ms [len(P_list)][len(C_list)])."""
+        cl = np.ascontiguousarray(C_list, np.int32)
+        pl = np.ascontiguousarray(P_list, np.int32)
+        ms = np.zeros((len(pl), len(cl)), np.float32)
+        bc, bp = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.tf_autotune(self._ctx, _ptr(cl), len(cl), _ptr(pl), len(pl),
+                                          float(lam), int(T_in),
+                                          WEIGHTED_LAMBDA if weighted else 0,
+                                          ctypes.byref(bc), ctypes.byref(bp), _ptr(ms)))
+        return bc.value, bp.value, ms
+
+    def graph_info(self):
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.tf_graph_info(self._ctx, ctypes.byref(r), ctypes.byref(c)))
+        return {"replays": r.value, "cached": c.value}
 
     def set_stream(self, stream):
         """Queue later work on `stream` (a cudaStream_t handle as int, or a torch stream)."""

@@ -183,6 +183,7 @@ struct Impl : CtxBase {
     int64_t sweeps = 0, last_launches = 0, loss_launches = 0;
     int64_t last_path = 0;  // mode-pass paths of the last sweep: bit 0 cp.async, bit 1 TMA
     int64_t launches = 0;
+    int64_t layout_gen = 0;  // bumped whenever the row schedule is rebuilt
 
     // Every device buffer of the context (tf_set_stream moves their frees to the new stream).
     template <class F>
@@ -196,6 +197,7 @@ struct Impl : CtxBase {
     }
 
     ~Impl() override {
+        drop_graphs();
         // device buffers go back to the pool behind the last work on st (their destructors)
         if (order_pending) cudaEventSynchronize(order_ev);  // the last copy out of h_order
         if (h_order) pinned_cache().put(h_order, sizeof(int32_t) * (size_t)K);
@@ -279,7 +281,7 @@ struct Impl : CtxBase {
         int dev = 0;
         TFS_CUDA(cudaGetDevice(&dev));
         TFS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-        P = num_sms * 32;
+        P = default_bins(num_sms, nnz);
         stat.alloc(1, st);
         TFS_CUDA(cudaMemsetAsync(stat.p, 0, sizeof(DeviceStatus), st));
         ticket.alloc(1, st);
@@ -410,6 +412,7 @@ struct Impl : CtxBase {
 
     void plan(int n) {
         ModeLayout &L = mode[n];
+        ++layout_gen;
         std::vector<int64_t> off((size_t)L.I + 1);
         TFS_CUDA(cudaMemcpyAsync(off.data(), L.off.p, off.size() * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st));
@@ -596,140 +599,253 @@ struct Impl : CtxBase {
             throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
         last_path = 0;
         const int nsplit = (K + C - 1) / C;
-        int cq = Cq;
-        const int32_t *Qp = d_Q.p;
-        for (int s = 0; s < nsplit; ++s) {
-            const int Cs = (s == nsplit - 1) ? K - s * C : C;
-            const int32_t *Sp = d_order.p + (size_t)s * C;
-            PackArgs<T> pk{};
-            pk.N = N;
-            pk.row_base[0] = 0;
-            for (int l = 0; l < N; ++l) {
-                pk.Z[l] = Z[l].p;
-                pk.A[l] = A[l].p;
-                pk.id_of[l] = mode[l].id_of.p;
-                pk.row_base[l + 1] = pk.row_base[l] + dims[l];
-            }
-            pk.K = K;
-            pk.W = W;
-            pk.C = Cs;
-            pk.Cq = cq;
-            pk.off_old = off_old;
-            pk.off_prev = off_prev;
-            pk.S = Sp;
-            pk.Q = Qp;
-            timed(TF_KIND_PACK, [&] { launch_pack<T>(pk, st); });
-            ++launches;
-            for (int t = 0; t < T_in; ++t) {
-                for (int n = 0; n < N; ++n) {
-                    const ModeLayout &L = mode[n];
-                    cur_mode = n;
-                    PassArgs<T> a{};
-                    a.items = L.items.p;
-                    a.bin_ptr = L.bin_ptr.p;
-                    a.P = L.P;
-                    a.N = N;
-                    a.n = n;
-                    a.C = Cs;
-                    a.Cq = cq;
-                    a.first = (t == 0);
-                    a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
-                    a.lambda = (T)lambda;
-                    for (int u = 0; u < N - 1; ++u) {
-                        a.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
-                        a.Zo[u] = Z[L.omode[u]].p;
+        // every launch of the splits (pack, mode passes, solves) and the copy of the last
+        // split's columns into Q; returns |Q|
+        auto run_splits = [&]() {
+            int cq = Cq;
+            const int32_t *Qp = d_Q.p;
+            for (int s = 0; s < nsplit; ++s) {
+                const int Cs = (s == nsplit - 1) ? K - s * C : C;
+                const int32_t *Sp = d_order.p + (size_t)s * C;
+                PackArgs<T> pk{};
+                pk.N = N;
+                pk.row_base[0] = 0;
+                for (int l = 0; l < N; ++l) {
+                    pk.Z[l] = Z[l].p;
+                    pk.A[l] = A[l].p;
+                    pk.id_of[l] = mode[l].id_of.p;
+                    pk.row_base[l + 1] = pk.row_base[l] + dims[l];
+                }
+                pk.K = K;
+                pk.W = W;
+                pk.C = Cs;
+                pk.Cq = cq;
+                pk.off_old = off_old;
+                pk.off_prev = off_prev;
+                pk.S = Sp;
+                pk.Q = Qp;
+                timed(TF_KIND_PACK, [&] { launch_pack<T>(pk, st); });
+                ++launches;
+                for (int t = 0; t < T_in; ++t) {
+                    for (int n = 0; n < N; ++n) {
+                        const ModeLayout &L = mode[n];
+                        cur_mode = n;
+                        PassArgs<T> a{};
+                        a.items = L.items.p;
+                        a.bin_ptr = L.bin_ptr.p;
+                        a.P = L.P;
+                        a.N = N;
+                        a.n = n;
+                        a.C = Cs;
+                        a.Cq = cq;
+                        a.first = (t == 0);
+                        a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
+                        a.lambda = (T)lambda;
+                        for (int u = 0; u < N - 1; ++u) {
+                            a.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
+                            a.Zo[u] = Z[L.omode[u]].p;
+                        }
+                        a.Zn = Z[n].p;
+                        a.rank_n = L.rank_of.p;
+                        a.res = res[n].p;
+                        a.A_n = A[n].p;
+                        a.K = K;
+                        a.S = Sp;
+                        a.partials = partials.p;
+                        a.stat = stat.p;
+                        a.ticket = ticket.p;
+                        a.ticket_base = ticket_base;
+                        if (wide) {
+                            // float: the tensor-core Gram where it measures faster (the
+                            // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
+                            const bool tc = sizeof(T) == 4 && path != 1 &&
+                                            (path == 2 || precision == 1 ||
+                                             wide_split_width(Cs, CM) == 128);
+                            const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
+                            // every block takes one ticket past the last bin
+                            ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
+                            timed(TF_KIND_MODE_PASS,
+                                  [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, precision == 0, st); });
+                            last_path |= tc ? 4 : 1;
+                            ++launches;
+                            if (L.n_single > 0) {
+                                timed(TF_KIND_SOLVE, [&] {
+                                    launch_solve_wide<T>(a, L.single.p, L.n_single, CM, W, st);
+                                });
+                                ++launches;
+                            }
+                            if (L.n_split > 0) {
+                                timed(TF_KIND_COMBINE, [&] {
+                                    launch_solve_wide<T>(a, L.split.p, L.n_split, CM, W, st);
+                                });
+                                ++launches;
+                            }
+                            continue;
+                        }
+                        if constexpr (sizeof(T) == 4) {
+                            if (use_tma) {
+                                const bool before[2] = {L.omode[0] < n, L.omode[1] < n};
+                                const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                                const TmaPlan plan =
+                                    tma_pass_plan(CM, t == 0, before, dims_o, num_sms, L.P);
+
+                                const int bidx[2] = {
+                                    plan.box[0] == 8 ? 0 : (plan.box[0] == 24 ? 1 : 2),
+                                    plan.box[1] == 8 ? 0 : (plan.box[1] == 24 ? 1 : 2)};
+                                CUtensorMap tm2[2] = {tmaps[L.omode[0]][bidx[0]],
+                                                      tmaps[L.omode[1]][bidx[1]]};
+                                ticket_base += (unsigned long long)L.P +
+                                               (unsigned long long)plan.grid * plan.warps;
+                                timed(TF_KIND_MODE_PASS, [&] {
+                                    launch_mode_pass_tma(a, tm2, plan, CM, t == 0, before, st);
+                                });
+                                last_path |= 2;
+                                ++launches;
+                                goto solved;
+                            }
+                        }
+                    {
+                        const PassPlan plan = mode_pass_plan<T>(CM, N, n, t == 0, num_sms, L.P);
+                        // every launched warp takes one ticket past the last bin
+                        ticket_base += (unsigned long long)L.P +
+                                       (unsigned long long)plan.grid * plan.warps;
+                        timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, plan, st); });
+                        last_path |= 1;
                     }
-                    a.Zn = Z[n].p;
-                    a.rank_n = L.rank_of.p;
-                    a.res = res[n].p;
-                    a.A_n = A[n].p;
-                    a.K = K;
-                    a.S = Sp;
-                    a.partials = partials.p;
-                    a.stat = stat.p;
-                    a.ticket = ticket.p;
-                    a.ticket_base = ticket_base;
-                    if (wide) {
-                        // float: the tensor-core Gram where it measures faster (the
-                        // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
-                        const bool tc = sizeof(T) == 4 && path != 1 &&
-                                        (path == 2 || precision == 1 ||
-                                         wide_split_width(Cs, CM) == 128);
-                        const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
-                        // every block takes one ticket past the last bin
-                        ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
-                        timed(TF_KIND_MODE_PASS,
-                              [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, precision == 0, st); });
-                        last_path |= tc ? 4 : 1;
                         ++launches;
+                    solved:
                         if (L.n_single > 0) {
-                            timed(TF_KIND_SOLVE, [&] {
-                                launch_solve_wide<T>(a, L.single.p, L.n_single, CM, W, st);
-                            });
+                            timed(TF_KIND_SOLVE,
+                                  [&] { launch_solve_rows<T>(a, CM, L.single.p, L.n_single, st); });
                             ++launches;
                         }
                         if (L.n_split > 0) {
-                            timed(TF_KIND_COMBINE, [&] {
-                                launch_solve_wide<T>(a, L.split.p, L.n_split, CM, W, st);
-                            });
+                            timed(TF_KIND_COMBINE,
+                                  [&] { launch_combine<T>(a, CM, L.split.p, L.n_split, st); });
                             ++launches;
                         }
-                        continue;
-                    }
-                    if constexpr (sizeof(T) == 4) {
-                        if (use_tma) {
-                            const bool before[2] = {L.omode[0] < n, L.omode[1] < n};
-                            const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
-                            const TmaPlan plan =
-                                tma_pass_plan(CM, t == 0, before, dims_o, num_sms, L.P);
-
-                            const int bidx[2] = {
-                                plan.box[0] == 8 ? 0 : (plan.box[0] == 24 ? 1 : 2),
-                                plan.box[1] == 8 ? 0 : (plan.box[1] == 24 ? 1 : 2)};
-                            CUtensorMap tm2[2] = {tmaps[L.omode[0]][bidx[0]],
-                                                  tmaps[L.omode[1]][bidx[1]]};
-                            ticket_base += (unsigned long long)L.P +
-                                           (unsigned long long)plan.grid * plan.warps;
-                            timed(TF_KIND_MODE_PASS, [&] {
-                                launch_mode_pass_tma(a, tm2, plan, CM, t == 0, before, st);
-                            });
-                            last_path |= 2;
-                            ++launches;
-                            goto solved;
-                        }
-                    }
-                {
-                    const PassPlan plan = mode_pass_plan<T>(CM, N, n, t == 0, num_sms, L.P);
-                    // every launched warp takes one ticket past the last bin
-                    ticket_base += (unsigned long long)L.P +
-                                   (unsigned long long)plan.grid * plan.warps;
-                    timed(TF_KIND_MODE_PASS, [&] { launch_mode_pass<T>(a, CM, plan, st); });
-                    last_path |= 1;
-                }
-                    ++launches;
-                solved:
-                    if (L.n_single > 0) {
-                        timed(TF_KIND_SOLVE,
-                              [&] { launch_solve_rows<T>(a, CM, L.single.p, L.n_single, st); });
-                        ++launches;
-                    }
-                    if (L.n_split > 0) {
-                        timed(TF_KIND_COMBINE,
-                              [&] { launch_combine<T>(a, CM, L.split.p, L.n_split, st); });
-                        ++launches;
                     }
                 }
+                cq = Cs;
+                Qp = Sp;
+                cur_mode = -1;
             }
-            cq = Cs;
-            Qp = Sp;
-            cur_mode = -1;
+            // the copies now hold R-hat of the last split's columns
+            TFS_CUDA(cudaMemcpyAsync(d_Q.p, Qp, sizeof(int32_t) * cq, cudaMemcpyDeviceToDevice,
+                                     st));
+            return cq;
+        };
+        int cq_end;
+        if (!graphs_on || prof_on || st == nullptr) {
+            cq_end = run_splits();
+        } else {
+            GraphKey gk{};
+            gk.C = C, gk.T_in = T_in, gk.CM = CM, gk.Cq = Cq, gk.path = path;
+            gk.precision = precision, gk.use_tma = use_tma, gk.flags = flags;
+            gk.lambda = lambda, gk.layout_gen = layout_gen, gk.partials = partials.p;
+            for (int l = 0; l < N; ++l) gk.Z[l] = Z[l].p;
+            cq_end = run_splits_graph(gk, run_splits);
         }
-        // the copies now hold R-hat of the last split's columns
-        TFS_CUDA(cudaMemcpyAsync(d_Q.p, Qp, sizeof(int32_t) * cq, cudaMemcpyDeviceToDevice, st));
-        Cq = cq;
+        Cq = cq_end;
         CM_last = CM;
         ++sweeps;
         last_launches = launches - launches0;
+    }
+
+    // ------------------------------------------------------------ sweeps as CUDA graphs
+    // The launches of a sweep depend only on the key below; the column order reaches the
+    // kernels through d_order, copied before the graph runs.  A key's first sweep runs
+    // eagerly (kernel attributes and plans settle), its second is captured into a graph
+    // and launched, later ones replay the graph: one launch per sweep instead of one per
+    // kernel.  The graph resets the bin counter itself (the mode passes' ticket bases
+    // are baked in as seen from zero).
+    struct GraphKey {
+        int C, T_in, CM, Cq, path, precision;
+        bool use_tma;
+        uint32_t flags;
+        double lambda;
+        int64_t layout_gen;
+        const void *partials;
+        const void *Z[kMaxModes];
+        bool operator==(const GraphKey &o) const {
+            if (C != o.C || T_in != o.T_in || CM != o.CM || Cq != o.Cq || path != o.path ||
+                precision != o.precision || use_tma != o.use_tma || flags != o.flags ||
+                lambda != o.lambda || layout_gen != o.layout_gen || partials != o.partials)
+                return false;
+            for (int l = 0; l < kMaxModes; ++l)
+                if (Z[l] != o.Z[l]) return false;
+            return true;
+        }
+    };
+    struct SweepGraph {
+        GraphKey key;
+        cudaGraphExec_t exec;
+        int64_t launches;               // kernels in the graph
+        unsigned long long ticket_end;  // bin counter after the graph
+        int64_t path_bits;
+        int cq_end;
+    };
+    static constexpr size_t kMaxGraphs = 8;
+    bool graphs_on = false;
+    std::vector<SweepGraph> graphs;  // least recently used first
+    GraphKey last_eager{};
+    bool have_last_eager = false;
+    int64_t graph_replays = 0;
+
+    template <class F>
+    int run_splits_graph(const GraphKey &gk, F &run_splits) {
+        for (size_t i = 0; i < graphs.size(); ++i) {
+            if (!(graphs[i].key == gk)) continue;
+            SweepGraph g = graphs[i];
+            graphs.erase(graphs.begin() + (long)i);
+            graphs.push_back(g);
+            TFS_CUDA(cudaGraphLaunch(g.exec, st));
+            launches += g.launches;
+            ticket_base = g.ticket_end;
+            last_path = g.path_bits;
+            ++graph_replays;
+            return g.cq_end;
+        }
+        if (!(have_last_eager && last_eager == gk)) {
+            last_eager = gk;
+            have_last_eager = true;
+            return run_splits();
+        }
+        const int64_t l0 = launches;
+        cudaGraph_t graph = nullptr;
+        int cq_end = 0;
+        TFS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            TFS_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned long long), st));
+            ticket_base = 0;
+            cq_end = run_splits();
+        } catch (...) {
+            cudaStreamEndCapture(st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw;
+        }
+        TFS_CUDA(cudaStreamEndCapture(st, &graph));
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TFS_CUDA(e);
+        if (graphs.size() >= kMaxGraphs) {
+            TFS_CUDA(cudaStreamSynchronize(st));
+            cudaGraphExecDestroy(graphs.front().exec);
+            graphs.erase(graphs.begin());
+        }
+        graphs.push_back({gk, exec, launches - l0, ticket_base, last_path, cq_end});
+        TFS_CUDA(cudaGraphLaunch(exec, st));
+        ++graph_replays;
+        return cq_end;
+    }
+
+    void drop_graphs() {
+        if (!graphs.empty()) cudaStreamSynchronize(st);
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+        have_last_eager = false;
     }
 
     // Tensor maps of every mode's packed slice (float, W = 32): boxes of 8, 24, 40 floats,
@@ -1151,12 +1267,99 @@ struct Impl : CtxBase {
         c[7] = last_path;
     }
 
+    // ------------------------------------------------------------ autotuning
+    // Times one sweep per (P, C) candidate pair from the current state and restores that
+    // state bit for bit after each trial (factors, residual copies, the columns Q, the
+    // sweep counter that seeds the default orders); leaves the fastest pair's schedule.
+    // Each trial is preceded by an untimed sweep from the same state (first-launch costs).
+    void autotune(const int *C_list, int n_C, const int *P_list, int n_P, double lambda,
+                  int T_in, uint32_t flags, int *best_C, int *best_P, float *ms_out) {
+        if (n_C < 1 || n_P < 1 || !C_list || !P_list || !best_C || !best_P)
+            throw ApiError{TF_EINVAL, "empty candidate list"};
+        for (int i = 0; i < n_C; ++i)
+            if (C_list[i] < 1 || C_list[i] > K || pick_cm(C_list[i]) == 0)
+                throw ApiError{TF_EINVAL, "C candidate out of range"};
+        for (int i = 0; i < n_P; ++i)
+            if (P_list[i] < 0) throw ApiError{TF_EINVAL, "P candidate must be >= 0"};
+        if (prof_on) throw ApiError{TF_EBUSY, "autotuning while profiling"};
+        TFS_CUDA(cudaStreamSynchronize(st));
+        // saved state
+        std::vector<std::unique_ptr<Buf<T>>> sA, sR;
+        for (int n = 0; n < N; ++n) {
+            sA.emplace_back(new Buf<T>());
+            sR.emplace_back(new Buf<T>());
+            sA[n]->alloc(A[n].n, st);
+            sR[n]->alloc(res[n].n, st);
+            TFS_CUDA(cudaMemcpyAsync(sA[n]->p, A[n].p, A[n].n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            TFS_CUDA(cudaMemcpyAsync(sR[n]->p, res[n].p, res[n].n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        }
+        Buf<int32_t> sQ;
+        sQ.alloc(K, st);
+        TFS_CUDA(cudaMemcpyAsync(sQ.p, d_Q.p, K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        const int Cq0 = Cq, CMl0 = CM_last;
+        const bool dirty0 = dirty, a00 = a0_zero;
+        const int64_t sweeps0 = sweeps, launches0 = launches, last0 = last_launches;
+        const int64_t path0 = last_path;
+        const int P0 = P;
+        auto restore = [&] {
+            for (int n = 0; n < N; ++n) {
+                TFS_CUDA(cudaMemcpyAsync(A[n].p, sA[n]->p, A[n].n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                TFS_CUDA(cudaMemcpyAsync(res[n].p, sR[n]->p, res[n].n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            }
+            TFS_CUDA(cudaMemcpyAsync(d_Q.p, sQ.p, K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            Cq = Cq0, CM_last = CMl0, dirty = dirty0, a0_zero = a00, sweeps = sweeps0;
+        };
+        const bool graphs0 = graphs_on;
+        graphs_on = false;  // a capture's host time would show up as device idle time
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        TFS_CUDA(cudaEventCreate(&e0));
+        TFS_CUDA(cudaEventCreate(&e1));
+        float best = -1.f;
+        try {
+            for (int ip = 0; ip < n_P; ++ip) {
+                set_schedule(policy, P_list[ip]);
+                for (int ic = 0; ic < n_C; ++ic) {
+                    restore();
+                    sweep(C_list[ic], lambda, T_in, nullptr, flags);
+                    restore();
+                    TFS_CUDA(cudaEventRecord(e0, st));
+                    sweep(C_list[ic], lambda, T_in, nullptr, flags);
+                    TFS_CUDA(cudaEventRecord(e1, st));
+                    TFS_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    TFS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms_out) ms_out[(size_t)ip * n_C + ic] = ms;
+                    if (best < 0.f || ms < best) {
+                        best = ms;
+                        *best_C = C_list[ic];
+                        *best_P = P_list[ip];
+                    }
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            restore();
+            graphs_on = graphs0;
+            set_schedule(policy, P0 == default_bins(num_sms, nnz) ? 0 : P0);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        graphs_on = graphs0;
+        restore();
+        set_schedule(policy, *best_P);
+        launches = launches0, last_launches = last0, last_path = path0;
+        TFS_CUDA(cudaStreamSynchronize(st));
+        check_errors();
+    }
+
     void set_schedule(tf_sched_policy pol, int P_) {
         if (pol < TF_SCHED_LPT || pol > TF_SCHED_RAN) throw ApiError{TF_EINVAL, "bad policy"};
         if (P_ < 0) throw ApiError{TF_EINVAL, "P must be >= 0"};
         TFS_CUDA(cudaStreamSynchronize(st));
         policy = pol;
-        P = P_ > 0 ? P_ : num_sms * 32;
+        P = P_ > 0 ? P_ : default_bins(num_sms, nnz);
         for (int n = 0; n < N; ++n) plan(n);
     }
 };
@@ -1435,7 +1638,7 @@ tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int 
     }
     // the same sizes tf_create and the sweeps allocate (see Impl::create / Impl::sweep)
     const double T = dtype == TF_F32 ? 4.0 : 8.0;
-    const double P = (double)num_sms * 32.0;
+    const double P = (double)tfs::default_bins(num_sms, nnz);
     const double e = (double)nnz, ostride = (double)((nnz + 64 + 63) / 64 * 64);
     const int W = tfs::slice_stride_elems(CM, (int)T);
     double layout = 0, plan = 0, factors = 0, maxI = 0;
@@ -1514,6 +1717,34 @@ tf_status tf_set_precision(tf_ctx *ctx, int mode) {
         if (mode == 1 && sizeof(*c.x.p) != 4)
             throw tfs::ApiError{TF_EINVAL, "the reduced-precision Gram needs a float context"};
         c.precision = mode;
+    });
+}
+
+tf_status tf_set_graphs(tf_ctx *ctx, int enable) {
+    if (enable < 0 || enable > 1) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        if (!enable) c.drop_graphs();
+        c.graphs_on = enable != 0;
+    });
+}
+
+tf_status tf_autotune(tf_ctx *ctx, const int32_t *C_list, int n_C, const int32_t *P_list,
+                      int n_P, double lambda, int T_in, uint32_t flags, int32_t *best_C,
+                      int32_t *best_P, float *ms) {
+    if (!C_list || !P_list || !best_C || !best_P || n_C < 1 || n_P < 1) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        int bc = 0, bp = 0;
+        std::vector<int> cl(C_list, C_list + std::max(n_C, 0)), pl(P_list, P_list + std::max(n_P, 0));
+        c.autotune(cl.data(), n_C, pl.data(), n_P, lambda, T_in, flags, &bc, &bp, ms);
+        *best_C = bc;
+        *best_P = bp;
+    });
+}
+
+tf_status tf_graph_info(tf_ctx *ctx, int64_t *replays, int64_t *cached) {
+    return dispatch(ctx, [&](auto &c) {
+        if (replays) *replays = c.graph_replays;
+        if (cached) *cached = (int64_t)c.graphs.size();
     });
 }
 

@@ -770,3 +770,118 @@ def test_set_stream_moves_later_work():
     f.sweep(6, 0.3, 1, p.column_order(4, 6))
     ref.sweep(6, 0.3, 1, p.column_order(4, 6))
     assert np.array_equal(f.factors(0), ref.factors(0))
+
+
+# --------------------------------------------------------------------------- graphs
+
+
+@pytest.mark.parametrize("dims,nnz,K,C,T_in,dt,weighted", [
+    ((300, 200, 50), 30_000, 8, 4, 1, tf.F64, False),     # narrow, FP64
+    ((300, 200, 50), 30_000, 10, 1, 1, tf.F64, False),    # CDTF
+    ((300, 200, 50), 30_000, 24, 20, 2, tf.F32, True),    # wide SIMT, T_in 2, weighted
+    ((150, 120, 40), 8_000, 80, 70, 1, tf.F32, False),    # wide, tensor-core Gram
+    ((120, 90, 60, 30), 25_000, 12, 5, 1, tf.F32, False), # 4-way, ragged last split
+])
+def test_graph_sweeps_match_eager(dims, nnz, K, C, T_in, dt, weighted):
+    """Sweeps replayed from a CUDA graph give bit for bit the factors and loss of eager
+    sweeps, with a new column order every sweep (the order reaches the graph through
+    device memory)."""
+    import torch
+    p = synth.small(190 + K, dims, nnz, 4, K)
+    c, x = p.numpy()
+    s = torch.cuda.Stream()
+    out = []
+    for graphs in (False, True):
+        f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=dt, stream=s.cuda_stream)
+        f.set_graphs(graphs)
+        for t in range(6):
+            f.sweep(C, 0.3, T_in, p.column_order(t, C), weighted=weighted)
+        out.append(([f.factors(n) for n in range(p.N)], f.loss(0.3, weighted),
+                    f.graph_info()))
+        f.close()
+    (fe, le, ge), (fg, lg, gg) = out
+    assert ge["replays"] == 0
+    assert gg["replays"] == 4 and gg["cached"] == 1   # sweeps 1-2 eager (Q changes), 3-6 graph
+    for n in range(p.N):
+        assert np.array_equal(fe[n], fg[n]), n
+    assert le == lg
+
+
+def test_graph_sweeps_across_state_changes():
+    """Graph sweeps interleaved with what changes a sweep's launches or its inputs: new
+    factors (residuals rebuilt), another schedule (new row plan), another C, a loss and a
+    fold-in between sweeps -- the same results as the same calls without graphs."""
+    import torch
+    p = synth.small(197, (400, 300, 60), 40_000, 4, 12)
+    c, x = p.numpy()
+    A1 = p.init_factors()[1].numpy() * 0.5
+    s = torch.cuda.Stream()
+    res = []
+    for graphs in (False, True):
+        f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F64, stream=s.cuda_stream)
+        f.set_graphs(graphs)
+        log = []
+        for t in range(4):
+            f.sweep(4, 0.2, 1, p.column_order(t, 4))
+        log.append(f.loss(0.2))
+        f.set_factors(1, A1)
+        for t in range(3):
+            f.sweep(4, 0.2, 1, p.column_order(10 + t, 4))
+        f.set_schedule(tf.SCHED_GREEDY, 0)
+        for t in range(3):
+            f.sweep(4, 0.2, 1, p.column_order(20 + t, 4))
+        for t in range(4):
+            Ct = 3 if t % 2 else 6
+            f.sweep(Ct, 0.2, 1, p.column_order(30 + t, Ct))
+        log.append(f.foldin(0, np.stack([np.arange(30) % 300, np.arange(30) % 60], 1),
+                            np.linspace(-1, 1, 30), 0.2))
+        for t in range(3):
+            f.sweep(4, 0.2, 1, p.column_order(40 + t, 4))
+        log.append([f.factors(n) for n in range(3)])
+        log.append(f.loss(0.2))
+        res.append(log)
+        f.close()
+    e, g = res
+    assert e[0] == g[0] and e[3] == g[3]
+    assert np.array_equal(e[1], g[1])
+    for n in range(3):
+        assert np.array_equal(e[2][n], g[2][n])
+
+
+# --------------------------------------------------------------------------- autotuning
+
+
+@pytest.mark.parametrize("dt", [tf.F32, tf.F64])
+def test_autotune_restores_state_and_keeps_best_schedule(dt):
+    """tf_autotune times every (P, C) pair, leaves the fastest pair's schedule, and
+    restores the state: later sweeps equal, bit for bit, those of a twin context that was
+    never autotuned but runs on the chosen schedule."""
+    p = synth.small(205, (600, 500, 80), 80_000, 4, 16)
+    c, x = p.numpy()
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=dt)
+    g = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=dt)
+    for h in (f, g):
+        for t in range(2):
+            h.sweep(4, 0.2, 1)   # default orders: they depend on the sweep counter
+    Cs, Ps = [2, 4, 8, 12], [0, 304, 2432]
+    bc, bp, ms = f.autotune(Cs, Ps, lam=0.2)
+    assert ms.shape == (3, 4) and (ms > 0).all()
+    assert ms[Ps.index(bp), Cs.index(bc)] == ms.min()
+    g.set_schedule(tf.SCHED_LPT, bp)
+    for h in (f, g):
+        for t in range(3):
+            h.sweep(4, 0.2, 1)
+    for n in range(3):
+        assert np.array_equal(f.factors(n), g.factors(n)), n
+    assert f.loss(0.2) == g.loss(0.2)
+
+
+def test_autotune_rejects_bad_candidates():
+    p = synth.small(206, (100, 80, 20), 5_000, 2, 8)
+    c, x = p.numpy()
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
+    for Cs, Ps in (([0, 2], [0]), ([9], [0]), ([2], [-1]), ([], [0]), ([2], [])):
+        with pytest.raises(tf.TFError) as e:
+            f.autotune(Cs, Ps)
+        assert e.value.status == tf.EINVAL
+    f.sweep(2, 0.1, 1)
