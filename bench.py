@@ -293,6 +293,57 @@ def batched(args, rank, world):
     return 0
 
 
+def fiveway(args, rank, world):
+    """The 5-way workload: mode lengths 1e6, --fiveway uniform-random distinct entries
+    (5e8 at full size), rank-20 truth + N(0, 0.1^2), FP32, K = 1000, lambda = 1; one sweep
+    per C of --fiveway-c, in sequence (no warm-up sweep: a sweep takes seconds),
+    device time by CUDA events, with the layout build time and the memory held."""
+    import numpy as np
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    from paper_1410_5209_gb300 import build as tfbuild
+    if rank != 0:
+        return 0
+    tfbuild.build()
+    tf.load()
+    K, lam, dims = 1000, 1.0, (1_000_000,) * 5
+    t0 = time.perf_counter()
+    p = synth.make_problem(dims, args.fiveway, 20, K, args.seed, dtype=torch.float32,
+                           device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    s = torch.cuda.Stream()
+    used0, _ = tf.pool_usage(reset_high=True)
+    t0 = time.perf_counter()
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+                         stream=s.cuda_stream, device_input=True)
+    f.sync()
+    create_s = time.perf_counter() - t0
+    rows = {}
+    Cs = [int(c) for c in args.fiveway_c.split(",") if c]
+    for C in Cs:   # one sweep per C, in sequence from the state the previous one left
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        f.sweep(C, lam, 1)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        loss, rmse = f.loss(lam)
+        rows[str(C)] = {"ms_per_sweep": ms, "nnz_rank_per_s": p.nnz * K / (ms / 1e3),
+                        "train_rmse_after": rmse,
+                        "pass_path": f.counters()["pass_path"]}
+    _, high = tf.pool_usage()
+    est = max(tf.estimate_bytes(p.dims, p.nnz, K, C, tf.F32, device_input=True) for C in Cs)
+    print(json.dumps({"metric": "nnz*rank updates/s per SALS sweep (5-way)", "unit": UNIT,
+                      "nnz": p.nnz, "dims": list(dims), "K": K, "lam": lam, "dtype": "f32",
+                      "per_C": rows, "generate_s": gen_s, "create_s": create_s,
+                      "device_bytes_high": high - used0, "device_bytes_estimate": est,
+                      "data": "synthetic"}), flush=True)
+    f.close()
+    return 0
+
+
 def small_sweeps(args):
     """The 1e5-entry FP64 parity workload (1000 x 1000 x 100, K = 10), C = 1 (CDTF) and
     C = 5: device time per sweep with eager launches and with the sweep replayed as a
@@ -441,6 +492,9 @@ def main():
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
     ap.add_argument("--study-sweeps", type=int, default=3)
     ap.add_argument("--study-policies", default="lpt,greedy,seq,ran")
+    ap.add_argument("--fiveway", type=int, default=0,
+                    help="entries of the 5-way workload to time instead (5e8 at full size)")
+    ap.add_argument("--fiveway-c", default="10,50,1")
     ap.add_argument("--batched", type=int, default=0,
                     help="factorise this many small independent tensors as one batch instead")
     args = ap.parse_args()
@@ -449,6 +503,8 @@ def main():
         return study(args, rank, world)
     if args.batched > 0:
         return batched(args, rank, world)
+    if args.fiveway > 0:
+        return fiveway(args, rank, world)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 
