@@ -474,6 +474,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
+    ap.add_argument("--C", type=int, default=0,
+                    help="subset size of the timed sweeps (0: the workload's C = 10)")
     ap.add_argument("--foldin-requests", type=int, default=200)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
@@ -524,6 +526,8 @@ def main():
         dist.barrier()
     tf.load()
 
+    if args.C:
+        WORKLOAD["C"] = args.C
     K, C, lam, T_in = WORKLOAD["K"], WORKLOAD["C"], WORKLOAD["lam"], WORKLOAD["T_in"]
     # each rank factorises its own replica (independent problems: no data-path collective)
     p = synth.skewed_3way(seed=args.seed + rank, nnz=args.nnz, device="cuda")
@@ -576,11 +580,11 @@ def main():
     bytes_per_launch = nnz * (4 * (N - 1) + 4 + 4.0 / (N * T_in))
     achieved = bytes_per_launch / (mp_avg_ms / 1e3) / 1e9
     traffic = NCU_TRAFFIC if (NCU_SOURCE_HASH == kernel_source_hash()
-                              and nnz == NCU_TRAFFIC_NNZ) else None
+                              and nnz == NCU_TRAFFIC_NNZ and C == 10) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
-                "kernel": " + ".join(n for b, n in ((1, "k_mode_pass"), (2, "k_mode_pass_tma"),
-                                                   (4, "k_pass_wide_tc"))
+                "kernel": " + ".join(n for b, n in ((1, "k_pass_wide" if C > 16 else "k_mode_pass"),
+                                                   (2, "k_mode_pass_tma"), (4, "k_pass_wide_tc"))
                                      if cnt["pass_path"] & b) or "?",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,

@@ -107,6 +107,19 @@ const char *tf_last_error(const tf_ctx *ctx);
 /* Waits for the context's stream and reports any device-side error. */
 tf_status tf_sync(tf_ctx *ctx);
 
+/* Row solves of float contexts (Eq. 4; the paper solves in the precision of its data).
+ * refine = 1: every C x C solve takes one step of iterative refinement, x += (L L^T)^-1
+ * (c - (B + lambda I) x) with the residual formed in FP64 from the sums as accumulated,
+ * which removes the FP32 Cholesky's error on ill-conditioned rows.  cond_limit > 0: a row
+ * whose smallest Cholesky pivot ratio d_j / (B_jj + lambda) is below 1 / cond_limit (or
+ * that meets a non-positive pivot) is solved again, entirely in FP64, from the same sums;
+ * such rows are counted (tf_solve_info).  Defaults 0, 0.  No effect on double contexts.
+ * The Gram sums themselves keep the precision of the pass (tf_set_precision). */
+tf_status tf_set_solve(tf_ctx *ctx, int refine, double cond_limit);
+
+/* Float rows re-solved in FP64 so far (synchronises). */
+tf_status tf_solve_info(tf_ctx *ctx, int64_t *fp64_rows);
+
 /* enable = 1: sweeps run as CUDA graphs.  The launches of a sweep (pack, mode passes,
  * solves, for every split) depend only on C, T_in, lambda, flags, the columns left from
  * the previous sweep and the context's settings; the second sweep with a given such key is

@@ -90,6 +90,8 @@ def load():
         "tf_version": [],
         "tf_get_shape": [P, P, P, P],
         "tf_set_graphs": [P, i32],
+        "tf_set_solve": [P, i32, f64],
+        "tf_solve_info": [P, P],
         "tf_autotune": [P, P, i32, P, i32, f64, i32, u32, P, P, P],
         "tf_graph_info": [P, P, P],
         "tf_get_stream": [P, P],
@@ -311,6 +313,16 @@ class Factorization:
 
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
+
+    def set_solve(self, refine=False, cond_limit=0.0):
+        """Float row solves: one FP64-residual refinement step; FP64 re-solve of rows whose
+        pivot ratio is below 1 / cond_limit (0: never)."""
+        self._check(self._lib.tf_set_solve(self._ctx, 1 if refine else 0, float(cond_limit)))
+
+    def fp64_rows(self):
+        n = ctypes.c_int64()
+        self._check(self._lib.tf_solve_info(self._ctx, ctypes.byref(n)))
+        return n.value
 
     def set_graphs(self, enable=True):
         """Run sweeps as CUDA graphs (captured on a shape's second sweep, then replayed)."""

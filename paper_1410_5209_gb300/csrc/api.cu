@@ -116,12 +116,14 @@ struct ModeLayout {
     int64_t ostride = 0;    // elements between two other-mode index arrays
     Buf<int32_t> rank_of;   // row id -> degree rank (slice row)
     Buf<int32_t> id_of;     // degree rank -> row id
+    Buf<int32_t> groups;    // slot groups of split rows (first slot, count), wide subsets
+    int n_groups = 0;
     int P = 0;
     int omode[kMaxModes - 1];
     template <class F>
     void each_buf(F f) {
         f(off), f(perm), f(oidx), f(items), f(bin_ptr), f(split), f(single), f(rank_of),
-            f(id_of);
+            f(id_of), f(groups);
     }
 };
 
@@ -174,6 +176,8 @@ struct Impl : CtxBase {
 
     int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported
     int precision = 0;             // 0 FP32-level Gram, 1 single-TF32 tensor-core Gram (wide C)
+    int solve_refine = 0;          // float: one refinement step of every row solve
+    float solve_cond = 0.f;        // float: FP64 solve of rows with pivot ratio < 1 / this
     CUtensorMap tmaps[kMaxModes][3];  // per mode: slice maps with boxes 8, 24, 40 floats
     const void *tmaps_for_Z[kMaxModes] = {nullptr};
     int Cq = 0, CM_last = 1;       // columns Q held by the copies' R-hat; register width
@@ -446,6 +450,18 @@ struct Impl : CtxBase {
         L.bin_ptr.alloc(bin_ptr.size(), st);
         L.split.alloc(split.size(), st);
         L.single.alloc(single.size(), st);
+        std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
+        for (const SplitRow &sr : split)
+            if (sr.n_slots > kSlotGroup)
+                for (int g = 0; g < sr.n_slots; g += kSlotGroup) {
+                    groups.push_back(sr.first_slot + g);
+                    groups.push_back(std::min(kSlotGroup, sr.n_slots - g));
+                }
+        L.n_groups = (int)(groups.size() / 2);
+        L.groups.alloc(std::max<size_t>(groups.size(), 2), st);
+        if (!groups.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.groups.p, groups.data(), groups.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
         if (!single.empty())
             TFS_CUDA(cudaMemcpyAsync(L.single.p, single.data(), single.size() * sizeof(SplitRow),
                                      cudaMemcpyHostToDevice, st));
@@ -641,6 +657,8 @@ struct Impl : CtxBase {
                         a.first = (t == 0);
                         a.weighted = (flags & TF_WEIGHTED_LAMBDA) ? 1 : 0;
                         a.lambda = (T)lambda;
+                        a.refine = solve_refine;
+                        a.cond_limit = solve_cond;
                         for (int u = 0; u < N - 1; ++u) {
                             a.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
                             a.Zo[u] = Z[L.omode[u]].p;
@@ -675,6 +693,14 @@ struct Impl : CtxBase {
                                 ++launches;
                             }
                             if (L.n_split > 0) {
+                                if (L.n_groups > 0) {
+                                    timed(TF_KIND_COMBINE, [&] {
+                                        launch_sum_slot_groups<T>(partials.p,
+                                                                  partial_stride(CM),
+                                                                  L.groups.p, L.n_groups, st);
+                                    });
+                                    ++launches;
+                                }
                                 timed(TF_KIND_COMBINE, [&] {
                                     launch_solve_wide<T>(a, L.split.p, L.n_split, CM, W, st);
                                 });
@@ -742,6 +768,7 @@ struct Impl : CtxBase {
             GraphKey gk{};
             gk.C = C, gk.T_in = T_in, gk.CM = CM, gk.Cq = Cq, gk.path = path;
             gk.precision = precision, gk.use_tma = use_tma, gk.flags = flags;
+            gk.refine = solve_refine, gk.cond = solve_cond;
             gk.lambda = lambda, gk.layout_gen = layout_gen, gk.partials = partials.p;
             for (int l = 0; l < N; ++l) gk.Z[l] = Z[l].p;
             cq_end = run_splits_graph(gk, run_splits);
@@ -760,7 +787,8 @@ struct Impl : CtxBase {
     // kernel.  The graph resets the bin counter itself (the mode passes' ticket bases
     // are baked in as seen from zero).
     struct GraphKey {
-        int C, T_in, CM, Cq, path, precision;
+        int C, T_in, CM, Cq, path, precision, refine;
+        float cond;
         bool use_tma;
         uint32_t flags;
         double lambda;
@@ -769,7 +797,8 @@ struct Impl : CtxBase {
         const void *Z[kMaxModes];
         bool operator==(const GraphKey &o) const {
             if (C != o.C || T_in != o.T_in || CM != o.CM || Cq != o.Cq || path != o.path ||
-                precision != o.precision || use_tma != o.use_tma || flags != o.flags ||
+                precision != o.precision || refine != o.refine || cond != o.cond ||
+                use_tma != o.use_tma || flags != o.flags ||
                 lambda != o.lambda || layout_gen != o.layout_gen || partials != o.partials)
                 return false;
             for (int l = 0; l < kMaxModes; ++l)
@@ -1746,6 +1775,20 @@ tf_status tf_graph_info(tf_ctx *ctx, int64_t *replays, int64_t *cached) {
         if (replays) *replays = c.graph_replays;
         if (cached) *cached = (int64_t)c.graphs.size();
     });
+}
+
+tf_status tf_set_solve(tf_ctx *ctx, int refine, double cond_limit) {
+    if (refine < 0 || refine > 1 || !(cond_limit >= 0.0) || !isfinite(cond_limit))
+        return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        c.solve_refine = refine;
+        c.solve_cond = (float)cond_limit;
+    });
+}
+
+tf_status tf_solve_info(tf_ctx *ctx, int64_t *fp64_rows) {
+    if (!fp64_rows) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) { *fp64_rows = (int64_t)c.read_status().fp64_rows; });
 }
 
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {

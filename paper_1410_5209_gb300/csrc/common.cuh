@@ -28,6 +28,7 @@ struct DeviceStatus {
     int bits;
     int pad;
     unsigned long long singular_rows;  // rows left unchanged by a pivot <= 0
+    unsigned long long fp64_rows;      // float rows re-solved in FP64 (ill-conditioned)
 };
 
 // ------------------------------------------------------------------ error plumbing

@@ -17,18 +17,22 @@ __device__ __forceinline__ T warp_allsum(T v) {
     return v;
 }
 
+// Factor of B + lam I in place (left-looking: column j from the finished columns 0..j-1,
+// lanes over the rows below the diagonal, each a dot product with the broadcast row j).
+// *min_ratio (if given) receives the smallest pivot ratio d_j / (B_jj + lam).
 template <class T>
-__device__ bool warp_chol_solve(T *P, T *c, int C, T lam, int lane) {
-    // left-looking: column j from the finished columns 0..j-1, lanes over the rows below
-    // the diagonal (each a dot product with the broadcast row j)
+__device__ bool warp_chol_factor(T *P, int C, T lam, int lane, T *min_ratio = nullptr) {
     bool ok = true;
+    T ratio = T(1);
     for (int j = 0; j < C; ++j) {
         const T *rj = P + ptri(j, 0);
         T s = T(0);
         for (int k = lane; k < j; k += 32) s += rj[k] * rj[k];
         s = warp_allsum(s);
-        const T d = P[ptri(j, j)] + lam - s;
+        const T a_jj = P[ptri(j, j)] + lam;
+        const T d = a_jj - s;
         ok = ok && (d > T(0));
+        if (a_jj > T(0)) ratio = d / a_jj < ratio ? d / a_jj : ratio;
         const T ljj = sqrt(d > T(0) ? d : T(1));
         for (int i = j + 1 + lane; i < C; i += 32) {
             const T *ri = P + ptri(i, 0);
@@ -47,7 +51,13 @@ __device__ bool warp_chol_solve(T *P, T *c, int C, T lam, int lane) {
         if (lane == 0) P[ptri(j, j)] = ljj;
         __syncwarp();
     }
-    // L y = c, then L^T x = y
+    if (min_ratio) *min_ratio = ratio;
+    return ok;
+}
+
+// c <- (L L^T)^-1 c with the factor of warp_chol_factor: L y = c, then L^T x = y.
+template <class T>
+__device__ void warp_chol_apply(const T *P, T *c, int C, int lane) {
     for (int i = 0; i < C; ++i) {
         T s = T(0);
         for (int k = lane; k < i; k += 32) s += P[ptri(i, k)] * c[k];
@@ -62,6 +72,12 @@ __device__ bool warp_chol_solve(T *P, T *c, int C, T lam, int lane) {
         if (lane == 0) c[i] = (c[i] - s) / P[ptri(i, i)];
         __syncwarp();
     }
+}
+
+template <class T>
+__device__ bool warp_chol_solve(T *P, T *c, int C, T lam, int lane) {
+    const bool ok = warp_chol_factor<T>(P, C, lam, lane);
+    warp_chol_apply<T>(P, c, C, lane);
     return ok;
 }
 

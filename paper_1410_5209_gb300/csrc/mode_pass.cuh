@@ -86,12 +86,14 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Solves (B + lam I) x = c for the leading C x C block of a CM x CM packed lower
-// triangle; rows/columns >= C are replaced by the identity (their x is 0).
-// Returns false when a pivot is <= 0 (x is then meaningless).
+// Cholesky factor, in place, of B + lam I for the leading C x C block of a CM x CM packed
+// lower triangle; rows/columns >= C are replaced by the identity.  min_ratio receives the
+// smallest pivot ratio d_j / (B_jj + lam) over the leading block (1 when perfectly
+// conditioned, near 0 when a column is nearly a combination of the earlier ones).
+// Returns false when a pivot is <= 0.
 template <class T, int CM>
-__device__ __forceinline__ bool chol_solve(T (&B)[CM * (CM + 1) / 2], const T (&c)[CM], int C,
-                                           T lam, T (&x)[CM]) {
+__device__ __forceinline__ bool chol_factor(T (&B)[CM * (CM + 1) / 2], int C, T lam,
+                                            T &min_ratio) {
 #pragma unroll
     for (int i = 0; i < CM; ++i) {
 #pragma unroll
@@ -105,12 +107,15 @@ __device__ __forceinline__ bool chol_solve(T (&B)[CM * (CM + 1) / 2], const T (&
         }
     }
     bool ok = true;
+    min_ratio = T(1);
 #pragma unroll
     for (int j = 0; j < CM; ++j) {
-        T d = B[tri(j, j)];
+        const T a_jj = B[tri(j, j)];
+        T d = a_jj;
 #pragma unroll
         for (int k = 0; k < j; ++k) d -= B[tri(j, k)] * B[tri(j, k)];
         ok = ok && (d > T(0));
+        if (a_jj > T(0)) min_ratio = fmin(min_ratio, d / a_jj);
         const T ljj = sqrt(d > T(0) ? d : T(1));
         B[tri(j, j)] = ljj;
 #pragma unroll
@@ -121,22 +126,93 @@ __device__ __forceinline__ bool chol_solve(T (&B)[CM * (CM + 1) / 2], const T (&
             B[tri(i, j)] = s / ljj;
         }
     }
+    return ok;
+}
+
+// x = (L L^T)^-1 r with the factor of chol_factor (r beyond C is ignored).
+template <class T, int CM>
+__device__ __forceinline__ void chol_apply(const T (&L)[CM * (CM + 1) / 2], const T (&r)[CM],
+                                           int C, T (&x)[CM]) {
     T y[CM];
 #pragma unroll
     for (int i = 0; i < CM; ++i) {
-        T s = (i < C) ? c[i] : T(0);
+        T s = (i < C) ? r[i] : T(0);
 #pragma unroll
-        for (int k = 0; k < i; ++k) s -= B[tri(i, k)] * y[k];
-        y[i] = s / B[tri(i, i)];
+        for (int k = 0; k < i; ++k) s -= L[tri(i, k)] * y[k];
+        y[i] = s / L[tri(i, i)];
     }
 #pragma unroll
     for (int i = CM - 1; i >= 0; --i) {
         T s = y[i];
 #pragma unroll
-        for (int k = i + 1; k < CM; ++k) s -= B[tri(k, i)] * x[k];
-        x[i] = s / B[tri(i, i)];
+        for (int k = i + 1; k < CM; ++k) s -= L[tri(k, i)] * x[k];
+        x[i] = s / L[tri(i, i)];
     }
+}
+
+// Solves (B + lam I) x = c for the leading C x C block of a CM x CM packed lower
+// triangle; rows/columns >= C are replaced by the identity (their x is 0).  B is
+// overwritten by its factor.  Returns false when a pivot is <= 0 (x is then meaningless).
+template <class T, int CM>
+__device__ __forceinline__ bool chol_solve(T (&B)[CM * (CM + 1) / 2], const T (&c)[CM], int C,
+                                           T lam, T (&x)[CM]) {
+    T ratio;
+    const bool ok = chol_factor<T, CM>(B, C, lam, ratio);
+    chol_apply<T, CM>(B, c, C, x);
     return ok;
+}
+
+// The row solve of the mode passes (Eq. 4).  Double contexts: the Cholesky above.  Float
+// contexts with a.cond_limit > 0: a row whose smallest pivot ratio is below 1 / cond_limit
+// (or that has a non-positive pivot) is solved again in FP64 from the same sums; with
+// a.refine: one step of iterative refinement, x += (L L^T)^-1 (c - (B + lam I) x) with the
+// residual formed in FP64.  B and c are the row's sums as accumulated; B is not modified.
+template <class T, int CM>
+__device__ __forceinline__ bool row_solve(const PassArgs<T> &a, const T (&B)[CM * (CM + 1) / 2],
+                                          const T (&c)[CM], T lam, T (&x)[CM]) {
+    constexpr int NT = CM * (CM + 1) / 2;
+    const int C = a.C;
+    T L[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) L[q] = B[q];
+    T ratio;
+    bool ok = chol_factor<T, CM>(L, C, lam, ratio);
+    if constexpr (sizeof(T) == 4) {
+        if (a.cond_limit > 0.f && (!ok || ratio * a.cond_limit < 1.f)) {
+            double Bd[NT], cd[CM], xd[CM];
+#pragma unroll
+            for (int q = 0; q < NT; ++q) Bd[q] = (double)B[q];
+#pragma unroll
+            for (int q = 0; q < CM; ++q) cd[q] = (double)c[q];
+            if (!chol_solve<double, CM>(Bd, cd, C, (double)lam, xd)) return false;
+#pragma unroll
+            for (int q = 0; q < CM; ++q) x[q] = (T)xd[q];
+            atomicAdd(&a.stat->fp64_rows, 1ull);
+            return true;
+        }
+        if (!ok) return false;
+        chol_apply<T, CM>(L, c, C, x);
+        if (a.refine) {
+            T r[CM], dx[CM];
+#pragma unroll
+            for (int i = 0; i < CM; ++i) {
+                double s = (i < C) ? (double)c[i] - (double)lam * (double)x[i] : 0.0;
+#pragma unroll
+                for (int j = 0; j < CM; ++j) {
+                    const T b = j <= i ? B[tri(i, j)] : B[tri(j, i)];
+                    if (i < C && j < C) s -= (double)b * (double)x[j];
+                }
+                r[i] = (T)s;
+            }
+            chol_apply<T, CM>(L, r, C, dx);
+#pragma unroll
+            for (int i = 0; i < CM; ++i) x[i] += dx[i];
+        }
+        return true;
+    } else {
+        if (ok) chol_apply<T, CM>(L, c, C, x);
+        return ok;
+    }
 }
 
 template <class T, int CM>
@@ -686,7 +762,9 @@ __global__ void __launch_bounds__(pass_max_warps<T>() * kWarp, 1)
 
 // Rows held by a single item: one thread per row reads its slot and solves
 // (B + lambda I) a = c (Eq. 4) by the register Cholesky of Section 3.1.
-template <class T, int CM>
+// XS: the solve options of float contexts (refinement / FP64 fallback) are on; the plain
+// Cholesky otherwise, so that the default kernels carry none of their registers.
+template <class T, int CM, bool XS>
 __global__ void __launch_bounds__(128) k_solve_rows(const PassArgs<T> a, const SplitRow *rows,
                                                     int n_rows) {
     constexpr int NT = CM * (CM + 1) / 2, NB = NT + CM;
@@ -700,13 +778,13 @@ __global__ void __launch_bounds__(128) k_solve_rows(const PassArgs<T> a, const S
 #pragma unroll
     for (int q = 0; q < CM; ++q) c[q] = p[NT + q];
     const T lam = a.weighted ? a.lambda * (T)sr.len : a.lambda;
-    if (chol_solve<T, CM>(B, c, a.C, lam, x))
+    if (XS ? row_solve<T, CM>(a, B, c, lam, x) : chol_solve<T, CM>(B, c, a.C, lam, x))
         write_row<T, CM>(a, sr.row, x);
     else
         atomicAdd(&a.stat->singular_rows, 1ull);
 }
 
-template <class T, int CM>
+template <class T, int CM, bool XS>
 __global__ void __launch_bounds__(kCombineThreads) k_combine(const PassArgs<T> a,
                                                              const SplitRow *rows) {
     constexpr int NT = CM * (CM + 1) / 2, NB = NT + CM;
@@ -735,7 +813,7 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(const PassArgs<T> a
 #pragma unroll
         for (int q = 0; q < CM; ++q) c[q] = tot[NT + q];
         const T lam = a.weighted ? a.lambda * (T)sr.len : a.lambda;
-        if (chol_solve<T, CM>(B, c, a.C, lam, x))
+        if (XS ? row_solve<T, CM>(a, B, c, lam, x) : chol_solve<T, CM>(B, c, a.C, lam, x))
             write_row<T, CM>(a, sr.row, x);
         else
             atomicAdd(&a.stat->singular_rows, 1ull);
@@ -883,7 +961,10 @@ void launch_mode_pass_cm(const PassArgs<T> &a, const PassPlan &plan, cudaStream_
 template <class T, int CM>
 void launch_combine_cm(const PassArgs<T> &a, const SplitRow *rows, int n_rows, cudaStream_t st) {
     if (n_rows <= 0) return;
-    k_combine<T, CM><<<n_rows, kCombineThreads, 0, st>>>(a, rows);
+    if (sizeof(T) == 4 && (a.refine || a.cond_limit > 0.f))
+        k_combine<T, CM, true><<<n_rows, kCombineThreads, 0, st>>>(a, rows);
+    else
+        k_combine<T, CM, false><<<n_rows, kCombineThreads, 0, st>>>(a, rows);
     TFS_CUDA(cudaGetLastError());
 }
 
@@ -891,7 +972,10 @@ template <class T, int CM>
 void launch_solve_rows_cm(const PassArgs<T> &a, const SplitRow *rows, int n_rows,
                           cudaStream_t st) {
     if (n_rows <= 0) return;
-    k_solve_rows<T, CM><<<(n_rows + 127) / 128, 128, 0, st>>>(a, rows, n_rows);
+    if (sizeof(T) == 4 && (a.refine || a.cond_limit > 0.f))
+        k_solve_rows<T, CM, true><<<(n_rows + 127) / 128, 128, 0, st>>>(a, rows, n_rows);
+    else
+        k_solve_rows<T, CM, false><<<(n_rows + 127) / 128, 128, 0, st>>>(a, rows, n_rows);
     TFS_CUDA(cudaGetLastError());
 }
 

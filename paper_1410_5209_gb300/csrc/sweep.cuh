@@ -50,6 +50,11 @@ struct PassArgs {
     DeviceStatus *stat;
     unsigned long long *ticket;          // monotone bin counter shared by all passes
     unsigned long long ticket_base;      // its value when this launch starts
+    // float contexts: one step of iterative refinement of every row solve (residual of the
+    // system in FP64), and a new solve in FP64 of rows whose smallest pivot ratio
+    // d_j / (B_jj + lambda) of the Cholesky is below 1 / cond_limit (0: never)
+    int refine;
+    float cond_limit;
 };
 
 template <class T>
@@ -155,6 +160,16 @@ template <class T>
 void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,
                        cudaStream_t st);
 int res_wide_blocks(int P);
+// Split rows of wide subsets with more than kSlotGroup partial slots: their slots are
+// first summed in groups of kSlotGroup consecutive slots, one block per group, each sum
+// stored in the group's first slot (groups [2 g] = first slot, [2 g + 1] = count);
+// k_solve_wide then adds the group sums in order.  A partial of a wide subset holds
+// C(C+1)/2 + C values, and a row split into thousands of chunks would otherwise be
+// summed by one warp.
+constexpr int kSlotGroup = 64;
+template <class T>
+void launch_sum_slot_groups(T *partials, int NB, const int32_t *groups, int n_groups,
+                            cudaStream_t st);
 template <class T>
 void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st);
 

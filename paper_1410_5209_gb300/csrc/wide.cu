@@ -492,9 +492,24 @@ __global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<fl
                      : "memory");
 }
 
+// Shared memory of one warp of k_solve_wide: the system (packed triangle and rhs) and,
+// for float contexts that refine or may fall back to FP64, a copy of the sums and a double
+// copy for the FP64 solve.
+template <class T>
+__host__ __device__ inline size_t wide_solve_warp_bytes(int C, bool refine, bool fallback) {
+    const size_t nb = (size_t)C * (C + 1) / 2 + C;
+    size_t b = nb * sizeof(T);
+    if (sizeof(T) == 4 && (refine || fallback)) b += nb * sizeof(T);
+    b = (b + 15) / 16 * 16;
+    if (sizeof(T) == 4 && fallback) b += nb * sizeof(double);
+    return b;
+}
+
 // One warp per row (kSolveWarps rows per block): sums the row's slots in slot order
 // into a packed lower triangle in shared memory, solves (B + lambda I) x = c and writes
-// x to A_n[row][S[c]] and to the cur region of the own slice row.
+// x to A_n[row][S[c]] and to the cur region of the own slice row.  Float contexts refine
+// the solve or solve ill-conditioned rows again in FP64 as PassArgs::refine / cond_limit
+// say (the narrow row_solve does the same per thread).
 template <class T>
 __global__ void __launch_bounds__(kSolveWarps * 32) k_solve_wide(const PassArgs<T> a,
                                                                  const SplitRow *rows, int n_rows,
@@ -505,24 +520,69 @@ __global__ void __launch_bounds__(kSolveWarps * 32) k_solve_wide(const PassArgs<
     const int r = blockIdx.x * (int)(blockDim.x >> 5) + warp;
     if (r >= n_rows) return;
     const int NT = CM * (CM + 1) / 2, NB = NT + CM;
-    const size_t per_warp = (size_t)C * (C + 1) / 2 + C;
-    T *P = reinterpret_cast<T *>(smem_raw) + warp * per_warp;
-    T *cv = P + (size_t)C * (C + 1) / 2;
+    const bool refine = sizeof(T) == 4 && a.refine;
+    const bool fallback = sizeof(T) == 4 && a.cond_limit > 0.f;
+    const size_t nt = (size_t)C * (C + 1) / 2;
+    unsigned char *wbase = smem_raw + warp * wide_solve_warp_bytes<T>(C, refine, fallback);
+    T *P = reinterpret_cast<T *>(wbase);
+    T *cv = P + nt;
+    T *P0 = cv + C;  // the sums as accumulated (refine / fallback)
+    T *c0 = P0 + nt;
     const SplitRow sr = rows[r];
+    // rows with more than kSlotGroup slots hold their group sums at every kSlotGroup-th slot
+    const int step = sr.n_slots > kSlotGroup ? kSlotGroup : 1;
     // the first C rows of the packed CM-triangle are the packed C-triangle
     for (int q = lane; q < C * (C + 1) / 2; q += 32) {
         T s = T(0);
-        for (int k = 0; k < sr.n_slots; ++k) s += a.partials[(int64_t)(sr.first_slot + k) * NB + q];
+        for (int k = 0; k < sr.n_slots; k += step)
+            s += a.partials[(int64_t)(sr.first_slot + k) * NB + q];
         P[q] = s;
+        if (refine || fallback) P0[q] = s;
     }
     for (int q = lane; q < C; q += 32) {
         T s = T(0);
-        for (int k = 0; k < sr.n_slots; ++k) s += a.partials[(int64_t)(sr.first_slot + k) * NB + NT + q];
+        for (int k = 0; k < sr.n_slots; k += step)
+            s += a.partials[(int64_t)(sr.first_slot + k) * NB + NT + q];
         cv[q] = s;
+        if (refine || fallback) c0[q] = s;
     }
     __syncwarp();
     const T lam = a.weighted ? a.lambda * (T)sr.len : a.lambda;
-    if (!warp_chol_solve<T>(P, cv, C, lam, lane)) {
+    T ratio = T(1);
+    bool ok = warp_chol_factor<T>(P, C, lam, lane, &ratio);
+    if (fallback && (!ok || ratio * (T)a.cond_limit < T(1))) {
+        double *Pd = reinterpret_cast<double *>(
+            wbase + ((2 * (nt + C) * sizeof(T) + 15) / 16) * 16);
+        double *cd = Pd + nt;
+        for (int q = lane; q < (int)nt; q += 32) Pd[q] = (double)P0[q];
+        for (int q = lane; q < C; q += 32) cd[q] = (double)c0[q];
+        __syncwarp();
+        ok = warp_chol_factor<double>(Pd, C, (double)lam, lane);
+        if (ok) {
+            warp_chol_apply<double>(Pd, cd, C, lane);
+            for (int q = lane; q < C; q += 32) cv[q] = (T)cd[q];
+            if (lane == 0) atomicAdd(&a.stat->fp64_rows, 1ull);
+        }
+        __syncwarp();
+    } else if (ok) {
+        warp_chol_apply<T>(P, cv, C, lane);
+        if (refine) {
+            // residual of the system as accumulated, in FP64: c - (B + lam I) x, into c0
+            for (int i = lane; i < C; i += 32) {
+                double s = (double)c0[i] - (double)lam * (double)cv[i];
+                for (int j = 0; j < C; ++j) {
+                    const T b = j <= i ? P0[ptri(i, j)] : P0[ptri(j, i)];
+                    s -= (double)b * (double)cv[j];
+                }
+                c0[i] = (T)s;
+            }
+            __syncwarp();
+            warp_chol_apply<T>(P, c0, C, lane);
+            for (int q = lane; q < C; q += 32) cv[q] += c0[q];
+            __syncwarp();
+        }
+    }
+    if (!ok) {
         if (lane == 0) atomicAdd(&a.stat->singular_rows, 1ull);
         return;
     }
@@ -531,6 +591,21 @@ __global__ void __launch_bounds__(kSolveWarps * 32) k_solve_wide(const PassArgs<
     for (int q = lane; q < C; q += 32) {
         z[q] = cv[q];
         Ar[a.S[q]] = cv[q];
+    }
+}
+
+// One block per group of consecutive slots of a split row: the group's elementwise sum,
+// in slot order, into its first slot.
+template <class T>
+__global__ void __launch_bounds__(256) k_sum_slot_groups(T *partials, int NB,
+                                                         const int32_t *groups) {
+    const int64_t first = groups[2 * blockIdx.x];
+    const int cnt = groups[2 * blockIdx.x + 1];
+    T *base = partials + first * NB;
+    for (int q = threadIdx.x; q < NB; q += blockDim.x) {
+        T s = base[q];
+        for (int k = 1; k < cnt; ++k) s += base[(int64_t)k * NB + q];
+        base[q] = s;
     }
 }
 
@@ -694,7 +769,8 @@ void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, i
     int dev = 0, smem_blk = 0;
     TFS_CUDA(cudaGetDevice(&dev));
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t per_warp = sizeof(T) * ((size_t)a.C * (a.C + 1) / 2 + a.C);
+    const size_t per_warp =
+        wide_solve_warp_bytes<T>(a.C, a.refine != 0, a.cond_limit > 0.f);
     const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kSolveWarps, smem_blk / per_warp));
     const size_t smem = per_warp * wpb;
     TFS_CUDA(raise_smem_limit((const void *)k_solve_wide<T>, (int)smem));
@@ -703,6 +779,14 @@ void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, i
 }
 
 int res_wide_blocks(int P) { return (P + kWideThreads / 32 - 1) / (kWideThreads / 32); }
+
+template <class T>
+void launch_sum_slot_groups(T *partials, int NB, const int32_t *groups, int n_groups,
+                            cudaStream_t st) {
+    if (n_groups <= 0) return;
+    k_sum_slot_groups<T><<<n_groups, 256, 0, st>>>(partials, NB, groups);
+    TFS_CUDA(cudaGetLastError());
+}
 
 template <class T>
 void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st) {
@@ -716,7 +800,8 @@ void launch_res_wide(const ResArgs<T> &a, int W, cudaStream_t st) {
                                       cudaStream_t);                                          \
     template void launch_solve_wide<T>(const PassArgs<T> &, const SplitRow *, int, int, int,  \
                                        cudaStream_t);                                         \
-    template void launch_res_wide<T>(const ResArgs<T> &, int, cudaStream_t);
+    template void launch_res_wide<T>(const ResArgs<T> &, int, cudaStream_t);                \
+    template void launch_sum_slot_groups<T>(T *, int, const int32_t *, int, cudaStream_t);
 TFS_INST(float)
 TFS_INST(double)
 #undef TFS_INST

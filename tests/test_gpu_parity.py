@@ -885,3 +885,79 @@ def test_autotune_rejects_bad_candidates():
             f.autotune(Cs, Ps)
         assert e.value.status == tf.EINVAL
     f.sweep(2, 0.1, 1)
+
+
+# --------------------------------------------------------------------------- solve options
+
+
+def _dup_column_case(K, seed):
+    """Factors of modes 2 and 3 with columns 0 and 1 equal: for every mode-1 row the Gram
+    matrix of Eq. 4 is singular in those columns, B + lambda I has condition ~ 1/lambda."""
+    p = synth.small(seed, (300, 200, 50), 30_000, 3, K)
+    c, x = p.numpy()
+    x = x.astype(np.float32).astype(np.float64)
+    A = [a.numpy().astype(np.float32).astype(np.float64) for a in p.init_factors()]
+    for n in (1, 2):
+        A[n][:, 1] = A[n][:, 0]
+    return p, c, x, A
+
+
+def _first_mode_error(p, c, x, A, C, lam, refine, cond):
+    t = oracle.Tensor(c, x, p.dims)
+    Ao = [a.copy() for a in A]
+    r = oracle.residual(t, Ao)
+    order = np.arange(p.K, dtype=np.int32)
+    # one split (C = K) so that mode 1's rows see exactly the prepared factors
+    oracle.sals_sweep(t, Ao, r, C, lam, 1, order)
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
+    for n in range(3):
+        f.set_factors(n, A[n])
+    f.set_solve(refine, cond)
+    f.sweep(C, lam, 1, order)
+    err = np.linalg.norm(f.factors(0) - Ao[0]) / np.linalg.norm(Ao[0])
+    out = err, f.counters()["singular_rows"], f.fp64_rows()
+    f.close()
+    return out
+
+
+@pytest.mark.parametrize("K", [4, 20])   # narrow register solve, wide warp solve
+def test_fp64_fallback_solves_rows_fp32_cannot(K):
+    """lambda = 1e-6 with duplicated columns: the FP32 Cholesky meets non-positive pivots
+    and leaves rows unchanged; with the FP64 fallback no row is singular and the first
+    mode's update matches the FP64 oracle."""
+    p, c, x, A = _dup_column_case(K, 210 + K)
+    err0, sing0, f640 = _first_mode_error(p, c, x, A, K, 1e-6, 0, 0.0)
+    err1, sing1, f641 = _first_mode_error(p, c, x, A, K, 1e-6, 0, 1e4)
+    assert sing0 > 0 and f640 == 0
+    assert sing1 == 0 and f641 > 0
+    assert err1 < 1e-5, (err0, err1)
+
+
+@pytest.mark.parametrize("K", [4, 20])
+def test_refinement_reduces_solve_error(K):
+    """lambda = 1e-3 with duplicated columns (condition ~ 1e3-1e4): one refinement step
+    with an FP64 residual brings the first mode's update to FP32 accuracy against the
+    FP64 oracle, far below the plain FP32 Cholesky's error."""
+    p, c, x, A = _dup_column_case(K, 230 + K)
+    err0, sing0, _ = _first_mode_error(p, c, x, A, K, 1e-3, 0, 0.0)
+    err1, sing1, _ = _first_mode_error(p, c, x, A, K, 1e-3, 1, 0.0)
+    assert sing0 == sing1 == 0
+    assert err1 < 1e-5 and err1 < err0 / 10, (err0, err1)
+
+
+def test_solve_options_leave_double_contexts_alone():
+    p = synth.small(240, (300, 200, 50), 30_000, 3, 8)
+    c, x = p.numpy()
+    out = []
+    for opts in ((0, 0.0), (1, 1e4)):
+        f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F64)
+        f.set_solve(*opts)
+        for t in range(2):
+            f.sweep(4, 0.2, 1, p.column_order(t, 4))
+        out.append([f.factors(n) for n in range(3)])
+        assert f.fp64_rows() == 0
+        f.close()
+    for n in range(3):
+        assert np.array_equal(out[0][n], out[1][n])
+    with pytest.raises(tf.TFError):   # a negative limit is refused
+        tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F64).set_solve(False, -1.0)
