@@ -210,18 +210,28 @@ def study(args, rank, world):
             tests.append(test_rmse())
         return times, rmses, tests
 
+    # forms: Gram precision (FP32-level; one TF32 product per term on the tensor cores, wide
+    # C only) x row solves (plain FP32 Cholesky; FP64-residual refinement + FP64 re-solve
+    # of rows with pivot ratio < 1e-4)
     for C in [int(c) for c in args.study_c.split(",")]:
         for prec in ((0, 1) if C > 16 else (0,)):
-            f.set_precision(prec)
-            run(C, 1)  # warm-up (kernel selection, buffers)
-            times, rmses, tests = run(C, args.study_sweeps)
-            ms = float(np.median(times))
-            print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz, "ms_per_sweep": ms,
-                              "precision": ["fp32", "tf32x1"][prec],
-                              "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
-                              "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
-                              "pass_path": f.counters()["pass_path"]}), flush=True)
+            for refine, cond in ((0, 0.0), (1, 1e4)):
+                f.set_precision(prec)
+                f.set_solve(refine, cond)
+                run(C, 1)  # warm-up (kernel selection, buffers)
+                f64_0 = f.fp64_rows()
+                times, rmses, tests = run(C, args.study_sweeps)
+                ms = float(np.median(times))
+                print(json.dumps({"study": "C", "C": C, "K": K, "nnz": p_nnz,
+                                  "ms_per_sweep": ms,
+                                  "precision": ["fp32", "tf32x1"][prec] +
+                                               ("+refine+fp64rows" if refine else ""),
+                                  "fp64_rows": f.fp64_rows() - f64_0,
+                                  "nnz_rank_per_s": p_nnz * K / (ms / 1e3),
+                                  "sweep_ms": times, "train_rmse": rmses, "test_rmse": tests,
+                                  "pass_path": f.counters()["pass_path"]}), flush=True)
         f.set_precision(0)
+        f.set_solve(0, 0.0)
     C = WORKLOAD["C"]
     policies = [q for q in args.study_policies.split(",") if q]
     for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),
