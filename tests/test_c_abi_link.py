@@ -1,5 +1,6 @@
 """The library is usable from plain C: a C program that includes include/tf_sals.h and
-links libtfsals.so calls the host-only entry points (no GPU needed)."""
+include/tf_server.h and links libtfsals.so calls the host-only entry points (no GPU
+needed)."""
 import os
 import shutil
 import subprocess
@@ -13,6 +14,7 @@ C_SRC = r"""
 #include <stdio.h>
 #include <string.h>
 #include "tf_sals.h"
+#include "tf_server.h"
 
 int main(void) {
     /* Algorithm 3 on 5 rows of one mode over 2 machines */
@@ -31,8 +33,17 @@ int main(void) {
     int64_t covered = 0;
     for (int64_t i = 0; i < n_items; ++i) covered += items[i].len;
     if (tf_create(NULL, NULL, TF_F32, dims, 0, 0, 1, 0, NULL, 0, NULL) != TF_EINVAL) return 4;
-    printf("%s|%d %d %d %d %d|%lld %lld %lld\n", tf_version(), a0[0], a0[1], a0[2], a0[3], a0[4],
-           (long long)n_items, (long long)covered, (long long)bin_ptr[4]);
+    /* the serving loop's admission decision and the memory estimate, host only */
+    const int64_t need[4] = {5, 3, 8, 1};
+    int32_t byp[4] = {0, 0, 0, 0}, admit[4];
+    const int started = tf_server_plan_admission(4, need, byp, 6, -1, 8, 8, admit);
+    const int64_t dims3[3] = {1000, 1000, 100};
+    int64_t est = 0;
+    if (tf_estimate_bytes(dims3, 3, 100000, 10, 5, TF_F32, 0, 152, &est) != TF_OK) return 5;
+    printf("%s|%d %d %d %d %d|%lld %lld %lld|%d %d%d%d%d %d%d%d%d|%lld\n", tf_version(), a0[0],
+           a0[1], a0[2], a0[3], a0[4], (long long)n_items, (long long)covered,
+           (long long)bin_ptr[4], started, admit[0], admit[1], admit[2], admit[3], byp[0],
+           byp[1], byp[2], byp[3], (long long)est);
     return 0;
 }
 """
@@ -51,10 +62,13 @@ def test_c_program_links_and_calls_host_entry_points():
         subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                         src, "-o", exe, lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
-    version, assign, plan = out.split("|")
+    version, assign, plan, adm, est = out.split("|")
     assert version.startswith("sals-gb300")
     # rows in the order 0 (7), 2 (4), 3 (4), 4 (2), 1 (1); each to the machine with the
     # fewest entries so far (cap 3 rows): 0 -> m0, 2 -> m1, 3 -> m1, 4 -> m0, 1 -> m1
     assert assign.split() == ["0", "1", "1", "1", "0"]
     n_items, covered, total = map(int, plan.split())
     assert covered == 110 and total == n_items and n_items > 3   # the 100-entry row is split
+    # first fit in arrival order with room 6: jobs 0 and 3 start, 1 and 2 are passed once
+    assert adm.split() == ["2", "1001", "0110"]
+    assert int(est) > 100000 * 4 * 10   # at least values, residual copies, orders, indices
