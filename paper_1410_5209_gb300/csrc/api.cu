@@ -6,11 +6,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <exception>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <thread>
 #include <vector>
 
 #include <cuda.h>
@@ -325,6 +327,8 @@ struct Impl : CtxBase {
         }
 
         // per-mode sorted layout
+        std::vector<std::vector<int64_t>> offs;
+        std::vector<PlanHost> plans;
         SortWorkspace ws;
         Buf<uint32_t> keys;
         keys.alloc(nnz, st);
@@ -350,26 +354,34 @@ struct Impl : CtxBase {
                 }
             }
             // degree ranks: slices are stored with each mode's rows in decreasing order of
-            // their entry counts (equal counts by row id)
+            // their entry counts (equal counts by row id); one host thread per mode
+            offs = download_offsets();
+            std::vector<std::vector<int32_t>> ids((size_t)N), ranks((size_t)N);
+            {
+                std::vector<std::thread> th;
+                for (int n = 0; n < N; ++n)
+                    th.emplace_back([&, n] {
+                        const int64_t I = mode[n].I;
+                        std::vector<int64_t> cnt((size_t)I);
+                        for (int64_t i = 0; i < I; ++i) cnt[i] = offs[n][i + 1] - offs[n][i];
+                        const std::vector<int64_t> order = rows_by_degree(cnt);
+                        ids[n].resize((size_t)I);
+                        ranks[n].resize((size_t)I);
+                        for (int64_t r = 0; r < I; ++r) {
+                            ids[n][r] = (int32_t)order[r];
+                            ranks[n][order[r]] = (int32_t)r;
+                        }
+                    });
+                for (auto &t : th) t.join();
+            }
             for (int n = 0; n < N; ++n) {
                 ModeLayout &L = mode[n];
-                std::vector<int64_t> off((size_t)L.I + 1);
-                TFS_CUDA(cudaMemcpyAsync(off.data(), L.off.p, off.size() * sizeof(int64_t),
-                                         cudaMemcpyDeviceToHost, st));
-                TFS_CUDA(cudaStreamSynchronize(st));
-                std::vector<int32_t> id((size_t)L.I), rank((size_t)L.I);
-                for (int64_t i = 0; i < L.I; ++i) id[i] = (int32_t)i;
-                std::stable_sort(id.begin(), id.end(), [&](int32_t a_, int32_t b_) {
-                    return off[a_ + 1] - off[a_] > off[b_ + 1] - off[b_];
-                });
-                for (int64_t r = 0; r < L.I; ++r) rank[id[r]] = (int32_t)r;
                 L.id_of.alloc(L.I, st);
                 L.rank_of.alloc(L.I, st);
-                TFS_CUDA(cudaMemcpyAsync(L.id_of.p, id.data(), L.I * sizeof(int32_t),
+                TFS_CUDA(cudaMemcpyAsync(L.id_of.p, ids[n].data(), L.I * sizeof(int32_t),
                                          cudaMemcpyHostToDevice, st));
-                TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, rank.data(), L.I * sizeof(int32_t),
+                TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, ranks[n].data(), L.I * sizeof(int32_t),
                                          cudaMemcpyHostToDevice, st));
-                TFS_CUDA(cudaStreamSynchronize(st));
             }
             for (int n = 0; n < N; ++n) {
                 ModeLayout &L = mode[n];
@@ -388,6 +400,9 @@ struct Impl : CtxBase {
                     ++t;
                 }
             }
+            // the row schedules, on the host while the device gathers the index streams
+            plans = plan_all_host(offs);
+            TFS_CUDA(cudaStreamSynchronize(st));  // ids / ranks uploaded
         } catch (...) {
             ws.release(st);
             throw;
@@ -396,7 +411,7 @@ struct Impl : CtxBase {
         keys.reset();
         soa.reset();
 
-        for (int n = 0; n < N; ++n) plan(n);
+        for (int n = 0; n < N; ++n) plan_upload(n, plans[n]);
 
         // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
         const double std = pow((double)K, -1.0 / (2.0 * N));
@@ -414,65 +429,107 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaStreamSynchronize(st));
     }
 
-    void plan(int n) {
-        ModeLayout &L = mode[n];
-        ++layout_gen;
-        std::vector<int64_t> off((size_t)L.I + 1);
-        TFS_CUDA(cudaMemcpyAsync(off.data(), L.off.p, off.size() * sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, st));
-        TFS_CUDA(cudaStreamSynchronize(st));
+    // Row schedule of one mode, computed on the host from its row offsets (no device call,
+    // so the modes' schedules can be computed in parallel threads).
+    struct PlanHost {
         std::vector<tf_item> items;
         std::vector<int64_t> bin_ptr;
+        std::vector<SplitRow> split, single;
+        std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
         int64_t n_slots = 0;
-        tf_status s = plan_mode(off.data(), L.I, P, 0, policy, seed, items, n_slots, bin_ptr);
+    };
+
+    PlanHost plan_host(const std::vector<int64_t> &off, int64_t I) const {
+        PlanHost h;
+        tf_status s = plan_mode(off.data(), I, P, 0, policy, seed, h.items, h.n_slots, h.bin_ptr);
         if (s != TF_OK) throw ApiError{s, "row scheduling failed"};
         // rows and their slots (a row's slots are consecutive, in entry order):
         // single-item rows are solved by k_solve_rows, split rows by k_combine
-        std::vector<tf_item> by_slot(items);
-        std::sort(by_slot.begin(), by_slot.end(),
-                  [](const tf_item &a, const tf_item &b) { return a.slot < b.slot; });
-        std::vector<SplitRow> split, single;
-        for (size_t i = 0; i < by_slot.size();) {
-            size_t j = i;
-            while (j < by_slot.size() && by_slot[j].row == by_slot[i].row) ++j;
-            const int64_t r = by_slot[i].row;
-            const SplitRow sr{by_slot[i].row, by_slot[i].slot, (int32_t)(j - i), 0,
-                              off[r + 1] - off[r]};
-            (j - i > 1 ? split : single).push_back(sr);
-            i = j;
+        std::vector<int32_t> item_of_slot((size_t)h.n_slots, -1);
+        for (size_t i = 0; i < h.items.size(); ++i) item_of_slot[(size_t)h.items[i].slot] = (int32_t)i;
+        for (int64_t q = 0; q < h.n_slots;) {
+            const tf_item &first = h.items[(size_t)item_of_slot[(size_t)q]];
+            int64_t q2 = q + 1;
+            while (q2 < h.n_slots && h.items[(size_t)item_of_slot[(size_t)q2]].row == first.row) ++q2;
+            const int64_t r = first.row;
+            const SplitRow sr{first.row, first.slot, (int32_t)(q2 - q), 0, off[r + 1] - off[r]};
+            (q2 - q > 1 ? h.split : h.single).push_back(sr);
+            q = q2;
         }
-        L.P = P;
-        L.n_items = (int64_t)items.size();
-        L.n_slots = n_slots;
-        L.n_split = (int)split.size();
-        L.n_single = (int)single.size();
-        L.items.alloc(items.size(), st);
-        L.bin_ptr.alloc(bin_ptr.size(), st);
-        L.split.alloc(split.size(), st);
-        L.single.alloc(single.size(), st);
-        std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
-        for (const SplitRow &sr : split)
+        for (const SplitRow &sr : h.split)
             if (sr.n_slots > kSlotGroup)
                 for (int g = 0; g < sr.n_slots; g += kSlotGroup) {
-                    groups.push_back(sr.first_slot + g);
-                    groups.push_back(std::min(kSlotGroup, sr.n_slots - g));
+                    h.groups.push_back(sr.first_slot + g);
+                    h.groups.push_back(std::min(kSlotGroup, sr.n_slots - g));
                 }
-        L.n_groups = (int)(groups.size() / 2);
-        L.groups.alloc(std::max<size_t>(groups.size(), 2), st);
-        if (!groups.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.groups.p, groups.data(), groups.size() * sizeof(int32_t),
+        return h;
+    }
+
+    // Device copies of a schedule (queued on st; h must live until st reaches them).
+    void plan_upload(int n, const PlanHost &h) {
+        ModeLayout &L = mode[n];
+        ++layout_gen;
+        L.P = P;
+        L.n_items = (int64_t)h.items.size();
+        L.n_slots = h.n_slots;
+        L.n_split = (int)h.split.size();
+        L.n_single = (int)h.single.size();
+        L.items.alloc(h.items.size(), st);
+        L.bin_ptr.alloc(h.bin_ptr.size(), st);
+        L.split.alloc(h.split.size(), st);
+        L.single.alloc(h.single.size(), st);
+        L.n_groups = (int)(h.groups.size() / 2);
+        L.groups.alloc(std::max<size_t>(h.groups.size(), 2), st);
+        if (!h.groups.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.groups.p, h.groups.data(), h.groups.size() * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, st));
-        if (!single.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.single.p, single.data(), single.size() * sizeof(SplitRow),
+        if (!h.single.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.single.p, h.single.data(), h.single.size() * sizeof(SplitRow),
                                      cudaMemcpyHostToDevice, st));
-        if (!items.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.items.p, items.data(), items.size() * sizeof(tf_item),
+        if (!h.items.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.items.p, h.items.data(), h.items.size() * sizeof(tf_item),
                                      cudaMemcpyHostToDevice, st));
-        TFS_CUDA(cudaMemcpyAsync(L.bin_ptr.p, bin_ptr.data(), bin_ptr.size() * sizeof(int64_t),
+        TFS_CUDA(cudaMemcpyAsync(L.bin_ptr.p, h.bin_ptr.data(), h.bin_ptr.size() * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st));
-        if (!split.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.split.p, split.data(), split.size() * sizeof(SplitRow),
+        if (!h.split.empty())
+            TFS_CUDA(cudaMemcpyAsync(L.split.p, h.split.data(), h.split.size() * sizeof(SplitRow),
                                      cudaMemcpyHostToDevice, st));
+    }
+
+    // Schedules of every mode from their row offsets on the host: one thread per mode.
+    std::vector<PlanHost> plan_all_host(const std::vector<std::vector<int64_t>> &offs) const {
+        std::vector<PlanHost> hs((size_t)N);
+        std::vector<std::exception_ptr> errs((size_t)N);
+        std::vector<std::thread> th;
+        for (int n = 0; n < N; ++n)
+            th.emplace_back([&, n] {
+                try {
+                    hs[n] = plan_host(offs[n], dims[n]);
+                } catch (...) {
+                    errs[n] = std::current_exception();
+                }
+            });
+        for (auto &t : th) t.join();
+        for (auto &e : errs)
+            if (e) std::rethrow_exception(e);
+        return hs;
+    }
+
+    std::vector<std::vector<int64_t>> download_offsets() {
+        std::vector<std::vector<int64_t>> offs((size_t)N);
+        for (int n = 0; n < N; ++n) {
+            offs[n].resize((size_t)mode[n].I + 1);
+            TFS_CUDA(cudaMemcpyAsync(offs[n].data(), mode[n].off.p, offs[n].size() * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+        }
+        TFS_CUDA(cudaStreamSynchronize(st));
+        return offs;
+    }
+
+    void plan_all() {
+        const auto offs = download_offsets();
+        const auto hs = plan_all_host(offs);
+        for (int n = 0; n < N; ++n) plan_upload(n, hs[n]);
         TFS_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
     }
 
@@ -1389,7 +1446,7 @@ struct Impl : CtxBase {
         TFS_CUDA(cudaStreamSynchronize(st));
         policy = pol;
         P = P_ > 0 ? P_ : default_bins(num_sms, nnz);
-        for (int n = 0; n < N; ++n) plan(n);
+        plan_all();
     }
 };
 

@@ -122,6 +122,8 @@ void launch_dup_check(const int32_t *coords_soa, int N, int64_t nnz, const int32
 
 // ------------------------------------------------------------------ scheduling (sched.cpp)
 
+// Row ids in decreasing order of count, equal counts in increasing id (host).
+std::vector<int64_t> rows_by_degree(const std::vector<int64_t> &count);
 tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_policy policy,
                     uint64_t seed, std::vector<tf_item> &items, int64_t &n_slots,
                     std::vector<int64_t> &bin_ptr);

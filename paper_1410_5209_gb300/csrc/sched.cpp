@@ -38,13 +38,67 @@ struct BinKey {
 };
 using MinHeap = std::priority_queue<BinKey, std::vector<BinKey>, std::greater<BinKey>>;
 
-// Rows in decreasing length, equal lengths in increasing index.
+// Rows in decreasing length, equal lengths in increasing index: one sort of packed keys
+// (length in the high 32 bits, complemented; index in the low 32 bits).
 std::vector<int64_t> rows_by_length(const int64_t *len, int64_t I) {
     std::vector<int64_t> order(I);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t b) { return len[a] > len[b]; });
+    // short lengths (chunked LPT jobs): a counting sort, stable in the index
+    int64_t max_len = 0;
+    bool nonneg = true;
+    for (int64_t i = 0; i < I; ++i) {
+        max_len = std::max(max_len, len[i]);
+        nonneg = nonneg && len[i] >= 0;
+    }
+    if (nonneg && max_len <= 4 * I + 1024) {
+        std::vector<int64_t> start((size_t)max_len + 2, 0);
+        for (int64_t i = 0; i < I; ++i) start[(size_t)(max_len - len[i]) + 1] += 1;
+        for (int64_t v = 0; v <= max_len; ++v) start[v + 1] += start[v];
+        for (int64_t i = 0; i < I; ++i) order[(size_t)start[(size_t)(max_len - len[i])]++] = i;
+        return order;
+    }
+    bool packed = I <= (int64_t)UINT32_MAX;
+    for (int64_t i = 0; i < I && packed; ++i) packed = len[i] >= 0 && len[i] <= (int64_t)UINT32_MAX;
+    if (!packed) {
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t a, int64_t b) { return len[a] > len[b]; });
+        return order;
+    }
+    std::vector<uint64_t> key((size_t)I);
+    for (int64_t i = 0; i < I; ++i)
+        key[i] = ((uint64_t)(UINT32_MAX - (uint64_t)len[i]) << 32) | (uint64_t)i;
+    std::sort(key.begin(), key.end());
+    for (int64_t i = 0; i < I; ++i) order[i] = (int64_t)(key[i] & 0xFFFFFFFFull);
     return order;
+}
+
+// LPT: every job, longest first, to the bin with the least load (lowest index on ties).
+// A min-heap of packed keys (load in the high bits, bin in the low 21 bits).
+void lpt_bins(const std::vector<int64_t> &job_len, const std::vector<int64_t> &order, int M,
+              std::vector<int32_t> &bin_of_job) {
+    std::vector<uint64_t> heap((size_t)M);
+    for (int m = 0; m < M; ++m) heap[m] = (uint64_t)m;  // already a min-heap
+    bin_of_job.assign(job_len.size(), -1);
+    auto sift_down = [&](size_t i) {
+        const size_t n = heap.size();
+        const uint64_t v = heap[i];
+        for (;;) {
+            size_t c = 2 * i + 1;
+            if (c >= n) break;
+            if (c + 1 < n && heap[c + 1] < heap[c]) ++c;
+            if (heap[c] >= v) break;
+            heap[i] = heap[c];
+            i = c;
+        }
+        heap[i] = v;
+    };
+    for (int64_t j : order) {
+        const uint64_t top = heap[0];
+        const int32_t m = (int32_t)(top & ((1u << 21) - 1));
+        bin_of_job[j] = m;
+        heap[0] = top + ((uint64_t)job_len[j] << 21);  // load grows, bin stays
+        sift_down(0);
+    }
 }
 
 // Greedy assignment of one mode's jobs to M bins.  cap_rows < 0 means no row cap.
@@ -104,6 +158,10 @@ tf_status assign_rows_impl(tf_sched_policy policy, int N, const int64_t *dims,
     return TF_OK;
 }
 
+std::vector<int64_t> rows_by_degree(const std::vector<int64_t> &count) {
+    return rows_by_length(count.data(), (int64_t)count.size());
+}
+
 tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_policy policy,
                     uint64_t seed, std::vector<tf_item> &items, int64_t &n_slots,
                     std::vector<int64_t> &bin_ptr) {
@@ -139,9 +197,13 @@ tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_
             std::vector<int64_t> len(jobs.size());
             for (size_t j = 0; j < jobs.size(); ++j) len[j] = jobs[j].len;
             std::vector<int64_t> order = rows_by_length(len.data(), (int64_t)len.size());
-            std::vector<int64_t> totals(P, 0);
-            const int64_t cap_rows = policy == TF_SCHED_GREEDY ? (I + P - 1) / P : -1;
-            greedy_bins(len, order, P, cap_rows, totals, bin);
+            if (policy == TF_SCHED_LPT && P < (1 << 21)) {
+                lpt_bins(len, order, P, bin);
+            } else {
+                std::vector<int64_t> totals(P, 0);
+                const int64_t cap_rows = policy == TF_SCHED_GREEDY ? (I + P - 1) / P : -1;
+                greedy_bins(len, order, P, cap_rows, totals, bin);
+            }
             // bins receive jobs longest first: keep that order inside each bin
             std::vector<tf_item> sorted;
             sorted.reserve(jobs.size());
@@ -162,13 +224,13 @@ tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_
         default:
             return TF_EINVAL;
     }
-    // group by bin (stable: keeps the assignment order within a bin)
-    std::stable_sort(jobs.begin(), jobs.end(),
-                     [](const tf_item &a, const tf_item &b) { return a.bin < b.bin; });
+    // group by bin, keeping the assignment order within a bin (a counting sort)
     bin_ptr.assign((size_t)P + 1, 0);
     for (const auto &it : jobs) bin_ptr[it.bin + 1] += 1;
     for (int p = 0; p < P; ++p) bin_ptr[p + 1] += bin_ptr[p];
-    items.swap(jobs);
+    std::vector<int64_t> fill(bin_ptr.begin(), bin_ptr.end() - 1);
+    items.resize(jobs.size());
+    for (const auto &it : jobs) items[(size_t)fill[it.bin]++] = it;
     return TF_OK;
 }
 
