@@ -29,7 +29,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-std::string g_server_create_err;
+thread_local std::string g_server_create_err;
 
 struct Job {
     int64_t id = 0;
