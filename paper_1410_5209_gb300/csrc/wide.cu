@@ -531,20 +531,42 @@ __global__ void __launch_bounds__(kSolveWarps * 32) k_solve_wide(const PassArgs<
     const SplitRow sr = rows[r];
     // rows with more than kSlotGroup slots hold their group sums at every kSlotGroup-th slot
     const int step = sr.n_slots > kSlotGroup ? kSlotGroup : 1;
-    // the first C rows of the packed CM-triangle are the packed C-triangle
-    for (int q = lane; q < C * (C + 1) / 2; q += 32) {
-        T s = T(0);
-        for (int k = 0; k < sr.n_slots; k += step)
-            s += a.partials[(int64_t)(sr.first_slot + k) * NB + q];
-        P[q] = s;
-        if (refine || fallback) P0[q] = s;
-    }
-    for (int q = lane; q < C; q += 32) {
-        T s = T(0);
-        for (int k = 0; k < sr.n_slots; k += step)
-            s += a.partials[(int64_t)(sr.first_slot + k) * NB + NT + q];
-        cv[q] = s;
-        if (refine || fallback) c0[q] = s;
+    const int ntc = C * (C + 1) / 2;
+    if (sr.n_slots == 1) {
+        // a row held by one item: its slot is the system; eight loads in flight per lane
+        // (the first C rows of the packed CM-triangle are the packed C-triangle)
+        const T *src = a.partials + (int64_t)sr.first_slot * NB;
+        for (int q0 = lane; q0 < ntc + C; q0 += 32 * 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + 32 * u;
+                v[u] = q < ntc ? src[q] : (q < ntc + C ? src[NT + (q - ntc)] : T(0));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < ntc + C) {  // cv follows P in shared memory, and c0 follows P0
+                    P[q] = v[u];
+                    if (refine || fallback) P0[q] = v[u];
+                }
+            }
+        }
+    } else {
+        for (int q = lane; q < ntc; q += 32) {
+            T s = T(0);
+            for (int k = 0; k < sr.n_slots; k += step)
+                s += a.partials[(int64_t)(sr.first_slot + k) * NB + q];
+            P[q] = s;
+            if (refine || fallback) P0[q] = s;
+        }
+        for (int q = lane; q < C; q += 32) {
+            T s = T(0);
+            for (int k = 0; k < sr.n_slots; k += step)
+                s += a.partials[(int64_t)(sr.first_slot + k) * NB + NT + q];
+            cv[q] = s;
+            if (refine || fallback) c0[q] = s;
+        }
     }
     __syncwarp();
     const T lam = a.weighted ? a.lambda * (T)sr.len : a.lambda;
@@ -766,12 +788,23 @@ template <class T>
 void launch_solve_wide(const PassArgs<T> &a, const SplitRow *rows, int n_rows, int CM, int W,
                        cudaStream_t st) {
     if (n_rows <= 0) return;
-    int dev = 0, smem_blk = 0;
+    int dev = 0, smem_blk = 0, smem_sm = 0;
     TFS_CUDA(cudaGetDevice(&dev));
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    TFS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     const size_t per_warp =
         wide_solve_warp_bytes<T>(a.C, a.refine != 0, a.cond_limit > 0.f);
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kSolveWarps, smem_blk / per_warp));
+    // warps per block: the most resident warps per SM (each warp holds one system in
+    // shared memory, so the block size decides how well the SM's shared memory is used)
+    int wpb = 1, best = 0;
+    for (int w = 1; w <= kSolveWarps; ++w) {
+        if ((size_t)w * per_warp > (size_t)smem_blk) break;
+        const int blocks = std::min<int>(32, (int)((size_t)smem_sm / ((size_t)w * per_warp + 1024)));
+        if (blocks * w >= best) {
+            best = blocks * w;
+            wpb = w;
+        }
+    }
     const size_t smem = per_warp * wpb;
     TFS_CUDA(raise_smem_limit((const void *)k_solve_wide<T>, (int)smem));
     k_solve_wide<T><<<(n_rows + wpb - 1) / wpb, wpb * 32, smem, st>>>(a, rows, n_rows, CM, W);
