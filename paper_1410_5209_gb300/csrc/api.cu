@@ -333,25 +333,36 @@ struct Impl : CtxBase {
         Buf<uint32_t> keys;
         keys.alloc(nnz, st);
         try {
+            // Mode 0's order, lexicographic in (i_0, i_1, ..., i_{N-1}), by N stable key sorts
+            // (least significant mode first).  Then, for n = N-1 down to 1, mode n's order
+            // (i_n, i_{n+1}, ..., i_{n-1}) is one stable sort by i_n of mode n+1's order:
+            // equal i_n keep (i_{n+1}, ..., i_{n-1}, i_n), which is the rest of mode n's key.
+            // 2N - 1 key sorts instead of N^2; the orders are total, so the same.
+            auto sorted_by = [&](ModeLayout &L, int m) {
+                launch_gather_keys(soa.p + (size_t)m * nnz, L.perm.p, keys.p, nnz, st);
+                radix_sort_pairs(keys.p, L.perm.p, nnz, ceil_log2_u64((uint64_t)dims[m]), ws, st);
+            };
             for (int n = 0; n < N; ++n) {
+                mode[n].I = dims[n];
+                mode[n].perm.alloc(nnz, st);
+                mode[n].off.alloc(mode[n].I + 1, st);
+            }
+            launch_iota(mode[0].perm.p, nnz, st);
+            for (int m = N - 1; m >= 0; --m) sorted_by(mode[0], m);
+            launch_offsets(keys.p, nnz, mode[0].I, mode[0].off.p, st);
+            launch_dup_check(soa.p, N, nnz, mode[0].perm.p, stat.p, st);
+            {
+                DeviceStatus s = read_status();
+                if (s.bits & kStatDup)
+                    throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
+            }
+            for (int n = N - 1; n >= 1; --n) {
                 ModeLayout &L = mode[n];
-                L.I = dims[n];
-                L.perm.alloc(nnz, st);
-                L.off.alloc(L.I + 1, st);
-                launch_iota(L.perm.p, nnz, st);
-                for (int t = N - 1; t >= 0; --t) {  // least significant mode first
-                    const int m = (n + t) % N;
-                    launch_gather_keys(soa.p + (size_t)m * nnz, L.perm.p, keys.p, nnz, st);
-                    radix_sort_pairs(keys.p, L.perm.p, nnz, ceil_log2_u64((uint64_t)dims[m]), ws,
-                                     st);
-                }
+                const ModeLayout &next = mode[(n + 1) % N];
+                TFS_CUDA(cudaMemcpyAsync(L.perm.p, next.perm.p, (size_t)nnz * sizeof(int32_t),
+                                         cudaMemcpyDeviceToDevice, st));
+                sorted_by(L, n);
                 launch_offsets(keys.p, nnz, L.I, L.off.p, st);
-                if (n == 0) {
-                    launch_dup_check(soa.p, N, nnz, L.perm.p, stat.p, st);
-                    DeviceStatus s = read_status();
-                    if (s.bits & kStatDup)
-                        throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
-                }
             }
             // degree ranks: slices are stored with each mode's rows in decreasing order of
             // their entry counts (equal counts by row id); one host thread per mode

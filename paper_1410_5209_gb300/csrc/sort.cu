@@ -3,9 +3,11 @@
 //
 // Each mode n gets the permutation of the observed entries that orders them
 // lexicographically by (i_n, i_{n+1}, ..., i_N, i_1, ..., i_{n-1}); with no duplicate
-// coordinates this order is total, so the permutation is unique.  It is produced by a
-// stable least-significant-digit radix sort (8-bit digits) over the modes from the
-// least to the most significant, with the entry permutation as payload.  Every pass
+// coordinates this order is total, so the permutation is unique.  The first mode's is
+// produced by stable least-significant-digit radix sorts (8-bit digits) over the modes
+// from the least to the most significant, with the entry permutation as payload; every
+// other mode's by one stable sort by its own index of the following mode's permutation
+// (the layout build in api.cu).  Every pass
 // is "count per tile -> one exclusive scan over (digit, tile) -> stable scatter", the
 // stable in-tile rank coming from warp match/popc over 32 consecutive keys at a time.
 #include "common.cuh"
