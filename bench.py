@@ -340,7 +340,7 @@ def fiveway(args, rank, world):
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     s = torch.cuda.Stream()
-    used0, _ = tf.pool_usage(reset_high=True)
+    used0, _, _ = tf.pool_usage(reset_high=True)
     t0 = time.perf_counter()
     f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
                          stream=s.cuda_stream, device_input=True)
@@ -359,7 +359,7 @@ def fiveway(args, rank, world):
         rows[str(C)] = {"ms_per_sweep": ms, "nnz_rank_per_s": p.nnz * K / (ms / 1e3),
                         "train_rmse_after": rmse,
                         "pass_path": f.counters()["pass_path"]}
-    _, high = tf.pool_usage()
+    _, high, _ = tf.pool_usage()
     est = max(tf.estimate_bytes(p.dims, p.nnz, K, C, tf.F32, device_input=True) for C in Cs)
     print(json.dumps({"metric": "nnz*rank updates/s per SALS sweep (5-way)", "unit": UNIT,
                       "nnz": p.nnz, "dims": list(dims), "K": K, "lam": lam, "dtype": "f32",

@@ -373,10 +373,17 @@ tf_status tf_plan_mode(const int64_t *off, int64_t I, int P, int64_t cap,
 tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int C_max,
                             tf_dtype dtype, uint32_t flags, int num_sms, int64_t *bytes);
 
-/* Bytes in use, and the high-water mark, of the current device's default stream-ordered
- * memory pool, which holds every context's device memory; reset_high != 0 restarts the
- * high-water mark at the current use.  Any output pointer may be NULL. */
-tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int reset_high);
+/* The library's stream-ordered memory pool on the current device, which holds every
+ * context's device memory: bytes in use, their high-water mark, and bytes the pool holds
+ * (in use, or freed by destroyed contexts and kept for later ones); reset_high != 0
+ * restarts the high-water mark at the current use.  Any output pointer may be NULL.  The
+ * pool keeps freed memory (creating a context after destroying one maps nothing new) and
+ * never makes one context's stream wait for another's to reuse a block. */
+tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int64_t *reserved, int reset_high);
+
+/* Returns the pool's unused memory to the device, keeping at most keep_bytes held
+ * (synchronises the device first). */
+tf_status tf_pool_trim(int64_t keep_bytes);
 
 /* Library version string. */
 const char *tf_version(void);

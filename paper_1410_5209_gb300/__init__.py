@@ -96,7 +96,8 @@ def load():
         "tf_graph_info": [P, P, P],
         "tf_get_stream": [P, P],
         "tf_estimate_bytes": [P, i32, i64, i32, i32, i32, u32, i32, P],
-        "tf_pool_usage": [P, P, i32],
+        "tf_pool_usage": [P, P, P, i32],
+        "tf_pool_trim": [i64],
         "tf_server_create": [P, P, P],
         "tf_server_destroy": [P],
         "tf_server_last_error": [P],
@@ -442,12 +443,20 @@ def estimate_bytes(dims, nnz, K, C_max, dtype=F32, device_input=False, num_sms=0
 
 
 def pool_usage(reset_high=False):
-    """(bytes in use, high-water mark) of the device's stream-ordered pool."""
-    used, high = ctypes.c_int64(), ctypes.c_int64()
-    st = load().tf_pool_usage(ctypes.byref(used), ctypes.byref(high), 1 if reset_high else 0)
+    """(bytes in use, high-water mark, bytes held) of the library's device memory pool."""
+    used, high, held = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = load().tf_pool_usage(ctypes.byref(used), ctypes.byref(high), ctypes.byref(held),
+                              1 if reset_high else 0)
     if st != OK:
         raise TFError(st, "tf_pool_usage failed")
-    return used.value, high.value
+    return used.value, high.value, held.value
+
+
+def pool_trim(keep_bytes=0):
+    """Return the pool's unused device memory, keeping at most keep_bytes."""
+    st = load().tf_pool_trim(int(keep_bytes))
+    if st != OK:
+        raise TFError(st, "tf_pool_trim failed")
 
 
 # ---------------------------------------------------------------- serving (tf_server.h)

@@ -22,7 +22,7 @@
 namespace tfs {
 
 // Device buffer owned by a context, allocated and freed in the order of the context's
-// stream (cudaMallocAsync / cudaFreeAsync).  cudaFree waits for every stream of the device,
+// stream (from the library's pool / cudaFreeAsync).  cudaFree waits for every stream of the device,
 // so a context built or destroyed beside running work (a serving process admitting and
 // retiring jobs) would stall all other work on the GPU; stream-ordered calls wait for
 // nothing but the context's own stream.  `s` is the stream the buffer is freed on; it
@@ -45,7 +45,7 @@ struct Buf {
         reset();
         if (count == 0) count = 1;
         s = st;
-        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
+        cudaError_t e = pool_alloc(reinterpret_cast<void **>(&p), count * sizeof(T), st);
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -102,6 +102,37 @@ class PinnedCache {
 PinnedCache &pinned_cache() {
     static PinnedCache c;
     return c;
+}
+
+cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pools[dev] = nullptr;
+        return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    cudaGetLastError();
+    pools[dev] = pool;
+    return pool;
 }
 
 struct ModeLayout {
@@ -1762,27 +1793,36 @@ tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int 
     return TF_OK;
 }
 
-tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int reset_high) {
-    int dev = 0;
-    cudaMemPool_t pool;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return TF_ECUDA;
-    }
-    uint64_t a = 0, b = 0;
+tf_status tf_pool_usage(int64_t *used, int64_t *used_high, int64_t *reserved, int reset_high) {
+    cudaMemPool_t pool = tfs::library_pool();
+    if (!pool) return TF_ECUDA;
+    uint64_t a = 0, b = 0, c = 0;
     if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &a) != cudaSuccess ||
-        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &b) != cudaSuccess) {
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &b) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &c) != cudaSuccess) {
         cudaGetLastError();
         return TF_ECUDA;
     }
     if (used) *used = (int64_t)a;
     if (used_high) *used_high = (int64_t)b;
+    if (reserved) *reserved = (int64_t)c;
     if (reset_high) {
         uint64_t zero = 0;
         if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) {
             cudaGetLastError();
             return TF_ECUDA;
         }
+    }
+    return TF_OK;
+}
+
+tf_status tf_pool_trim(int64_t keep_bytes) {
+    if (keep_bytes < 0) return TF_EINVAL;
+    cudaMemPool_t pool = tfs::library_pool();
+    if (!pool) return TF_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, (size_t)keep_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TF_ECUDA;
     }
     return TF_OK;
 }

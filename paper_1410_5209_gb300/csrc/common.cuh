@@ -97,6 +97,19 @@ cudaError_t raise_smem_limit(const void *kern, int bytes);
 
 size_t sort_workspace_bytes(int64_t n);  // device bytes SortWorkspace::reserve(n) holds
 
+// The library's stream-ordered memory pool on the current device, created on first use.
+// Freed blocks stay in it for later contexts (no unmapping when a context is destroyed,
+// none of the mapping cost when the next one is created) until tf_pool_trim; the pool
+// inserts no cross-stream dependencies to reuse a block (a context never waits for
+// another context's stream).  nullptr when no pool can be created.
+cudaMemPool_t library_pool();
+
+// Stream-ordered allocation from library_pool() (the device's default pool as a fallback).
+inline cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = library_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+
 void radix_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int bits, SortWorkspace &ws,
                       cudaStream_t st);
 

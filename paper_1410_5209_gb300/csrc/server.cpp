@@ -120,7 +120,11 @@ void tf_server::admit_locked() {
     for (auto &kv : jobs)
         if (kv.second->info.state == TF_JOB_RUNNING && !kv.second->first_sweep_done)
             pending += kv.second->info.bytes;
-    const int64_t room = (int64_t)free_b - cfg.hbm_reserve - pending;
+    // memory the library's pool holds but no context uses is free for new jobs too
+    int64_t used = 0, held = 0;
+    if (tf_pool_usage(&used, nullptr, &held, 0) != TF_OK) used = held = 0;
+    const int64_t room = (int64_t)free_b + std::max<int64_t>(0, held - used) - cfg.hbm_reserve -
+                         pending;
     const int64_t budget_left = cfg.hbm_budget > 0 ? cfg.hbm_budget - admitted_bytes : -1;
     const int n = (int)queue.size();
     std::vector<int64_t> need(n);

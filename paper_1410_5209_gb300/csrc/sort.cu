@@ -262,7 +262,7 @@ void SortWorkspace::reserve(int64_t n, cudaStream_t st) {
         if (p) cudaFreeAsync(p, st);
         p = nullptr;
         cap = 0;
-        TFS_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&p), want * sizeof(*p), st));
+        TFS_CUDA(pool_alloc(reinterpret_cast<void **>(&p), want * sizeof(*p), st));
         cap = want;
     };
     size_t cap_vals = cap_items;

@@ -48,13 +48,13 @@ def orders(p, C, sweeps):
 def test_estimate_bounds_the_pool_high_water():
     p = synth.small(320, (3000, 2000, 100), 400_000, 4, 48)
     c, x = p.numpy()
-    used0, _ = tf.pool_usage(reset_high=True)
+    used0, _, _ = tf.pool_usage(reset_high=True)
     f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
     for C, s in ((10, 0), (40, 1)):
         f.sweep(C, 0.1, 1, p.column_order(s, C))
     f.loss(0.1)
     f.sync()
-    _, high = tf.pool_usage()
+    _, high, _ = tf.pool_usage()
     est = tf.estimate_bytes(p.dims, p.nnz, p.K, 40, tf.F32)
     grew = high - used0
     f.close()
