@@ -142,3 +142,7 @@ def test_lpt_splits_heavy_rows_and_balances(lib):
 def test_plan_handles_empty_mode(lib):
     items, n_slots, bin_ptr = tf.plan_mode(np.zeros(4, np.int64), 8, 0, tf.SCHED_LPT)
     assert len(items) == 3 and np.all(items["len"] == 0) and n_slots == 3
+
+
+def test_pool_trim_rejects_negative_without_gpu(lib):
+    assert lib.tf_pool_trim(-1) == tf.EINVAL

@@ -144,3 +144,26 @@ def test_refusals_and_shutdown():
     info = srv.job_info(ids[-1])
     assert info["state"] in (tf.JOB_QUEUED, tf.JOB_RUNNING, tf.JOB_DONE)
     srv.close()
+
+
+def test_pool_keeps_freed_memory_until_trimmed():
+    """A destroyed context's memory stays in the library's pool (the next context of the
+    same size takes it without growing the pool); tf_pool_trim hands it back."""
+    p = synth.small(350, (3000, 2000, 100), 300_000, 4, 16)
+    c, x = p.numpy()
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
+    f.sweep(4, 0.1, 1)
+    f.sync()
+    used1, _, held1 = tf.pool_usage()
+    f.close()
+    used2, _, held2 = tf.pool_usage()
+    assert used2 < used1 and held2 >= held1 - (1 << 21)
+    g = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
+    g.sweep(4, 0.1, 1)
+    g.sync()
+    _, _, held3 = tf.pool_usage()
+    assert held3 <= held2 + (8 << 20)   # reused, not grown (up to pool rounding)
+    g.close()
+    tf.pool_trim(0)
+    used4, _, held4 = tf.pool_usage()
+    assert held4 <= used4 + (2 << 20)
