@@ -156,6 +156,8 @@ def test_pool_keeps_freed_memory_until_trimmed():
     f.sync()
     used1, _, held1 = tf.pool_usage()
     f.close()
+    import torch
+    torch.cuda.synchronize()   # the frees run in stream order
     used2, _, held2 = tf.pool_usage()
     assert used2 < used1 and held2 >= held1 - (1 << 21)
     g = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F32)
