@@ -1,13 +1,15 @@
-// Serving loop: a scheduler thread that admits factorisation jobs against free device
-// memory and batches fold-in requests continuously, built on the public C ABI of the
-// library (every step of the method runs in the library's kernels).
+// Serving loop: threads that admit factorisation jobs against free device memory and
+// batch fold-in requests continuously, built on the public C ABI of the library (every
+// step of the method runs in the library's kernels).
 //
-// Threads: the scheduler thread owns the model context and runs the fold-in batches on
-// a stream of the device's highest priority; each admitted job has a worker thread that
+// Threads: an admission thread starts jobs; a batching thread owns the model context and
+// runs the fold-in batches on a stream of the device's highest priority (neither holds
+// the lock while it calls into CUDA); each admitted job has a worker thread that
 // creates the job's context on its own stream of the lowest priority, runs its sweeps
 // and its loss, and leaves the context for the caller to read and release.  All shared
-// state sits behind one mutex; one condition variable wakes the scheduler (new work,
-// freed memory), another the callers waiting for a finished job or fold-in.
+// state sits behind one mutex; condition variables wake the admission thread (new jobs,
+// freed memory), the batching thread (new fold-ins) and the callers waiting for a
+// finished job or fold-in.
 #include <string.h>
 
 #include <algorithm>
@@ -76,7 +78,7 @@ struct tf_server {
     Clock::time_point t0;
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_fold, cv_done;
     bool stop = false;
     std::string err;
 
@@ -87,12 +89,13 @@ struct tf_server {
     std::map<int64_t, std::shared_ptr<Foldin>> foldins; // every fold-in not yet collected
     int64_t running = 0, admitted_bytes = 0;
     tf_server_stats st{};
-    std::thread sched;
+    std::thread sched, batcher;
 
     double now() const { return secs(t0, Clock::now()); }
     void run_scheduler();
+    void run_batcher();
     void run_job(std::shared_ptr<Job> j);
-    void admit_locked();
+    void admit_locked(int64_t free_b, int64_t pool_unused);
     void batch_foldins(std::unique_lock<std::mutex> &lk);
 };
 
@@ -105,26 +108,19 @@ size_t elem_bytes(tf_dtype t) { return t == TF_F64 ? 8 : 4; }
 // Admission: scan the queue in arrival order and start every job that fits (first fit);
 // a job that does not fit while a later one starts is passed once more; a job passed
 // max_bypass times blocks everything behind it until it fits.
-void tf_server::admit_locked() {
+// free_b: the device's free memory; pool_unused: memory the library's pool holds but no
+// context uses (free for new jobs too) -- both read by the caller without the lock.
+void tf_server::admit_locked(int64_t free_b, int64_t pool_unused) {
     if (queue.empty()) return;
     const int slots = (int)std::max<int64_t>(0, cfg.max_running - running);
     if (slots == 0) return;
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
     // memory that admitted jobs have yet to allocate: a job's whole estimate until its
     // first sweep has run
     int64_t pending = 0;
     for (auto &kv : jobs)
         if (kv.second->info.state == TF_JOB_RUNNING && !kv.second->first_sweep_done)
             pending += kv.second->info.bytes;
-    // memory the library's pool holds but no context uses is free for new jobs too
-    int64_t used = 0, held = 0;
-    if (tf_pool_usage(&used, nullptr, &held, 0) != TF_OK) used = held = 0;
-    const int64_t room = (int64_t)free_b + std::max<int64_t>(0, held - used) - cfg.hbm_reserve -
-                         pending;
+    const int64_t room = free_b + pool_unused - cfg.hbm_reserve - pending;
     const int64_t budget_left = cfg.hbm_budget > 0 ? cfg.hbm_budget - admitted_bytes : -1;
     const int n = (int)queue.size();
     std::vector<int64_t> need(n);
@@ -262,18 +258,39 @@ void tf_server::batch_foldins(std::unique_lock<std::mutex> &lk) {
     cv_done.notify_all();
 }
 
+// Admission thread.  Device-memory queries can wait for the driver while other threads
+// allocate; they run without the lock, so submissions and fold-in batches never wait
+// for them.
 void tf_server::run_scheduler() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
-        admit_locked();
+        if (!queue.empty() && running < cfg.max_running) {
+            lk.unlock();
+            size_t free_b = 0, total_b = 0;
+            int64_t used = 0, held = 0;
+            const bool ok = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess;
+            if (!ok) cudaGetLastError();
+            if (tf_pool_usage(&used, nullptr, &held, 0) != TF_OK) used = held = 0;
+            lk.lock();
+            if (ok && !stop) admit_locked((int64_t)free_b, std::max<int64_t>(0, held - used));
+        }
+        // wake for new jobs or freed memory; poll now and then, since device memory can
+        // also be freed by other users of the GPU
+        cv_work.wait_for(lk, std::chrono::milliseconds(50));
+    }
+}
+
+// Fold-in thread: a batch whenever requests wait (continuous batching).
+void tf_server::run_batcher() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
         if (!fq.empty()) {
             batch_foldins(lk);
             continue;
         }
-        // wake for new work or freed memory; poll now and then, since device memory can
-        // also be freed by other users of the GPU
-        cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        cv_fold.wait(lk, [&] { return stop || !fq.empty(); });
     }
 }
 
@@ -352,6 +369,7 @@ tf_status tf_server_create(const tf_server_config *cfg, tf_ctx *model, tf_server
         s->model_dtype = dt;
     }
     s->sched = std::thread(&tf_server::run_scheduler, s.get());
+    s->batcher = std::thread(&tf_server::run_batcher, s.get());
     *out = s.release();
     return TF_OK;
 }
@@ -376,9 +394,11 @@ void tf_server_destroy(tf_server *srv) {
         srv->fq.clear();
         for (auto &kv : srv->jobs) all.push_back(kv.second);
         srv->cv_work.notify_all();
+        srv->cv_fold.notify_all();
         srv->cv_done.notify_all();
     }
     srv->sched.join();
+    srv->batcher.join();
     for (auto &j : all) {
         if (j->worker.joinable()) j->worker.join();
         tf_destroy(j->ctx);
@@ -525,7 +545,7 @@ tf_status tf_server_submit_foldin(tf_server *srv, int mode, const int32_t *other
     srv->foldins[q->id] = q;
     srv->fq.push_back(q);
     *req_id = q->id;
-    srv->cv_work.notify_all();
+    srv->cv_fold.notify_one();
     return TF_OK;
 }
 
