@@ -73,7 +73,11 @@ std::vector<int64_t> rows_by_length(const int64_t *len, int64_t I) {
 }
 
 // LPT: every job, longest first, to the bin with the least load (lowest index on ties).
-// A min-heap of packed keys (load in the high bits, bin in the low 21 bits).
+// A job's load is its entries plus kItemCost: every item has a fixed cost in the mode
+// pass (its first step, its partial write), so the many short or empty rows of a tensor
+// spread over the bins instead of piling into whichever bin is least loaded last.  A
+// min-heap of packed keys (load in the high bits, bin in the low 21 bits).
+constexpr int64_t kItemCost = 32;
 void lpt_bins(const std::vector<int64_t> &job_len, const std::vector<int64_t> &order, int M,
               std::vector<int32_t> &bin_of_job) {
     std::vector<uint64_t> heap((size_t)M);
@@ -96,7 +100,7 @@ void lpt_bins(const std::vector<int64_t> &job_len, const std::vector<int64_t> &o
         const uint64_t top = heap[0];
         const int32_t m = (int32_t)(top & ((1u << 21) - 1));
         bin_of_job[j] = m;
-        heap[0] = top + ((uint64_t)job_len[j] << 21);  // load grows, bin stays
+        heap[0] = top + ((uint64_t)(job_len[j] + kItemCost) << 21);  // load grows, bin stays
         sift_down(0);
     }
 }
