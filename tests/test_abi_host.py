@@ -146,3 +146,22 @@ def test_plan_handles_empty_mode(lib):
 
 def test_pool_trim_rejects_negative_without_gpu(lib):
     assert lib.tf_pool_trim(-1) == tf.EINVAL
+
+
+def test_lpt_spreads_short_and_empty_rows(lib):
+    """Many empty and one-entry rows beside a few long ones (a batch of small tensors):
+    LPT balances the items per bin as well as the entries, so no warp is left with
+    thousands of tiny items after the others finish."""
+    rng = np.random.default_rng(5)
+    cnt = np.concatenate([np.zeros(20_000, np.int64), np.ones(20_000, np.int64),
+                          rng.integers(2, 200, 20_000), rng.integers(1_000, 50_000, 200)])
+    rng.shuffle(cnt)
+    off = np.zeros(len(cnt) + 1, np.int64)
+    off[1:] = np.cumsum(cnt)
+    P = 2048
+    items, n_slots, bin_ptr = tf.plan_mode(off, P)
+    per_bin = np.diff(bin_ptr)
+    assert per_bin.max() <= 4 * per_bin.mean() + 8, (per_bin.max(), per_bin.mean())
+    loads = np.zeros(P)
+    np.add.at(loads, items["bin"], items["len"])
+    assert loads.max() <= 1.1 * loads.mean() + 100
