@@ -19,6 +19,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -145,7 +146,18 @@ void tf_server::admit_locked(int64_t free_b, int64_t pool_unused) {
         ++running;
         st.running_peak = std::max(st.running_peak, running);
         st.bytes_admitted_peak = std::max(st.bytes_admitted_peak, admitted_bytes);
-        j->worker = std::thread(&tf_server::run_job, this, j);
+        try {
+            j->worker = std::thread(&tf_server::run_job, this, j);
+        } catch (...) {  // no thread for it: the job fails, its admission is undone
+            admitted_bytes -= j->info.bytes;
+            --running;
+            j->info.state = TF_JOB_FAILED;
+            j->info.status = TF_ENOMEM;
+            j->info.started_s = -1;
+            j->info.finished_s = now();
+            ++st.jobs_failed;
+            cv_done.notify_all();
+        }
     }
     queue.swap(rest);
 }
@@ -227,25 +239,34 @@ void tf_server::batch_foldins(std::unique_lock<std::mutex> &lk) {
     lk.unlock();
     const int n = (int)b.size();
     const size_t eb = elem_bytes(model_dtype);
-    std::vector<int64_t> off((size_t)n + 1, 0);
-    for (int r = 0; r < n; ++r) off[r + 1] = off[r] + b[r]->m;
-    std::vector<int32_t> other((size_t)std::max<int64_t>(off[n], 1) * std::max(model_N - 1, 1));
-    std::vector<char> vals((size_t)std::max<int64_t>(off[n], 1) * eb);
-    for (int r = 0; r < n; ++r) {
-        memcpy(other.data() + off[r] * (model_N - 1), b[r]->other.data(),
-               b[r]->other.size() * sizeof(int32_t));
-        memcpy(vals.data() + off[r] * eb, b[r]->vals.data(), b[r]->vals.size());
+    std::vector<char> rows;
+    std::vector<int32_t> status;
+    tf_status s = TF_OK;
+    try {  // host staging of the batch; a failed allocation fails the batch
+        std::vector<int64_t> off((size_t)n + 1, 0);
+        for (int r = 0; r < n; ++r) off[r + 1] = off[r] + b[r]->m;
+        std::vector<int32_t> other((size_t)std::max<int64_t>(off[n], 1) *
+                                   std::max(model_N - 1, 1));
+        std::vector<char> vals((size_t)std::max<int64_t>(off[n], 1) * eb);
+        for (int r = 0; r < n; ++r) {
+            memcpy(other.data() + off[r] * (model_N - 1), b[r]->other.data(),
+                   b[r]->other.size() * sizeof(int32_t));
+            memcpy(vals.data() + off[r] * eb, b[r]->vals.data(), b[r]->vals.size());
+        }
+        rows.assign((size_t)n * model_K * eb, 0);
+        status.assign((size_t)n, 0);
+        s = tf_foldin_batch(model, mode, n, off.data(), other.data(), vals.data(), lam,
+                            rows.data(), status.data());
+    } catch (...) {
+        s = TF_ENOMEM;
     }
-    std::vector<char> rows((size_t)n * model_K * eb, 0);
-    std::vector<int32_t> status((size_t)n, 0);
-    tf_status s = tf_foldin_batch(model, mode, n, off.data(), other.data(), vals.data(), lam,
-                                  rows.data(), status.data());
     const auto t = Clock::now();
     lk.lock();
     for (int r = 0; r < n; ++r) {
         auto &q = *b[r];
-        q.row.assign(rows.begin() + (size_t)r * model_K * eb,
-                     rows.begin() + (size_t)(r + 1) * model_K * eb);
+        if (s == TF_OK)
+            q.row.assign(rows.begin() + (size_t)r * model_K * eb,
+                         rows.begin() + (size_t)(r + 1) * model_K * eb);
         q.status = s == TF_OK ? status[r] : 16 + (int32_t)s;
         q.done = true;
         q.done_at = t;
@@ -368,8 +389,25 @@ tf_status tf_server_create(const tf_server_config *cfg, tf_ctx *model, tf_server
         s->model_K = K;
         s->model_dtype = dt;
     }
-    s->sched = std::thread(&tf_server::run_scheduler, s.get());
-    s->batcher = std::thread(&tf_server::run_batcher, s.get());
+    try {
+        s->sched = std::thread(&tf_server::run_scheduler, s.get());
+        s->batcher = std::thread(&tf_server::run_batcher, s.get());
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        s->cv_fold.notify_all();
+        if (s->sched.joinable()) s->sched.join();
+        if (s->batcher.joinable()) s->batcher.join();
+        if (s->model) {
+            tf_set_stream(s->model, s->model_old_stream);
+            cudaStreamDestroy(s->hi);
+        }
+        g_server_create_err = "could not start the server's threads";
+        return TF_ENOMEM;
+    }
     *out = s.release();
     return TF_OK;
 }
@@ -442,13 +480,19 @@ tf_status tf_server_submit_job(tf_server *srv, const tf_job_desc *d, int64_t *jo
                 seen[c] = 1;
             }
         }
-    auto j = std::make_shared<Job>();
-    j->d = *d;
-    j->dims.assign(d->dims, d->dims + d->N);
-    j->coords.assign(d->coords, d->coords + (size_t)d->nnz * d->N);
-    const char *v = static_cast<const char *>(d->values);
-    j->values.assign(v, v + (size_t)d->nnz * elem_bytes(d->dtype));
-    if (d->col_orders) j->orders.assign(d->col_orders, d->col_orders + (size_t)d->sweeps * d->K);
+    std::shared_ptr<Job> j;
+    try {  // the host copy of the inputs
+        j = std::make_shared<Job>();
+        j->d = *d;
+        j->dims.assign(d->dims, d->dims + d->N);
+        j->coords.assign(d->coords, d->coords + (size_t)d->nnz * d->N);
+        const char *v = static_cast<const char *>(d->values);
+        j->values.assign(v, v + (size_t)d->nnz * elem_bytes(d->dtype));
+        if (d->col_orders)
+            j->orders.assign(d->col_orders, d->col_orders + (size_t)d->sweeps * d->K);
+    } catch (...) {
+        return fail(TF_ENOMEM, "host copy of the job's inputs failed");
+    }
     j->d.coords = nullptr;
     j->d.values = nullptr;
     j->d.dims = nullptr;
@@ -531,13 +575,18 @@ tf_status tf_server_submit_foldin(tf_server *srv, int mode, const int32_t *other
                                   const void *vals, int64_t m, double lambda, int64_t *req_id) {
     if (!srv || !req_id || m < 0 || (m > 0 && (!other || !vals))) return TF_EINVAL;
     if (!srv->model || mode < 0 || mode >= srv->model_N || !(lambda >= 0.0)) return TF_EINVAL;
-    auto q = std::make_shared<Foldin>();
-    q->mode = mode;
-    q->lambda = lambda;
-    q->m = m;
-    q->other.assign(other, other + (size_t)m * (srv->model_N - 1));
-    const char *v = static_cast<const char *>(vals);
-    q->vals.assign(v, v + (size_t)m * elem_bytes(srv->model_dtype));
+    std::shared_ptr<Foldin> q;
+    try {  // the host copy of the request
+        q = std::make_shared<Foldin>();
+        q->mode = mode;
+        q->lambda = lambda;
+        q->m = m;
+        q->other.assign(other, other + (size_t)m * (srv->model_N - 1));
+        const char *v = static_cast<const char *>(vals);
+        q->vals.assign(v, v + (size_t)m * elem_bytes(srv->model_dtype));
+    } catch (...) {
+        return TF_ENOMEM;
+    }
     q->submitted = Clock::now();
     std::lock_guard<std::mutex> g(srv->mu);
     if (srv->stop) return TF_EBUSY;
