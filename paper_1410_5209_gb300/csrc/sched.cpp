@@ -80,6 +80,7 @@ std::vector<int64_t> rows_by_length(const int64_t *len, int64_t I) {
 constexpr int64_t kItemCost = 32;
 void lpt_bins(const std::vector<int64_t> &job_len, const std::vector<int64_t> &order, int M,
               std::vector<int32_t> &bin_of_job) {
+    // a 4-ary heap: half the levels of a binary one, the four children in one cache line
     std::vector<uint64_t> heap((size_t)M);
     for (int m = 0; m < M; ++m) heap[m] = (uint64_t)m;  // already a min-heap
     bin_of_job.assign(job_len.size(), -1);
@@ -87,9 +88,12 @@ void lpt_bins(const std::vector<int64_t> &job_len, const std::vector<int64_t> &o
         const size_t n = heap.size();
         const uint64_t v = heap[i];
         for (;;) {
-            size_t c = 2 * i + 1;
-            if (c >= n) break;
-            if (c + 1 < n && heap[c + 1] < heap[c]) ++c;
+            const size_t c0 = 4 * i + 1;
+            if (c0 >= n) break;
+            size_t c = c0;
+            const size_t cend = std::min(c0 + 4, n);
+            for (size_t k = c0 + 1; k < cend; ++k)
+                if (heap[k] < heap[c]) c = k;
             if (heap[c] >= v) break;
             heap[i] = heap[c];
             i = c;
@@ -208,16 +212,19 @@ tf_status plan_mode(const int64_t *off, int64_t I, int P, int64_t cap, tf_sched_
                 const int64_t cap_rows = policy == TF_SCHED_GREEDY ? (I + P - 1) / P : -1;
                 greedy_bins(len, order, P, cap_rows, totals, bin);
             }
-            // bins receive jobs longest first: keep that order inside each bin
-            std::vector<tf_item> sorted;
-            sorted.reserve(jobs.size());
+            // bins receive jobs longest first: keep that order inside each bin (grouped
+            // by bin in the same pass)
+            bin_ptr.assign((size_t)P + 1, 0);
+            for (size_t j = 0; j < jobs.size(); ++j) bin_ptr[bin[j] + 1] += 1;
+            for (int p = 0; p < P; ++p) bin_ptr[p + 1] += bin_ptr[p];
+            std::vector<int64_t> fill(bin_ptr.begin(), bin_ptr.end() - 1);
+            items.resize(jobs.size());
             for (int64_t j : order) {
                 tf_item it = jobs[j];
                 it.bin = bin[j];
-                sorted.push_back(it);
+                items[(size_t)fill[it.bin]++] = it;
             }
-            jobs.swap(sorted);
-            break;
+            return TF_OK;
         }
         case TF_SCHED_SEQ:
             for (auto &it : jobs) it.bin = (int32_t)(((int64_t)it.row * P) / std::max<int64_t>(I, 1));
