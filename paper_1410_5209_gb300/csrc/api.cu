@@ -656,7 +656,7 @@ struct Impl : CtxBase {
         if (T_in < 1) throw ApiError{TF_EINVAL, "T_in must be >= 1"};
         if (!(lambda >= 0.0) || !isfinite(lambda)) throw ApiError{TF_EINVAL, "lambda must be >= 0"};
         const int CM = pick_cm(C);
-        if (CM == 0) throw ApiError{TF_EINVAL, "C >= 128 is not supported by this build"};
+        if (CM == 0) throw ApiError{TF_EINVAL, "C >= 128 is not supported (the widest Gram tile is 128 columns)"};
         const bool wide = CM > 16;
         int64_t launches0 = launches;
         if (dirty) {
