@@ -46,6 +46,7 @@ struct Job {
     tf_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     std::thread worker;
+    std::mutex use;  // calls on ctx after the worker is done (factors, release)
 };
 
 struct Foldin {
@@ -439,8 +440,11 @@ void tf_server_destroy(tf_server *srv) {
     srv->batcher.join();
     for (auto &j : all) {
         if (j->worker.joinable()) j->worker.join();
+        std::lock_guard<std::mutex> u(j->use);
         tf_destroy(j->ctx);
+        j->ctx = nullptr;
         if (j->stream) cudaStreamDestroy(j->stream);
+        j->stream = nullptr;
     }
     if (srv->model) {
         tf_set_stream(srv->model, srv->model_old_stream);
@@ -538,15 +542,17 @@ tf_status tf_server_wait_job(tf_server *srv, int64_t id, double timeout_s, tf_jo
 
 tf_status tf_server_job_factors(tf_server *srv, int64_t id, int n, void *host_A) {
     if (!srv || !host_A) return TF_EINVAL;
-    tf_ctx *ctx = nullptr;
+    std::shared_ptr<Job> j;
     {
         std::lock_guard<std::mutex> g(srv->mu);
         auto it = srv->jobs.find(id);
         if (it == srv->jobs.end()) return TF_EINVAL;
         if (it->second->info.state != TF_JOB_DONE) return TF_EBUSY;
-        ctx = it->second->ctx;
+        j = it->second;
     }
-    return tf_get_factors(ctx, n, host_A);
+    std::lock_guard<std::mutex> u(j->use);  // a concurrent release waits for this copy
+    if (!j->ctx) return TF_EINVAL;           // released in the meantime
+    return tf_get_factors(j->ctx, n, host_A);
 }
 
 tf_status tf_server_release_job(tf_server *srv, int64_t id) {
@@ -561,10 +567,13 @@ tf_status tf_server_release_job(tf_server *srv, int64_t id) {
         srv->jobs.erase(it);
     }
     if (j->worker.joinable()) j->worker.join();
-    tf_destroy(j->ctx);  // stream-ordered frees: no wait on other streams
-    j->ctx = nullptr;
-    if (j->stream) cudaStreamDestroy(j->stream);
-    j->stream = nullptr;
+    {
+        std::lock_guard<std::mutex> u(j->use);
+        tf_destroy(j->ctx);  // stream-ordered frees: no wait on other streams
+        j->ctx = nullptr;
+        if (j->stream) cudaStreamDestroy(j->stream);
+        j->stream = nullptr;
+    }
     std::lock_guard<std::mutex> g(srv->mu);
     if (j->info.started_s >= 0) srv->admitted_bytes -= j->info.bytes;
     srv->cv_work.notify_all();
