@@ -3,9 +3,11 @@
  *
  *   - Factorisation jobs (a tensor, K, C, lambda, T_in and a number of outer sweeps of
  *     Algorithm 1).  A job is admitted when its device footprint (tf_estimate_bytes) fits
- *     the free device memory, and the job budget when one is set; each admitted job runs
- *     in its own context on its own low-priority stream from its own host thread, so the
- *     kernels of several jobs overlap on the device.  Its factors and residuals stay on the
+ *     the free device memory (with what the library's pool holds unused, less the reserve
+ *     and the footprints of admitted jobs still building their layout), and the job budget
+ *     when one is set; each admitted job runs in its own context on its own low-priority
+ *     stream from its own host thread, so the kernels of several jobs overlap on the
+ *     device.  Its factors and residuals stay on the
  *     device until the caller releases it.
  *   - Fold-in requests: a new slice of one mode solved against the frozen factors of a
  *     model context (the ALS row update of Eq. 2 for that slice).  Requests that arrive
@@ -17,7 +19,8 @@
  * share no device state), and a fold-in gives the row it gives alone (a request's partial
  * Gram matrices are summed in its own fixed block order whatever batch it lands in).
  *
- * Threading: every tf_server_* call is thread-safe.  While a server exists, its model
+ * Threading: every tf_server_* call is thread-safe (a job's factors may be read while
+ * another thread releases it: the release waits).  While a server exists, its model
  * context belongs to the server: the caller makes no call on it until tf_server_destroy.
  * Inputs are copied at submission; the caller keeps ownership of every buffer.
  */
@@ -86,9 +89,9 @@ typedef struct {
     int64_t running_peak;        /* most jobs running at once */
 } tf_server_stats;
 
-/* Starts the scheduler thread on the current device.  model (may be NULL: no fold-ins)
- * is moved to a stream of the device's highest priority for the server's life and back
- * to its own stream by tf_server_destroy.  *out is NULL on failure. */
+/* Starts the admission and batching threads on the current device.  model (may be NULL:
+ * no fold-ins) is moved to a stream of the device's highest priority for the server's life
+ * and back to its own stream by tf_server_destroy.  *out is NULL on failure. */
 tf_status tf_server_create(const tf_server_config *cfg, tf_ctx *model, tf_server **out);
 
 /* Stops the server: queued jobs and fold-ins fail with TF_EBUSY, running jobs stop after
