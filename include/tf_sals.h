@@ -86,7 +86,9 @@ typedef struct {
  *   dims    [N] mode lengths I_n, 1 <= I_n <= 2^31 - 1 (host)
  *   N       1..8;  nnz 0..2^31 - 1;  K >= 1
  *   seed    seeds the default initialisation and the default column orders
- *   stream  cudaStream_t to order all work on (NULL = the legacy default stream)
+ *   stream  cudaStream_t to order all work on (NULL = the legacy default stream); it must
+ *           stay valid until tf_destroy, which frees the context's memory on it (or until
+ *           tf_set_stream moves the context to another stream)
  * Builds, on the device, the per-mode sorted layout (Omega_i^(n) of the table of
  * symbols, entries of a row in lexicographic order of the remaining coordinates taken
  * cyclically from mode n), with bit-exact row offsets; validates coordinates
