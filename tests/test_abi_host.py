@@ -26,6 +26,8 @@ def test_library_exports_every_declared_symbol(lib):
     assert len(names) >= 19
     for n in names:
         assert hasattr(lib, n), n
+        # and the binding declares its argument types (no default ctypes conversions)
+        assert getattr(lib, n).argtypes is not None, n
     assert tf.version().startswith("sals-gb300")
 
 
