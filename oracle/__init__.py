@@ -35,12 +35,34 @@ WEIGHTED = 1
 _lib = None
 
 
-def build(src: str = _SRC, out: str = _LIB_PATH) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math)."""
+_OMP_PATH = os.path.join(_BUILD, "libsals_oracle_omp.so")
+
+
+def build(src: str = _SRC, out: str = _LIB_PATH, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math); openmp=True also builds the
+    OpenMP variant used only as the benchmark's multi-core CPU baseline."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
+    if openmp:
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o",
+                        _OMP_PATH, src, "-lm"], check=True)
     return out
+
+
+_omp_lib = None
+
+
+def load_parallel():
+    """The OpenMP build of the same source (rows of a mode in parallel, each row's
+    arithmetic unchanged): for the multi-core CPU baseline only."""
+    global _omp_lib
+    if _omp_lib is None:
+        if (not os.path.exists(_OMP_PATH)
+                or os.path.getmtime(_OMP_PATH) < os.path.getmtime(_SRC)):
+            build(openmp=True)
+        _omp_lib = _bind(ctypes.CDLL(_OMP_PATH))
+    return _omp_lib
 
 
 def load(path: str | None = None):

@@ -14,6 +14,9 @@
  *   - Eq. (2)                 ALS row solve, used here for the fold-in of a new row
  *   - Algorithm 3             greedy row assignment (with the row cap and both tie-breaks)
  * No blocking, fusion or reordering is applied beyond what those statements give.
+ * Compiled plain (serial) for the tests; the CPU baseline of the benchmark also compiles
+ * it with -fopenmp, which runs the rows of a mode and the per-entry R-hat / R updates in
+ * parallel without changing any row's or entry's arithmetic.
  *
  * Readings where the paper is silent (each one is also listed in the design notes):
  *   - Omega_i^(n) is visited in lexicographic order of the coordinate tuple taken
@@ -236,18 +239,28 @@ int orc_sals_sweep(int N, const int64_t *dims, int64_t nnz, const int32_t *coord
         const int32_t *S = col_order + (int64_t)s * C;
         int Cs = (s == nsplit - 1) ? K - s * C : C;
         /* R-hat: r_hat = r + sum_{c in S} prod_n a (Algorithm 1, "compute R-hat") */
+#pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < nnz; ++e)
             rhat[e] = r[e] + model_part(N, coords + e * N, K, A, S, Cs);
-        /* T_in x (modes x rows), Eq. (4) */
+        /* T_in x (modes x rows), Eq. (4).  The rows of one mode are independent given the
+         * other modes (Section 3.3), so the OpenMP build of this file (the CPU baseline)
+         * updates them in parallel; each row's arithmetic is the serial one. */
         for (int t = 0; t < T_in; ++t)
-            for (int n = 0; n < N; ++n)
+            for (int n = 0; n < N; ++n) {
+                int64_t bad = 0;
+                int oom = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad) reduction(| : oom)
                 for (int64_t i = 0; i < dims[n]; ++i) {
                     int st = orc_row_update(N, n, i, coords, rhat, K, A, S, Cs, lambda, flags,
                                             off[n], perm[n]);
-                    if (st < 0) { free(rhat); return ORC_ENOMEM; }
-                    if (st == 1 && stats) stats[0] += 1;
+                    if (st < 0) oom = 1;
+                    if (st == 1) bad += 1;
                 }
+                if (oom) { free(rhat); return ORC_ENOMEM; }
+                if (stats) stats[0] += bad;
+            }
         /* Eq. (5): r = r_hat - sum_{c in S} prod_n a */
+#pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < nnz; ++e)
             r[e] = rhat[e] - model_part(N, coords + e * N, K, A, S, Cs);
     }
