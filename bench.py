@@ -137,24 +137,54 @@ def dist_env():
     return rank, world, local
 
 
-def run_oracle_sample(m_entries, seed, sweeps=1):
+def oracle_threads():
+    """Threads the OpenMP build of the oracle runs with on this host."""
+    return int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or (os.cpu_count() or 1)
+
+
+def run_oracle_sample(m_entries, seed, sweeps=1, parallel=False):
     """The FP64 oracle as it stands on the first m_entries of the workload (a prefix of
-    the same seeded draw), K = 100, C = 10: seconds per sweep and the update count."""
+    the same seeded draw), K = 100, C = 10: seconds per sweep and the update count.
+    parallel: its OpenMP build (rows of a mode in parallel on every host core)."""
     import numpy as np
     import oracle
     import synth
+    lib = oracle.load_parallel() if parallel else oracle.load()
     p = synth.skewed_3way(seed=seed, nnz=m_entries, device="cpu")
     c, x = p.numpy()
     t = oracle.Tensor(c, x.astype(np.float64), p.dims)
     A = [a.numpy() for a in p.init_factors()]
-    r = oracle.residual(t, A)
-    t.groups()
+    r = oracle.residual(t, A, lib)
+    t.groups(lib)
     times = []
     for s in range(sweeps):
         t0 = time.perf_counter()
-        oracle.sals_sweep(t, A, r, WORKLOAD["C"], WORKLOAD["lam"], 1, p.column_order(s, WORKLOAD["C"]))
+        oracle.sals_sweep(t, A, r, WORKLOAD["C"], WORKLOAD["lam"], 1,
+                          p.column_order(s, WORKLOAD["C"]), lib=lib)
         times.append(time.perf_counter() - t0)
     return times, p.nnz * p.K
+
+
+def run_oracle_parity_workload(parallel):
+    """The parity workload in full (1000 x 1000 x 100, 1e5 entries, K = 10, lambda = 1,
+    FP64, five sweeps at C = 5 and at C = 1): seconds per sweep for each C."""
+    import oracle
+    import synth
+    lib = oracle.load_parallel() if parallel else oracle.load()
+    p = synth.parity_3way()
+    c, x = p.numpy()
+    out = {}
+    for C in (5, 1):
+        t = oracle.Tensor(c, x, p.dims)
+        A = [a.numpy() for a in p.init_factors()]
+        r = oracle.residual(t, A, lib)
+        t.groups(lib)
+        t0 = time.perf_counter()
+        for s in range(5):
+            oracle.sals_sweep(t, A, r, C, 1.0, 1, p.column_order(s, C), lib=lib)
+        out[f"C{C}_ms_per_sweep"] = 1e3 * (time.perf_counter() - t0) / 5
+        out[f"C{C}_nnz_rank_per_s"] = p.nnz * p.K / ((time.perf_counter() - t0) / 5)
+    return out
 
 
 def reference_arm(args, rank, world):
@@ -162,17 +192,19 @@ def reference_arm(args, rank, world):
         return 0
     m = args.ref_sample
     steps = args.warmup + args.steps
-    times, units = run_oracle_sample(m, args.seed, steps)
+    threads = oracle_threads()
+    times, units = run_oracle_sample(m, args.seed, steps, parallel=True)
     timed = times[args.warmup:]
     ms = 1e3 * sum(timed) / len(timed)
     value = units / (ms / 1e3)
     sample = (f"first {m} entries (prefix of the seeded 1e8-entry draw) of the workload, "
-              f"one full sweep per step (K=100, C=10), single-threaded C")
+              f"one full sweep per step (K=100, C=10), FP64 C with OpenMP over rows "
+              f"({threads} threads)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {**WORKLOAD, "sample_nnz": m},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -497,6 +529,7 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-sample", type=int, default=400_000)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample-parallel", type=int, default=8_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
@@ -606,7 +639,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "kernel": " + ".join(n for b, n in ((1, "k_pass_wide" if C > 16 else "k_mode_pass"),
-                                                   (2, "k_mode_pass_tma"), (4, "k_pass_wide_tc"))
+                                                   (2, "k_mode_pass_tma"), (4, "k_pass_wide_tc"),
+                                                   (8, "k_lean_pass"))
                                      if cnt["pass_path"] & b) or "?",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
@@ -730,11 +764,24 @@ def main():
                           "pinned host memory + tf_destroy, mean over the timed steps"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, u = run_oracle_sample(args.cpu_sample, args.seed, 1)
-        out["cpu_baseline"] = {"value": u / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"first {args.cpu_sample} entries (prefix of the seeded "
-                                         f"draw) of the same workload, one full sweep, K=100, "
-                                         f"C=10, FP64 single-threaded C"}
+        # the oracle as it stands, after the timed region: its OpenMP build on every host
+        # core over a larger prefix, the serial build over a smaller one, and the parity
+        # workload in full with both
+        threads = oracle_threads()
+        tp, up = run_oracle_sample(args.cpu_sample_parallel, args.seed, 1, parallel=True)
+        ts, us = run_oracle_sample(args.cpu_sample, args.seed, 1)
+        out["cpu_baseline"] = {
+            "value": up / tp[0], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "host_cpus": os.cpu_count(),
+            "sample": f"first {args.cpu_sample_parallel} entries (prefix of the seeded draw) "
+                      f"of the same workload, one full sweep, K=100, C=10, FP64 C with "
+                      f"OpenMP over rows ({threads} threads)",
+            "single_thread": {"value": us / ts[0], "unit": UNIT, "cores": 1,
+                              "sample": f"first {args.cpu_sample} entries, one full sweep"},
+            "parity_workload": {"single_thread": run_oracle_parity_workload(False),
+                                "openmp": run_oracle_parity_workload(True),
+                                "what": "1000x1000x100, 1e5 entries, K=10, lambda=1, FP64, "
+                                        "5 sweeps at C=5 and at C=1, in full"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

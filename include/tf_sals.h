@@ -215,14 +215,17 @@ tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
  * or fragments that pool, and latency-bound loops that must not take the device-wide
  * synchronisation a cudaMalloc or cudaFree may cause.  tf_loss keeps its reduction
  * buffer in the context and allocates it on first use; this entry point instead uses a
- * fixed device array of 8192 doubles (64 KiB) built into the library, one per device,
- * and calls no allocating routine.
+ * fixed device array of 24,576 doubles (192 KiB) built into the library, one per
+ * device, and calls no allocating routine.
  *   Arguments, result and synchronisation as tf_loss; the result is bit-identical to
  *   tf_loss's on the same state.
  *   Limit: the reduction needs 2 + B + 256 N doubles, B = the residual kernel's block
- *   count (at most P, the schedule's bin count).  Beyond 8192 the call returns
- *   TF_EINVAL, says so in tf_last_error, and launches nothing; the default schedule
- *   fits for every N <= 8 on a 152-SM GPU.
+ *   count (at most P, the schedule's bin count).  Beyond 24,576 the call returns
+ *   TF_EINVAL, says so in tf_last_error, and launches nothing.  The default schedule
+ *   (at most 128 bins per SM) fits for every N <= 8 on GPUs of up to 175 SMs; a
+ *   schedule set with tf_set_schedule fits while P + 256 N <= 24,574.
+ *   Device: the call must be made with the context's device current (the device that
+ *   was current at tf_create); otherwise it returns TF_EINVAL and launches nothing.
  *   Set-up: the first call on each device (the device current at the call) looks up
  *   the array's device address with cudaGetSymbolAddress; make that first call before
  *   any stream capture begins.
@@ -292,15 +295,26 @@ tf_status tf_get_counters(tf_ctx *ctx, int64_t counters[8]);
  * entries), so results agree to rounding. */
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 
-/* Data path of the mode pass: 0 = automatic (C <= 16: the cp.async SIMT pass, whose
- * slice-row gathers are served by L1 for hot rows; 16 < C < 128: for float contexts the
- * Gram on the tensor cores (tcgen05, three TF32 products per term, FP32 accumulation)
- * when C >= 64, where it measures faster, SIMT FMAs otherwise and for double),
- * 1 = SIMT everywhere, 2 = the TMA tile::gather4 pass with its shared-memory row cache
- * for C <= 10 (float, N = 3; TF_EINVAL from the next sweep where it does not apply)
- * and the tensor-core Gram for every wide C.  For C <= 16 all paths give bit-identical
- * results; the tensor-core Gram agrees with the SIMT one to FP32 rounding. */
+/* Data path of the mode pass: 0 = automatic (C <= 16: for float three-way tensors and
+ * C <= 12 the lean pass (hot slice rows resident in shared memory, packed two-wide FP32
+ * Gram), else the cp.async SIMT pass; 16 < C < 128: for float contexts the Gram on the
+ * tensor cores (tcgen05, three TF32 products per term, FP32 accumulation) when C >= 64,
+ * where it measures faster, SIMT FMAs otherwise and for double), 1 = the cp.async SIMT
+ * pass everywhere, 2 = the TMA tile::gather4 pass with its shared-memory row cache for
+ * C <= 10 (float, N = 3; TF_EINVAL from the next sweep where it does not apply) and the
+ * tensor-core Gram for every wide C, 3 = the lean pass (TF_EINVAL from the next sweep
+ * where it does not apply; wide C as path 0).  The cp.async and TMA passes give
+ * bit-identical results; the lean pass sums each row's terms in another order and the
+ * tensor-core Gram rounds its products differently, both agreeing to FP32 rounding. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
+
+/* Shared-memory row cache of the lean pass (kernel path 0 or 3): at most max_rows rows of
+ * each other mode's slice are held in shared memory per launch (< 0: as many as fit, the
+ * rows with the most entries first; 0: none), and ring_rows (1..32) distinct rows per
+ * other mode and step are staged ahead for the rest (more are read from global memory).
+ * Where a row comes from does not change any result (bit-identical).  TF_EINVAL for
+ * ring_rows outside 1..32.  No counterpart in the paper. */
+tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int ring_rows);
 
 /* Precision of the Gram matrix of wide subsets (16 < C < 128) in float contexts:
  * 0 = FP32-level (default; on the tensor cores three TF32 products per term), 1 = the

@@ -151,6 +151,7 @@ struct ModeLayout {
     Buf<int32_t> id_of;     // degree rank -> row id
     Buf<int32_t> groups;    // slot groups of split rows (first slot, count), wide subsets
     int n_groups = 0;
+    std::vector<int64_t> deg_cum;  // host: entries of the first R rows in degree-rank order
     int P = 0;
     int omode[kMaxModes - 1];
     template <class F>
@@ -163,6 +164,7 @@ struct ModeLayout {
 struct CtxBase {
     std::string err;
     tf_dtype dtype;
+    int device = 0;  // ordinal of the device current when the context was created
     virtual ~CtxBase() = default;
 };
 
@@ -190,7 +192,8 @@ struct Impl : CtxBase {
     Buf<double> red;               // reduction scratch
     Buf<int64_t> d_dims;
     Buf<int32_t> f_other;          // fold-in scratch
-    Buf<T> f_x, f_out, f_part;
+    Buf<T> f_x, f_out, f_part, f_fac;
+    Buf<double> f_rpart;           // fold-in refinement: factors and FP64 partial residuals
     Buf<int64_t> f_meta;           // tiled fold-in block table / request offsets / status
     Buf<int32_t> p_coords;         // tf_predict staging
     Buf<T> p_out;
@@ -207,7 +210,10 @@ struct Impl : CtxBase {
     int64_t prof_launches[TF_KIND_COUNT] = {0};
     double prof_ms[TF_KIND_COUNT] = {0};
 
-    int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported
+    int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported,
+                                   // 3 lean float pass (three-way tensors)
+    int lean_cache_rows = -1;      // lean pass: cached rows per other mode (< 0: as fit)
+    int lean_ring_cap = 12;        // lean pass: staged cold rows of the varying mode per step
     int precision = 0;             // 0 FP32-level Gram, 1 single-TF32 tensor-core Gram (wide C)
     int solve_refine = 0;          // float: one refinement step of every row solve
     float solve_cond = 0.f;        // float: FP64 solve of rows with pivot ratio < 1 / this
@@ -226,7 +232,8 @@ struct Impl : CtxBase {
     template <class F>
     void each_buf(F f) {
         f(x), f(partials), f(d_order), f(d_Q), f(stat), f(ticket), f(red), f(d_dims);
-        f(f_other), f(f_x), f(f_out), f(f_part), f(f_meta), f(p_coords), f(p_out);
+        f(f_other), f(f_x), f(f_out), f(f_part), f(f_fac), f(f_rpart), f(f_meta), f(p_coords),
+            f(p_out);
         for (int n = 0; n < kMaxModes; ++n) {
             f(A[n]), f(res[n]), f(Z[n]);
             mode[n].each_buf(f);
@@ -317,6 +324,7 @@ struct Impl : CtxBase {
         dims.assign(dims_in, dims_in + N);
         int dev = 0;
         TFS_CUDA(cudaGetDevice(&dev));
+        device = dev;
         TFS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
         P = default_bins(num_sms, nnz);
         stat.alloc(1, st);
@@ -409,9 +417,12 @@ struct Impl : CtxBase {
                         const std::vector<int64_t> order = rows_by_degree(cnt);
                         ids[n].resize((size_t)I);
                         ranks[n].resize((size_t)I);
+                        std::vector<int64_t> &dc = mode[n].deg_cum;
+                        dc.assign((size_t)I + 1, 0);
                         for (int64_t r = 0; r < I; ++r) {
                             ids[n][r] = (int32_t)order[r];
                             ranks[n][order[r]] = (int32_t)r;
+                            dc[r + 1] = dc[r] + cnt[order[r]];
                         }
                     });
                 for (auto &t : th) t.join();
@@ -712,6 +723,11 @@ struct Impl : CtxBase {
         }
         if (path == 2 && !use_tma && !(wide && sizeof(T) == 4))
             throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
+        // the lean float pass wherever it exists (three-way tensors, even widths <= 12)
+        const bool use_lean = sizeof(T) == 4 && !wide && (path == 0 || path == 3) &&
+                              lean_pass_supported(CM, N);
+        if (path == 3 && !use_lean && !wide)
+            throw ApiError{TF_EINVAL, "lean mode pass not available here"};
         last_path = 0;
         const int nsplit = (K + C - 1) / C;
         // every launch of the splits (pack, mode passes, solves) and the copy of the last
@@ -808,6 +824,21 @@ struct Impl : CtxBase {
                             continue;
                         }
                         if constexpr (sizeof(T) == 4) {
+                            if (use_lean) {
+                                const std::vector<int64_t> *dc[2] = {&mode[L.omode[0]].deg_cum,
+                                                                     &mode[L.omode[1]].deg_cum};
+                                const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                                const LeanPlan plan =
+                                    lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
+                                                   lean_cache_rows, lean_ring_cap);
+                                ticket_base += (unsigned long long)L.P +
+                                               (unsigned long long)plan.grid * plan.warps;
+                                timed(TF_KIND_MODE_PASS,
+                                      [&] { launch_lean_pass((const PassArgs<float> &)a, CM, plan, st); });
+                                last_path |= 8;
+                                ++launches;
+                                goto solved;
+                            }
                             if (use_tma) {
                                 const bool before[2] = {L.omode[0] < n, L.omode[1] < n};
                                 const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
@@ -1028,55 +1059,26 @@ struct Impl : CtxBase {
 
     // ------------------------------------------------------------ loss
     void loss(double lambda, uint32_t flags, double *loss_out, double *rmse_out) {
-        if (dirty) rebuild_residuals();
-        const ModeLayout &L = mode[0];
-        const int blocks = res_grid<T>(CM_last, L.P, N);
-        const int reg_blocks = 256;
-        red.ensure((size_t)blocks + (size_t)N * reg_blocks + 4, st);
-        ResArgs<T> a{};
-        a.items = L.items.p;
-        a.bin_ptr = L.bin_ptr.p;
-        a.P = L.P;
-        a.N = N;
-        a.n = 0;
-        a.Cq = Cq;
-        a.what = 0;
-        for (int t = 0; t < N - 1; ++t) {
-            a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
-            a.Zo[t] = Z[L.omode[t]].p;
-        }
-        a.Zn = Z[0].p;
-        a.rank_n = L.rank_of.p;
-        a.res = res[0].p;
-        a.block_out = red.p + 2;
-        double *regp = red.p + 2 + blocks;
-        timed(TF_KIND_LOSS, [&] {
-            launch_res<T>(a, CM_last, st);
-            launch_sum_blocks(red.p + 2, blocks, red.p + 0, st);
-            for (int n = 0; n < N; ++n)
-                launch_reg<T>(A[n].p, dims[n], K,
-                              (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,
-                              regp + (size_t)n * reg_blocks, reg_blocks, st);
-            launch_sum_blocks(regp, N * reg_blocks, red.p + 1, st);
-        });
-        loss_launches = 3 + N;
-        double h[2];
-        TFS_CUDA(cudaMemcpyAsync(h, red.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TFS_CUDA(cudaStreamSynchronize(st));
-        check_errors();
-        if (loss_out) *loss_out = h[0] + lambda * h[1];
-        if (rmse_out) *rmse_out = nnz > 0 ? sqrt(h[0] / (double)nnz) : 0.0;
+        red.ensure(loss_scratch_need(), st);
+        loss_into(lambda, flags, loss_out, rmse_out, red.p, red.n);
     }
 
-    // loss() with its block partials and two sums in `scratch` (cap doubles, device
-    // memory the caller owns) instead of the context's reduction buffer: the same
-    // kernels in the same order, so the result is bit-identical to loss().
+    // Doubles of reduction scratch the loss needs: two totals, one partial per block of
+    // the residual kernel and 256 per mode of the regularisation sums.
+    static constexpr int kRegBlocks = 256;
+    size_t loss_scratch_need() const {
+        return 2 + (size_t)res_grid<T>(CM_last, mode[0].P, N) + (size_t)N * kRegBlocks;
+    }
+
+    // The loss with its block partials and two sums in `scratch` (cap doubles of device
+    // memory): tf_loss passes the context's reduction buffer, tf_loss_noalloc the
+    // library's static array; the kernels and their order are the same, so the results
+    // are bit-identical.
     void loss_into(double lambda, uint32_t flags, double *loss_out, double *rmse_out,
                    double *scratch, size_t cap) {
         const ModeLayout &L = mode[0];
         const int blocks = res_grid<T>(CM_last, L.P, N);
-        const int reg_blocks = 256;
-        const size_t need = 2 + (size_t)blocks + (size_t)N * reg_blocks;
+        const size_t need = loss_scratch_need();
         if (need > cap)
             throw ApiError{TF_EINVAL, "loss reduction needs " + std::to_string(need) +
                                           " scratch doubles; the static array holds " +
@@ -1099,12 +1101,16 @@ struct Impl : CtxBase {
         a.res = res[0].p;
         a.block_out = scratch + 2;
         double *regp = scratch + 2 + blocks;
-        launch_res<T>(a, CM_last, st);
-        launch_sum_blocks(scratch + 2, blocks, scratch + 0, st);
-        for (int n = 0; n < N; ++n)
-            launch_reg<T>(A[n].p, dims[n], K, (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,
-                          regp + (size_t)n * reg_blocks, reg_blocks, st);
-        launch_sum_blocks(regp, N * reg_blocks, scratch + 1, st);
+        timed(TF_KIND_LOSS, [&] {
+            launch_res<T>(a, CM_last, st);
+            launch_sum_blocks(scratch + 2, blocks, scratch + 0, st);
+            for (int n = 0; n < N; ++n)
+                launch_reg<T>(A[n].p, dims[n], K,
+                              (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,
+                              regp + (size_t)n * kRegBlocks, kRegBlocks, st);
+            launch_sum_blocks(regp, N * kRegBlocks, scratch + 1, st);
+        });
+        loss_launches = 3 + N;
         double h[2];
         TFS_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         TFS_CUDA(cudaStreamSynchronize(st));
@@ -1250,6 +1256,12 @@ struct Impl : CtxBase {
         f_x.ensure((size_t)std::max<int64_t>(m, 1), st);
         f_out.ensure((size_t)n_req * K, st);
         f_part.ensure(foldin_part_elems(K, blocks), st);
+        const bool refine = sizeof(T) == 4;
+        if (refine) {
+            size_t fac_elems = 0;
+            f_rpart.ensure(foldin_refine_elems(K, blocks, n_req, &fac_elems), st);
+            f_fac.ensure(fac_elems, st);
+        }
         // one int64 staging buffer: block entry ranges [2B], then as int32 the blocks'
         // requests [B], the requests' first blocks [n_req + 1] and their status [n_req]
         const size_t B = (size_t)std::max(blocks, 1);
@@ -1290,6 +1302,9 @@ struct Impl : CtxBase {
         a.blk_req = d32;
         a.req_blk = d32 + B;
         a.req_status = const_cast<int32_t *>(d32 + B + n_req + 1);
+        a.refine = refine ? 1 : 0;
+        a.fac = refine ? f_fac.p : nullptr;
+        a.rpart = refine ? f_rpart.p : nullptr;
         launch_foldin_tiled<T>(a, blocks, n_req, st);
         std::vector<T> rows((size_t)n_req * K);
         TFS_CUDA(cudaMemcpyAsync(status, a.req_status, (size_t)n_req * sizeof(int32_t),
@@ -1502,17 +1517,25 @@ struct tf_ctx {
 // ------------------------------------------------------------ loss without allocation
 // Scratch of tf_loss_noalloc: the per-block partial sums of the loss reductions and the
 // two totals, in a fixed device array instead of memory the context allocates.  One
-// array per device, shared by every call on that device.
-static constexpr size_t kLossScratchDoubles = 8192;  // 64 KiB
+// array per device, shared by every call on that device.  Sized for the default
+// schedule of a 152-SM GPU in the worst case: 2 totals + 19,456 residual blocks (one
+// warp per bin, 128 bins per SM, one warp per block when a warp's ring is large) +
+// 256 regularisation blocks for each of up to 8 modes = 21,506 doubles.
+static constexpr size_t kLossScratchDoubles = 24576;  // 192 KiB
 static __device__ __align__(256) double g_loss_scratch[kLossScratchDoubles];
 
 namespace {
 
-// Device address of g_loss_scratch on the current device, looked up once per device
-// (the first call on a device does the lookup; later calls reuse it).
-double *loss_scratch_current_device() {
-    int dev = 0;
-    TFS_CUDA(cudaGetDevice(&dev));
+// Device address of g_loss_scratch on `dev`, which must be the current device; looked
+// up once per device (the first call on a device does the lookup, later calls reuse it).
+double *loss_scratch_on(int dev) {
+    int cur = 0;
+    TFS_CUDA(cudaGetDevice(&cur));
+    if (cur != dev)
+        throw tfs::ApiError{TF_EINVAL, "tf_loss_noalloc: the current device (" +
+                                           std::to_string(cur) +
+                                           ") is not the context's device (" +
+                                           std::to_string(dev) + ")"};
     static std::mutex mu;
     static std::vector<double *> addr;  // by device ordinal
     std::lock_guard<std::mutex> lock(mu);
@@ -1681,7 +1704,7 @@ tf_status tf_loss(tf_ctx *ctx, double lambda, uint32_t flags, double *loss, doub
 tf_status tf_loss_noalloc(tf_ctx *ctx, double lambda, uint32_t flags, double *loss,
                           double *train_rmse) {
     return dispatch(ctx, [&](auto &c) {
-        c.loss_into(lambda, flags, loss, train_rmse, loss_scratch_current_device(),
+        c.loss_into(lambda, flags, loss, train_rmse, loss_scratch_on(c.device),
                     kLossScratchDoubles);
     });
 }
@@ -1900,8 +1923,20 @@ tf_status tf_solve_info(tf_ctx *ctx, int64_t *fp64_rows) {
 }
 
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
-    if (path < 0 || path > 2) return TF_EINVAL;
-    return dispatch(ctx, [&](auto &c) { c.path = path; });
+    if (path < 0 || path > 3) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        c.path = path;
+        c.drop_graphs();
+    });
+}
+
+tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int ring_rows) {
+    if (ring_rows < 1 || ring_rows > 32) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        c.lean_cache_rows = max_rows;
+        c.lean_ring_cap = ring_rows;
+        c.drop_graphs();
+    });
 }
 
 tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P) {

@@ -1,6 +1,9 @@
 // Fold-in of a new row against frozen factors: the ALS row solve of Eq. (2),
 // a = (B + lambda I_K)^{-1} c with B = sum_e h_e h_e^T, c = sum_e x_e h_e and
 // h_e,k = prod_{l != mode} a^(l)_{i_l k}, over the request's m entries.
+// Float contexts (K < 128) refine every solve once: the residual of the normal equations
+// is formed from the entries in FP64 and the correction solved with the FP32 factor,
+// which takes the row to FP32 accuracy whatever the rounding of the FP32 Gram sums.
 //
 // One CTA per request.  Entries are taken in tiles of kTileE: the tile's H rows are
 // built in shared memory, then each thread adds the tile's contribution to its own
@@ -231,6 +234,85 @@ __global__ void __launch_bounds__(32) k_fold_solve(const FoldArgs<T> a) {
         return;
     }
     for (int q = lane; q < K; q += 32) a.out[(int64_t)r * K + q] = cv[q];
+    if (a.refine)
+        for (int q = lane; q < NT; q += 32) a.fac[(int64_t)r * NT + q] = P[q];
+}
+
+// Refinement, first half: per block of entries (the Gram's block table), the FP64 sum
+// over its entries of h_e (x_e - h_e . x0), x0 the request's first solution.  One warp
+// per entry at a time (lanes over k, coalesced row reads); h_e,k is a product of FP32
+// factor values formed in FP64, so the entry residual x_e - h_e . x0 carries no
+// cancellation error of the working precision.  The block's warps add their sums in
+// warp order.
+constexpr int kFoldResThreads = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kFoldResThreads) k_fold_resid(const FoldArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *wsum = reinterpret_cast<double *>(smem_raw);  // [8][K]
+    const int K = a.K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = kFoldResThreads / 32;
+    const int req = a.blk_req[blockIdx.x];
+    const int64_t b0 = a.blk_range[2 * blockIdx.x], b1 = a.blk_range[2 * blockIdx.x + 1];
+    double *acc = wsum + (size_t)w * K;
+    for (int k = lane; k < K; k += 32) acc[k] = 0.0;
+    const bool skip = a.req_status[req] != 0;  // bad index or pivot: no refinement
+    const T *x0 = a.out + (int64_t)req * K;
+    if (!skip) {
+        for (int64_t e = b0 + w; e < b1; e += NW) {
+            const T *rows[kMaxModes];
+            int t = 0;
+            for (int l = 0; l < a.N; ++l) {
+                if (l == a.mode) continue;
+                const int32_t idx = a.other[e * (a.N - 1) + t];  // checked by k_fold_gram
+                rows[t] = a.A[l] + (int64_t)idx * K;
+                ++t;
+            }
+            double dot = 0.0;
+            for (int k = lane; k < K; k += 32) {
+                double h = 1.0;
+                for (int u = 0; u < a.N - 1; ++u) h *= (double)rows[u][k];
+                dot += h * (double)x0[k];
+            }
+            dot = warp_sum_d(dot);
+            const double rho = (double)a.x[e] - dot;
+            for (int k = lane; k < K; k += 32) {
+                double h = 1.0;
+                for (int u = 0; u < a.N - 1; ++u) h *= (double)rows[u][k];
+                acc[k] += h * rho;
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double s = 0.0;
+        for (int ww = 0; ww < NW; ++ww) s += wsum[(size_t)ww * K + k];
+        a.rpart[(int64_t)blockIdx.x * K + k] = s;
+    }
+}
+
+// Refinement, second half: one warp per request sums its blocks' partials in block
+// order, subtracts lambda x0 (FP64), solves for the correction with the stored factor
+// and adds it to x0.
+template <class T>
+__global__ void __launch_bounds__(32) k_fold_refine(const FoldArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K = a.K, lane = threadIdx.x, r = blockIdx.x;
+    const int NT = K * (K + 1) / 2;
+    T *L = reinterpret_cast<T *>(smem_raw);
+    T *d = L + NT;
+    if (a.req_status[r] != 0) return;
+    const int bb = a.req_blk[r], be = a.req_blk[r + 1];
+    T *x = a.out + (int64_t)r * K;
+    for (int q = lane; q < NT; q += 32) L[q] = a.fac[(int64_t)r * NT + q];
+    for (int k = lane; k < K; k += 32) {
+        double s = 0.0;
+        for (int b = bb; b < be; ++b) s += a.rpart[(int64_t)b * K + k];
+        d[k] = (T)(s - (double)a.lambda * (double)x[k]);
+    }
+    __syncwarp();
+    warp_chol_apply<T>(L, d, K, lane);
+    for (int k = lane; k < K; k += 32) x[k] += d[k];
 }
 
 }  // namespace
@@ -274,6 +356,20 @@ void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream
     TFS_CUDA(raise_smem_limit((const void *)k_fold_solve<T>, (int)smem));
     k_fold_solve<T><<<n_req, 32, smem, st>>>(a);
     TFS_CUDA(cudaGetLastError());
+    if (a.refine && blocks > 0) {
+        const size_t rs = sizeof(double) * (kFoldResThreads / 32) * (size_t)a.K;
+        TFS_CUDA(raise_smem_limit((const void *)k_fold_resid<T>, (int)rs));
+        k_fold_resid<T><<<blocks, kFoldResThreads, rs, st>>>(a);
+        TFS_CUDA(cudaGetLastError());
+        TFS_CUDA(raise_smem_limit((const void *)k_fold_refine<T>, (int)smem));
+        k_fold_refine<T><<<n_req, 32, smem, st>>>(a);
+        TFS_CUDA(cudaGetLastError());
+    }
+}
+
+size_t foldin_refine_elems(int K, int blocks, int n_req, size_t *fac_elems) {
+    *fac_elems = (size_t)std::max(n_req, 1) * ((size_t)K * (K + 1) / 2);
+    return (size_t)std::max(blocks, 1) * (size_t)K;
 }
 
 template <class T>

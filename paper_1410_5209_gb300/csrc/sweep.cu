@@ -46,12 +46,15 @@ __global__ void k_pack(const PackArgs<T> a) {
     const int64_t i = r - a.row_base[l];  // slice row (rank)
     const T *Ar = a.A[l] + (int64_t)a.id_of[l][i] * a.K;
     T *z = a.Z[l] + i * a.W;
-    for (int c = 0; c < a.C; ++c) {
-        const T v = Ar[a.S[c]];
+    // regions are CM = off_prev wide; columns beyond C (cur, old) and Cq (prev) are
+    // zero, so products over a full region need no column mask
+    const int CM = a.off_prev;
+    for (int c = 0; c < CM; ++c) {
+        const T v = c < a.C ? Ar[a.S[c]] : T(0);
         z[c] = v;
         z[a.off_old + c] = v;
+        z[a.off_prev + c] = c < a.Cq ? Ar[a.Q[c]] : T(0);
     }
-    for (int c = 0; c < a.Cq; ++c) z[a.off_prev + c] = Ar[a.Q[c]];
 }
 
 template <class T>

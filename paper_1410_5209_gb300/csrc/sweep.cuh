@@ -122,6 +122,14 @@ struct FoldArgs {
     const int32_t *blk_req;
     const int32_t *req_blk;
     int32_t *req_status;
+    // float contexts: one step of iterative refinement of every request's solve.  The
+    // solve keeps its Cholesky factor in fac [n_req][K (K + 1) / 2]; a second pass over
+    // the request's entries forms the residual of the normal equations,
+    // c - (B + lambda I) x0 = sum_e h_e (x_e - h_e . x0) - lambda x0, in FP64 (per-block
+    // partials in rpart [blocks][K]); the correction solved with the factor is added.
+    int refine;
+    T *fac;
+    double *rpart;
 };
 
 constexpr int kPassThreads = 128;
@@ -247,11 +255,41 @@ bool foldin_tiled_ok(int K);
 int foldin_plan_blocks(const int64_t *offsets, int n_req, std::vector<int64_t> &blk_range,
                        std::vector<int32_t> &blk_req, std::vector<int32_t> &req_blk);
 size_t foldin_part_elems(int K, int blocks);
+// Refinement buffers of a tiled fold-in: returns the FP64 partial residual elements
+// (blocks x K); *fac_elems receives the factor store's elements (n_req x K(K+1)/2).
+size_t foldin_refine_elems(int K, int blocks, int n_req, size_t *fac_elems);
 template <class T>
 void launch_foldin_tiled(const FoldArgs<T> &a, int blocks, int n_req, cudaStream_t st);
 template <class T>
 size_t foldin_smem_bytes(int K);
 
+
+// Per-launch parameters of the lean pass (host plan -> kernel).
+struct LeanParams {
+    int R[2];          // cached rows of each other mode (slice rows 0 .. R-1)
+    int cap[2];        // ring rows of each other mode per step
+    int cache_off[2];  // float offsets of the caches in dynamic shared memory
+    int ring_off;      // float offset of warp 0's ring
+    int ring_floats;   // floats per warp ring (staged rows, own rows, index lists)
+    int slot_floats;   // floats of one ring slot (the varying mode's rows, then the run mode's)
+    int own_off;       // float offset of the own-row slots within a warp ring
+    int list_off;      // float offset of the index lists within a warp ring
+};
+
+struct LeanPlan {
+    LeanParams p;
+    int warps = 0, grid = 0;
+    size_t smem = 0;
+};
+// Lean float pass (lean_pass.cu): three-way tensors, even register widths up to 12.
+bool lean_pass_supported(int CM, int N);
+// Plan of mode n's lean pass: cached rows of the two other modes chosen by entries covered
+// (deg_cum[t][R] = entries whose mode-t row is among that slice's first R rows), at most
+// max_cache_rows each (< 0: no limit), ring_cap staged cold rows per other mode per step.
+LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
+                        const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
+                        int max_cache_rows, int ring_cap);
+void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl, cudaStream_t st);
 
 // TMA-fed mode pass (float, N = 3, CM <= 10; tma_pass.cuh).  A plan fixes the gather
 // box width per other mode, the rows of each other mode's slice held in the block's
