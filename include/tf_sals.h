@@ -308,13 +308,15 @@ tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
  * tensor-core Gram rounds its products differently, both agreeing to FP32 rounding. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
-/* Shared-memory row cache of the lean pass (kernel path 0 or 3): at most max_rows rows of
+/* Shared-memory layout of the lean pass (kernel path 0 or 3): at most max_rows rows of
  * each other mode's slice are held in shared memory per launch (< 0: as many as fit, the
- * rows with the most entries first; 0: none), and ring_rows (1..32) distinct rows per
- * other mode and step are staged ahead for the rest (more are read from global memory).
- * Where a row comes from does not change any result (bit-identical).  TF_EINVAL for
- * ring_rows outside 1..32.  No counterpart in the paper. */
-tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int ring_rows);
+ * rows with the most entries first; 0: none); the distinct rows outside that cache that a
+ * step of 32 entries needs are staged two steps ahead in a per-warp pool of pool_rows
+ * rows (2..32; a step is cut short where its rows would not fit); warps per block 1..12
+ * (0: the default, 12).  The lean pass plans, once per row schedule and setting, where
+ * each entry's rows will be; no setting changes any result (bit-identical).  TF_EINVAL
+ * for values outside these ranges.  No counterpart in the paper. */
+tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int pool_rows, int warps);
 
 /* Precision of the Gram matrix of wide subsets (16 < C < 128) in float contexts:
  * 0 = FP32-level (default; on the tensor cores three TF32 products per term), 1 = the

@@ -80,7 +80,7 @@ def load():
         "tf_get_counters": [P, P],
         "tf_set_schedule": [P, i32, i32],
         "tf_set_kernel_path": [P, i32],
-        "tf_set_pass_cache": [P, i32, i32],
+        "tf_set_pass_cache": [P, i32, i32, i32],
         "tf_set_precision": [P, i32],
         "tf_set_stream": [P, P],
         "tf_profile": [P, i32],
@@ -316,9 +316,11 @@ class Factorization:
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
 
-    def set_pass_cache(self, max_rows=-1, ring_rows=12):
-        """Lean pass: cached rows per other mode (< 0 as fit, 0 none), staged rows per step."""
-        self._check(self._lib.tf_set_pass_cache(self._ctx, int(max_rows), int(ring_rows)))
+    def set_pass_cache(self, max_rows=-1, pool_rows=32, warps=0):
+        """Lean pass: cached rows per other mode (< 0 as fit, 0 none), staged rows per
+        step, warps per block (0 default)."""
+        self._check(self._lib.tf_set_pass_cache(self._ctx, int(max_rows), int(pool_rows),
+                                                int(warps)))
 
     def set_solve(self, refine=False, cond_limit=0.0):
         """Float row solves: one FP64-residual refinement step; FP64 re-solve of rows whose

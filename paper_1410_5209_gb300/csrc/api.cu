@@ -213,7 +213,21 @@ struct Impl : CtxBase {
     int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported,
                                    // 3 lean float pass (three-way tensors)
     int lean_cache_rows = -1;      // lean pass: cached rows per other mode (< 0: as fit)
-    int lean_ring_cap = 12;        // lean pass: staged cold rows of the varying mode per step
+    int lean_ring_cap = 32;        // lean pass: staged cold rows per step (both modes)
+    int lean_warps = 0;            // lean pass: warps per block (0: default)
+    // Gather plans of the lean pass, built once per (mode, cache rows, pool, refresh
+    // flavour, row schedule) and reused by every later split and sweep.
+    struct GatherPlan {
+        int n = -1, RR = 0, RV = 0, cap = 0, first = 0;
+        int64_t layout_gen = -1;
+        Buf<unsigned char> steps;  // GStep records then the per-step own-row ranks
+        Buf<uint32_t> step_ptr, word;
+        Buf<int32_t> list;
+        int64_t nsteps = 0;
+        uint64_t used = 0;  // last use (LRU)
+    };
+    std::vector<std::unique_ptr<GatherPlan>> gplans;
+    uint64_t gplan_clock = 0;
     int precision = 0;             // 0 FP32-level Gram, 1 single-TF32 tensor-core Gram (wide C)
     int solve_refine = 0;          // float: one refinement step of every row solve
     float solve_cond = 0.f;        // float: FP64 solve of rows with pivot ratio < 1 / this
@@ -238,6 +252,7 @@ struct Impl : CtxBase {
             f(A[n]), f(res[n]), f(Z[n]);
             mode[n].each_buf(f);
         }
+        for (auto &g : gplans) f(g->steps), f(g->step_ptr), f(g->word), f(g->list);
     }
 
     ~Impl() override {
@@ -661,6 +676,93 @@ struct Impl : CtxBase {
         }
     }
 
+    // ------------------------------------------------------------ lean-pass gather plans
+    // The plan of mode n's lean pass for cache rows (RR, RV) of its run / varying modes
+    // and a pool of cap rows: built on the device (a counting pass, two scans, an emitting
+    // pass) the first time a split needs it, then kept (one per mode) until the row
+    // schedule or the cache sizes change.  The refreshing and the plain inner iterations
+    // share it: their cache sizes are both planned for the refreshing pass's wider rows.
+    GatherPlanDev gather_plan(int n, int RR, int RV, int cap) {
+        const int first = 1;
+        const ModeLayout &L = mode[n];
+        for (auto &g : gplans)
+            if (g->n == n && g->RR == RR && g->RV == RV && g->cap == cap &&
+                g->layout_gen == layout_gen) {
+                g->used = ++gplan_clock;
+                GatherPlanDev d;
+                d.steps = g->steps.p;
+                d.rank = reinterpret_cast<const int32_t *>(g->steps.p + (size_t)g->nsteps * 16);
+                d.step_ptr = g->step_ptr.p;
+                d.list = g->list.p;
+                d.word = g->word.p;
+                return d;
+            }
+        // drop plans of an old schedule, then the least recently used beyond one per mode
+        gplans.erase(std::remove_if(gplans.begin(), gplans.end(),
+                                    [&](const std::unique_ptr<GatherPlan> &g) {
+                                        return g->layout_gen != layout_gen;
+                                    }),
+                     gplans.end());
+        {
+            int cnt = 0;
+            for (auto &g : gplans) cnt += g->n == n;
+            if (cnt >= 1) {
+                size_t victim = gplans.size();
+                for (size_t i = 0; i < gplans.size(); ++i)
+                    if (gplans[i]->n == n && (victim == gplans.size() || gplans[i]->used < gplans[victim]->used))
+                        victim = i;
+                gplans.erase(gplans.begin() + (long)victim);
+            }
+        }
+        auto g = std::make_unique<GatherPlan>();
+        g->n = n, g->RR = RR, g->RV = RV, g->cap = cap, g->first = first;
+        g->layout_gen = layout_gen;
+        const int Pn = L.P;
+        const int run = lean_run_mode(n), var = 1 - run;
+        const int32_t *ixR = L.oidx.p + (size_t)run * L.ostride, *ixV = L.oidx.p + (size_t)var * L.ostride;
+        Buf<uint32_t> cnt, tmp;
+        cnt.alloc((size_t)2 * Pn + 2, st);
+        TFS_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)2 * Pn + 2) * sizeof(uint32_t), st));
+        launch_gather_plan(L.items.p, L.bin_ptr.p, Pn, ixR, ixV, L.rank_of.p, RR, RV, cap, first,
+                           cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, st);
+        // step counts cnt[0 .. P), list counts cnt[P .. 2P): exclusive scans over P + 1
+        g->step_ptr.alloc((size_t)Pn + 1, st);
+        Buf<uint32_t> list_ptr;
+        list_ptr.alloc((size_t)Pn + 1, st);
+        Buf<uint32_t> lcnt;
+        lcnt.alloc((size_t)Pn + 1, st);
+        TFS_CUDA(cudaMemcpyAsync(lcnt.p, cnt.p + Pn, (size_t)Pn * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+        TFS_CUDA(cudaMemsetAsync(lcnt.p + Pn, 0, sizeof(uint32_t), st));
+        TFS_CUDA(cudaMemsetAsync(cnt.p + Pn, 0, sizeof(uint32_t), st));
+        tmp.alloc(scan_temp_elems((int64_t)Pn + 1), st);
+        scan_exclusive_u32(cnt.p, g->step_ptr.p, (int64_t)Pn + 1, tmp.p, st);
+        scan_exclusive_u32(lcnt.p, list_ptr.p, (int64_t)Pn + 1, tmp.p, st);
+        uint32_t tot[2];
+        TFS_CUDA(cudaMemcpyAsync(&tot[0], g->step_ptr.p + Pn, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaMemcpyAsync(&tot[1], list_ptr.p + Pn, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaStreamSynchronize(st));
+        g->nsteps = tot[0];
+        g->steps.alloc((size_t)std::max<uint32_t>(tot[0], 1) * gather_plan_step_bytes(), st);
+        g->list.alloc((size_t)std::max<uint32_t>(tot[1], 1), st);
+        g->word.alloc((size_t)std::max<int64_t>(nnz, 1), st);
+        int32_t *rank = reinterpret_cast<int32_t *>(g->steps.p + (size_t)g->nsteps * 16);
+        launch_gather_plan(L.items.p, L.bin_ptr.p, Pn, ixR, ixV, L.rank_of.p, RR, RV, cap, first,
+                           nullptr, g->step_ptr.p, list_ptr.p, g->steps.p, rank, g->list.p,
+                           g->word.p, 1, st);
+        g->used = ++gplan_clock;
+        GatherPlanDev d;
+        d.steps = g->steps.p;
+        d.rank = rank;
+        d.step_ptr = g->step_ptr.p;
+        d.list = g->list.p;
+        d.word = g->word.p;
+        gplans.push_back(std::move(g));
+        return d;
+    }
+
     // ------------------------------------------------------------ the sweep
     void sweep(int C, double lambda, int T_in, const int32_t *order, uint32_t flags) {
         if (C < 1 || C > K) throw ApiError{TF_EINVAL, "C must be in 1..K"};
@@ -830,11 +932,16 @@ struct Impl : CtxBase {
                                 const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
                                 const LeanPlan plan =
                                     lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
-                                                   lean_cache_rows, lean_ring_cap);
+                                                   lean_cache_rows, lean_ring_cap, lean_warps);
+                                const int run = lean_run_mode(n);
+                                const GatherPlanDev gp =
+                                    gather_plan(n, plan.p.R[run], plan.p.R[1 - run],
+                                                plan.p.cap[0]);
                                 ticket_base += (unsigned long long)L.P +
                                                (unsigned long long)plan.grid * plan.warps;
-                                timed(TF_KIND_MODE_PASS,
-                                      [&] { launch_lean_pass((const PassArgs<float> &)a, CM, plan, st); });
+                                timed(TF_KIND_MODE_PASS, [&] {
+                                    launch_lean_pass((const PassArgs<float> &)a, CM, plan, gp, st);
+                                });
                                 last_path |= 8;
                                 ++launches;
                                 goto solved;
@@ -1806,7 +1913,16 @@ tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int 
     const double transpose = x + soa + host_copy;
     const double sorting = x + soa + e * 4 + (double)tfs::sort_workspace_bytes(nnz) + layout;
     const double partials = (maxI + P) * tfs::partial_stride(CM) * T;
-    const double steady = x + layout + plan + factors + partials;
+    // gather plans of the lean float pass (three-way tensors), one per mode: a location
+    // word per entry, at most two list entries per entry, at most three records per
+    // 32-entry step (a record holds at least half a pool of rows' worth of lanes)
+    double gplans = 0;
+    if (dtype == TF_F32 && N == 3)
+        for (int n = 0; n < N; ++n)
+            gplans += e * 4 + e * 8 +
+                      (3.0 * e / 32 + 3.0 * ((double)dims[n] + P)) * tfs::gather_plan_step_bytes() +
+                      (P + 1) * 4 * 2;
+    const double steady = x + layout + plan + factors + partials + gplans;
     // stream-ordered pool rounding: large buffers round up to the pool's 2 MiB mapping
     // granularity (at most 2 MiB each), small ones share chunks
     const double raw = base + std::max(transpose, std::max(sorting, steady));
@@ -1930,11 +2046,12 @@ tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
     });
 }
 
-tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int ring_rows) {
-    if (ring_rows < 1 || ring_rows > 32) return TF_EINVAL;
+tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int pool_rows, int warps) {
+    if (pool_rows < 2 || pool_rows > 32 || warps < 0 || warps > 12) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         c.lean_cache_rows = max_rows;
-        c.lean_ring_cap = ring_rows;
+        c.lean_ring_cap = pool_rows;
+        c.lean_warps = warps;
         c.drop_graphs();
     });
 }

@@ -1,24 +1,30 @@
 // Mode pass of a SALS split for float three-way tensors (Algorithm 1's inner loop over the
 // rows of mode n, Eq. 4 per row, with the R-hat / R updates of Section 3.1 fused as in the
-// cp.async pass): the same arithmetic per entry, organised to move fewer bytes through the
-// SM's load/store pipe and to issue fewer instructions.
+// cp.async pass), split into a planning kernel that runs once per row schedule and slice
+// width, and the pass itself, which runs every split.
 //
+// The index streams of a tensor never change after it is built, so where each entry's
+// other-mode rows will be in shared memory can be decided once:
 //   * Hot slice rows stay in shared memory.  Slices are stored in decreasing order of their
 //     rows' entry counts, so the first R rows of an other mode's slice are the rows that
-//     most entries gather; a block copies them once per launch and every entry whose row
-//     is among them reads it there (no global load, no staging copy).  The host picks R
-//     per other mode from the modes' degree sums so that the cached rows cover the most
+//     most entries gather; each pass copies them once per block.  The host picks R per
+//     other mode from the modes' degree sums so that the cached rows cover the most
 //     entries that fit.
-//   * Rows outside the cache are staged one step ahead through a per-warp ring: the warp
-//     lists the step's distinct cold rows (consecutive equal indices are one row) and
-//     copies them with 16-byte cp.async, a fixed group of lanes per row.  A step with more
-//     distinct cold rows than the ring holds reads the rest straight from global memory.
-//   * Index and residual streams are loaded into registers two steps ahead; the item's own
-//     row (its previous / old columns for the R-hat refresh) is staged with its first step.
-//   * The Gram matrix, right-hand side and refresh products use packed two-wide FP32
-//     instructions (fma.rn.f32x2): a lane accumulates B in 2 x 2 blocks of the lower
-//     triangle.  At the end of an item the 32 lanes' sums are combined by a reduce-scatter
-//     (halving exchanges, fixed order) and written to the item's partial slot.
+//   * The plan (k_gather_plan) cuts each item (a row or row chunk) into steps of up to 32
+//     consecutive entries, short enough that a step's distinct cold rows (rows outside the
+//     caches; consecutive equal indices are one row) fit a warp's staging pool, lists those
+//     rows per step, and gives every entry one 32-bit word: where its varying-mode row is
+//     (cache row or pool position) and where its run-mode row is, or that the lane already
+//     holds the products of that row (the same run index as the lane's previous entry).
+//   * The pass (k_lean_pass) walks a bin's steps: it loads the entries' words and residuals
+//     and the steps' cold-row lists three steps ahead, stages the listed rows two steps
+//     ahead with 16-byte cp.async (a fixed group of lanes per row), and computes: per lane,
+//     products of the run-mode row with the own row's previous / old columns that stay in
+//     registers while the run index holds, the Hadamard product h, the R-hat refresh, and
+//     the Gram matrix, right-hand side with packed two-wide FP32 instructions
+//     (fma.rn.f32x2; 2 x 2 blocks of the lower triangle).  At the end of an item the 32
+//     lanes' sums are combined by a reduce-scatter (halving exchanges, fixed order) and
+//     written to the item's partial slot.
 #include <algorithm>
 #include <numeric>
 
@@ -66,9 +72,6 @@ __device__ __forceinline__ unsigned saddr(const void *p) {
 __device__ __forceinline__ void lds2(unsigned a, u64 &x, u64 &y) {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "r"(a));
 }
-__device__ __forceinline__ void ldg2(const float *p, u64 &x, u64 &y) {
-    asm volatile("ld.global.v2.b64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "l"(p));
-}
 __device__ __forceinline__ u64 lds1(unsigned a) {
     u64 x;
     asm volatile("ld.shared.b64 %0, [%1];" : "=l"(x) : "r"(a));
@@ -85,6 +88,7 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
 
 // Compile-time geometry for register width CM (even) and the refresh flavour.
 //   NLO other modes precede mode n (updated earlier in this split: their rows carry the
@@ -105,21 +109,138 @@ struct LG {
     static constexpr int NT = CM * (CM + 1) / 2;
 };
 
-constexpr int kLeanSlots = 3;  // ring slots: cold rows are staged two steps ahead
+constexpr int kLeanSlots = 3;        // pool slots: cold rows are staged two steps ahead
+constexpr uint32_t kPoolBit = 0x8000u, kKeep = 0xFFFFu;
 
+// Step record of a gather plan: lanes [lo, hi) of the 32-entry step starting at entry j0
+// of one item (a step's lanes are split over several records when its distinct cold rows
+// exceed the pool; each lane still takes the same entry as in an unsplit step, so the
+// per-lane sums, and the results, do not depend on the split).  info packs hi (bits 0-5),
+// first record of the item (6), last record of the item (7), own-row buffer (8-9), staged
+// varying-mode rows nV (10-15), run-mode rows nR (16-21) and lo (22-26); the record's cold
+// rows are list[list_off .. + nV + nR) (varying first).
+struct GStep {
+    int32_t j0, list_off;
+    uint32_t info;
+    int32_t slot;  // partial slot of the item
+};
+
+// ---------------------------------------------------------------------------- planning
+// One warp per bin.  emit = 0: counts the bin's records and list entries into cnt[b] and
+// cnt[P + b].  emit = 1: writes them at step_ptr[b] / list_ptr[b] (exclusive scans of the
+// counts) and every entry's word.
+struct GPlanArgs {
+    const tf_item *items;
+    const int64_t *bin_ptr;
+    int P;
+    const int32_t *ixR, *ixV;  // run / varying mode index streams (slice ranks)
+    const int32_t *rank_n;     // own row -> slice rank
+    int RR, RV, cap, first;
+    uint32_t *cnt;
+    const uint32_t *step_ptr, *list_ptr;
+    GStep *steps;
+    int32_t *rank;   // own slice rank per record (first records of items)
+    int32_t *list;
+    uint32_t *word;  // per entry: varying location | run location << 16
+    int emit;
+};
+
+__global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
+    const int lane = threadIdx.x & 31;
+    const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= g.P) return;
+    const uint32_t lt = (1u << lane) - 1u, le = lt | (1u << lane);
+    uint32_t ns = 0, nl = 0;
+    const uint32_t s0 = g.emit ? g.step_ptr[b] : 0u, l0 = g.emit ? g.list_ptr[b] : 0u;
+    const int64_t it0 = g.bin_ptr[b], it1 = g.bin_ptr[b + 1];
+    for (int64_t it = it0; it < it1; ++it) {
+        const tf_item x = g.items[it];
+        const int jend = (int)(x.begin + x.len);
+        int j = (int)x.begin;
+        int prevR = -1;  // run index of this lane's previous entry in the item
+        bool first = true;
+        const int own = g.emit && g.first ? g.rank_n[x.row] : 0;
+        do {
+            const int cmax = min(kWarp, jend - j);
+            const bool valid = lane < cmax;
+            const int iV = valid ? g.ixV[j + lane] : -1, iR = valid ? g.ixR[j + lane] : -1;
+            const int pV = __shfl_up_sync(0xFFFFFFFFu, iV, 1), pR = __shfl_up_sync(0xFFFFFFFFu, iR, 1);
+            const bool coldV = valid && iV >= g.RV;
+            const bool need = valid && (first || iR != prevR);
+            const bool coldR = need && iR >= g.RR;
+            const uint32_t mV = __ballot_sync(0xFFFFFFFFu, coldV);
+            const uint32_t mR = __ballot_sync(0xFFFFFFFFu, coldR);
+            // records of this step: lanes [lo, hi), the most whose distinct cold rows fit
+            int lo = 0;
+            do {
+                // heads relative to the record's first lane
+                const bool pcV = lane > lo && ((mV >> (lane - 1)) & 1u);
+                const bool pcR = lane > lo && ((mR >> (lane - 1)) & 1u);
+                const uint32_t from = lo >= 32 ? 0u : ~((1u << lo) - 1u);
+                const uint32_t hV = __ballot_sync(0xFFFFFFFFu, coldV && (!pcV || pV != iV)) & from;
+                const uint32_t hR = __ballot_sync(0xFFFFFFFFu, coldR && (!pcR || pR != iR)) & from;
+                const int upto = __popc(hV & le) + __popc(hR & le);
+                const int hi = cmax > 0
+                                   ? lo + __popc(__ballot_sync(0xFFFFFFFFu,
+                                                               valid && lane >= lo && upto <= g.cap))
+                                   : 0;
+                const uint32_t keep = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & from;
+                const int nV = __popc(hV & keep), nR = __popc(hR & keep);
+                if (g.emit) {
+                    if (lane >= lo && lane < hi) {
+                        const uint32_t locV =
+                            coldV ? (kPoolBit | (uint32_t)(__popc(hV & le) - 1)) : (uint32_t)iV;
+                        const uint32_t locR =
+                            !need   ? kKeep
+                            : coldR ? (kPoolBit | (uint32_t)(nV + __popc(hR & le) - 1))
+                                    : (uint32_t)iR;
+                        g.word[j + lane] = locV | (locR << 16);
+                        if ((hV >> lane) & 1u) g.list[l0 + nl + __popc(hV & lt)] = iV;
+                        if ((hR >> lane) & 1u) g.list[l0 + nl + nV + __popc(hR & lt)] = iR;
+                    }
+                    if (lane == 0) {
+                        GStep st;
+                        st.j0 = j;
+                        st.list_off = (int32_t)(l0 + nl);
+                        const bool last = hi >= cmax && j + cmax >= jend;
+                        st.info = (uint32_t)hi | (first && lo == 0 ? 64u : 0u) | (last ? 128u : 0u) |
+                                  ((uint32_t)((it - it0) & 3) << 8) | ((uint32_t)nV << 10) |
+                                  ((uint32_t)nR << 16) | ((uint32_t)lo << 22);
+                        st.slot = x.slot;
+                        g.steps[s0 + ns] = st;
+                        g.rank[s0 + ns] = own;
+                    }
+                }
+                ++ns;
+                nl += (uint32_t)(nV + nR);
+                lo = hi;
+            } while (lo < cmax);
+            if (valid) prevR = iR;
+            j += cmax;
+            first = false;
+        } while (j < jend);
+    }
+    if (!g.emit && lane == 0) {
+        g.cnt[b] = ns;
+        g.cnt[g.P + b] = nl;
+    }
+}
+
+// ---------------------------------------------------------------------------- the pass
 template <int CM, bool FIRST, int NLO, int RUN>
 __global__ void __launch_bounds__(kLeanThreads, 1)
-    k_lean_pass(const PassArgs<float> a, const LeanParams lp) {
+    k_lean_pass(const PassArgs<float> a, const LeanParams lp, const GStep *__restrict__ steps,
+                const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_ptr,
+                const int32_t *__restrict__ list, const uint32_t *__restrict__ word) {
     using G = LG<CM, FIRST, NLO, RUN>;
     constexpr int H = G::H, W = G::W, NACC = G::NACC, VAR = G::VAR;
     constexpr int NVR = G::nv(RUN), NVV = G::nv(VAR), CSR = G::cs(RUN), CSV = G::cs(VAR);
+    constexpr int CSP = CSR > CSV ? CSR : CSV;  // pool row stride
     constexpr bool LOR = G::lo(RUN), LOV = G::lo(VAR);
     extern __shared__ __align__(16) float sm[];
     __shared__ short tgt[2 * NACC];  // partial-slot index of each accumulator float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u, le_mask = lt_mask | (1u << lane);
     const float *ZR = a.Zo[RUN], *ZV = a.Zo[VAR];
-    const int32_t *ixR = a.oidx[RUN], *ixV = a.oidx[VAR];
 
     // accumulator layout -> partial slot index (B lower triangle, then c); -1 = unused
     for (int q = threadIdx.x; q < 2 * NACC; q += blockDim.x) {
@@ -157,10 +278,7 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
         __syncthreads();
     }
     const unsigned cacheR = saddr(sm + lp.cache_off[RUN]), cacheV = saddr(sm + lp.cache_off[VAR]);
-    float *ring = sm + lp.ring_off + warp * lp.ring_floats;
-    int32_t *list = reinterpret_cast<int32_t *>(ring + lp.list_off);  // [2][32]
-    const int RR = lp.R[RUN], RV = lp.R[VAR], capR = lp.cap[RUN], capV = lp.cap[VAR];
-    const int run_off = capV * CSV;  // run-mode rows follow the varying mode's in a slot
+    const unsigned ring_s = saddr(sm + lp.ring_off + warp * lp.ring_floats);
 
     u64 acc[NACC];
 #pragma unroll
@@ -171,220 +289,167 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
 #pragma unroll
     for (int k = 0; k < H; ++k) wc[k] = wp[k] = wo[k] = 0ull;
 
-    // The bin's items, one per lane (item wbase + lane), reloaded every 32 items.
-    int64_t wbase = 0;
-    int w_j0 = 0, w_len = 0, w_slot = 0, w_rank = 0;
-    auto load_window = [&](int64_t base, int64_t it_end) {
-        wbase = base;
-        w_j0 = w_len = w_slot = w_rank = 0;
-        if (base + lane < it_end) {
-            const tf_item x = a.items[base + lane];
-            w_j0 = (int)x.begin;
-            w_len = x.len;
-            w_slot = x.slot;
-            if (FIRST) w_rank = a.rank_n[x.row];
-        }
-    };
-    // Step: entries [j0, jend) of item `it`; meta: bit 0 valid, 1 first, 2 last step.
-    struct St {
-        int j0, jend, it, meta, slot, rank;
-    };
-    auto step_at = [&](int64_t it, int64_t it_end) {
-        St s;
-        s.it = (int)it;
-        if (it >= it_end) {
-            s.j0 = s.jend = s.meta = s.slot = s.rank = 0;
-            return s;
-        }
-        if (it - wbase >= 32) load_window(it, it_end);
-        const int src = (int)(it - wbase);
-        s.j0 = __shfl_sync(0xFFFFFFFFu, w_j0, src);
-        const int len = __shfl_sync(0xFFFFFFFFu, w_len, src);
-        s.slot = __shfl_sync(0xFFFFFFFFu, w_slot, src);
-        s.rank = FIRST ? __shfl_sync(0xFFFFFFFFu, w_rank, src) : 0;
-        s.jend = s.j0 + len;
-        s.meta = 1 | 2 | (len <= kWarp ? 4 : 0);
-        return s;
-    };
-    auto step_next = [&](const St &s, int64_t it_end) {
-        if (!(s.meta & 1)) return s;
-        if (s.j0 + kWarp < s.jend) {
-            St n = s;
-            n.j0 += kWarp;
-            n.meta = 1 | (n.j0 + kWarp >= n.jend ? 4 : 0);
-            return n;
-        }
-        return step_at((int64_t)s.it + 1, it_end);
-    };
-    struct Sr {
-        int iR, iV;
-        float rv;
-    };
-    auto load_streams = [&](const St &s) {
-        Sr r;
-        r.iR = r.iV = -1;
-        r.rv = 0.f;
-        const int j = s.j0 + lane;
-        if ((s.meta & 1) && j < s.jend) {
-            r.iR = __ldg(ixR + j);
-            r.iV = __ldg(ixV + j);
-            r.rv = a.res[j];
-        }
-        return r;
-    };
-    // Step s (streams r; rp = the streams of the step before it): which lanes recompute
-    // their run-mode products (nx), and the distinct cold rows that must be staged --
-    // every cold varying row, and the cold run rows of lanes that recompute -- listed and
-    // copied into ring slot `slot` (16-byte cp.async, a fixed lane group per row); on an
-    // item's first step also the own row's prev | old regions.  hV / hR: head masks.
-    struct Sm {
-        uint32_t hV, hR, nx;
-    };
-    auto fetch = [&](const St &s, const Sr &r, const Sr &rp, int slot) {
-        Sm m;
-        m.hV = m.hR = m.nx = 0u;
-        if (!(s.meta & 1)) return m;
-        const bool valid = s.j0 + lane < s.jend;
-        float *rows = ring + slot * lp.slot_floats;
-        {
-            const int p = __shfl_up_sync(0xFFFFFFFFu, r.iV, 1);
-            const bool cold = valid && r.iV >= RV;
-            m.hV = __ballot_sync(0xFFFFFFFFu, cold && (lane == 0 || p != r.iV));
-            const int k = __popc(m.hV & lt_mask);
-            if (((m.hV >> lane) & 1u) && k < capV) list[k] = r.iV;
-        }
-        {
-            const bool nx = valid && ((s.meta & 2) || r.iR != rp.iR);
-            m.nx = __ballot_sync(0xFFFFFFFFu, nx);
-            const bool key = nx && r.iR >= RR;
-            const int p = __shfl_up_sync(0xFFFFFFFFu, r.iR, 1);
-            const uint32_t keys = __ballot_sync(0xFFFFFFFFu, key);
-            const bool pkey = lane > 0 && ((keys >> (lane - 1)) & 1u);
-            m.hR = __ballot_sync(0xFFFFFFFFu, key && (!pkey || p != r.iR));
-            const int k = __popc(m.hR & lt_mask);
-            if (((m.hR >> lane) & 1u) && k < capR) list[32 + k] = r.iR;
-        }
-        __syncwarp();
-        {
-            constexpr int RPR = 32 / NVV;
-            const int n = min(__popc(m.hV), capV);
-            const int sub = lane / NVV, part = lane - sub * NVV;
-            for (int k0 = 0; k0 < n; k0 += RPR) {
-                const int k = k0 + sub;
-                if (sub < RPR && k < n)
-                    cp16(saddr(rows + k * CSV + 4 * part), ZV + (int64_t)list[k] * W + 4 * part);
-            }
-        }
-        {
-            constexpr int RPR = 32 / NVR;
-            const int n = min(__popc(m.hR), capR);
-            const int sub = lane / NVR, part = lane - sub * NVR;
-            for (int k0 = 0; k0 < n; k0 += RPR) {
-                const int k = k0 + sub;
-                if (sub < RPR && k < n)
-                    cp16(saddr(rows + run_off + k * CSR + 4 * part),
-                         ZR + (int64_t)list[32 + k] * W + 4 * part);
-            }
-        }
-        if (FIRST && (s.meta & 2) && lane < 2 * CM)
-            cp4(saddr(ring + lp.own_off + (s.it & 3) * 2 * CM + lane),
-                a.Zn + (int64_t)s.rank * W + CM + lane);
-        __syncwarp();  // the list is rewritten by the next fetch
-        return m;
-    };
-
     unsigned long long tk_next = 0;
     if (lane == 0) tk_next = atomicAdd(a.ticket, 1ull) - a.ticket_base;
     tk_next = __shfl_sync(0xFFFFFFFFu, tk_next, 0);
     for (;;) {
         const unsigned long long tk = tk_next;
         if (tk >= (unsigned long long)a.P) break;
-        const int64_t it0 = a.bin_ptr[tk], it1 = a.bin_ptr[tk + 1];
+        const int s_begin = (int)step_ptr[tk], s_end = (int)step_ptr[tk + 1];
         if (lane == 0) tk_next = atomicAdd(a.ticket, 1ull) - a.ticket_base;
         tk_next = __shfl_sync(0xFFFFFFFFu, tk_next, 0);
-        load_window(it0, it1);
+        // the bin's step records, one per lane (steps wb + lane), reloaded as needed
+        int wb = s_begin;
+        GStep rec;
+        int rrank = 0;
+        auto window = [&](int base) {
+            wb = base;
+            rec.j0 = rec.list_off = rec.slot = 0;
+            rec.info = 0u;
+            rrank = 0;
+            if (base + lane < s_end) {
+                rec = steps[base + lane];
+                if (FIRST) rrank = srank[base + lane];
+            }
+        };
+        window(s_begin);
+        // per step in flight: info (uniform), the lane's word and residual, the lane's entry
+        // of the step's cold-row list
+        auto info_of = [&](int s) -> uint32_t {
+            return s < s_end ? __shfl_sync(0xFFFFFFFFu, rec.info, s - wb) : 0u;
+        };
+        auto load_words = [&](int s, uint32_t &w, float &rv) {
+            w = kKeep | (kKeep << 16);
+            rv = 0.f;
+            if (s >= s_end) return;
+            const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
+            const int j0 = __shfl_sync(0xFFFFFFFFu, rec.j0, s - wb);
+            const int hi = (int)(inf & 63u), lo = (int)((inf >> 22) & 31u);
+            if (lane >= lo && lane < hi) {
+                w = __ldg(word + j0 + lane);
+                rv = a.res[j0 + lane];
+            }
+        };
+        auto load_list = [&](int s, int &li) {
+            li = 0;
+            if (s >= s_end) return;
+            const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
+            const int loff = __shfl_sync(0xFFFFFFFFu, rec.list_off, s - wb);
+            const int nlist = (int)((inf >> 10) & 63u) + (int)((inf >> 16) & 63u);
+            if (lane < nlist) li = __ldg(list + loff + lane);
+        };
+        // stages step s's cold rows (list entries held by its lanes) into pool slot `slot`,
+        // and on an item's first step the own row's prev | old regions
+        auto stage = [&](int s, int li, int slot) {
+            if (s >= s_end) return;
+            const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
+            const int nV = (int)((inf >> 10) & 63u), nR = (int)((inf >> 16) & 63u);
+            const unsigned pool = ring_s + 4u * (unsigned)(slot * lp.slot_floats);
+            {
+                constexpr int RPR = 32 / NVV;
+                const int sub = lane / NVV, part = lane - sub * NVV;
+                for (int k0 = 0; k0 < nV; k0 += RPR) {
+                    const int k = k0 + sub;
+                    const int row = __shfl_sync(0xFFFFFFFFu, li, k & 31);
+                    if (sub < RPR && k < nV)
+                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part), ZV + (int64_t)row * W + 4 * part);
+                }
+            }
+            {
+                constexpr int RPR = 32 / NVR;
+                const int sub = lane / NVR, part = lane - sub * NVR;
+                for (int k0 = 0; k0 < nR; k0 += RPR) {
+                    const int k = nV + k0 + sub;
+                    const int row = __shfl_sync(0xFFFFFFFFu, li, k & 31);
+                    if (sub < RPR && k0 + sub < nR)
+                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part), ZR + (int64_t)row * W + 4 * part);
+                }
+            }
+            if (FIRST && (inf & 64u)) {
+                const int rk = __shfl_sync(0xFFFFFFFFu, rrank, s - wb);
+                if (lane < 2 * CM)
+                    cp4(ring_s + 4u * (unsigned)(lp.own_off + (int)((inf >> 8) & 3u) * 2 * CM + lane),
+                        a.Zn + (int64_t)rk * W + CM + lane);
+            }
+        };
 
-        St s0 = step_at(it0, it1);
-        St s1 = step_next(s0, it1);
-        St s2 = step_next(s1, it1);
-        Sr r0 = load_streams(s0), r1 = load_streams(s1), r2 = load_streams(s2);
-        Sm m0 = fetch(s0, r0, r0, 0);
+        // Pipeline: words, residuals and list entries three steps ahead, rows two steps
+        // ahead.
+        uint32_t w0, w1, w2;
+        float v0, v1, v2;
+        int l0, l1, l2;
+        load_words(s_begin, w0, v0);
+        load_words(s_begin + 1, w1, v1);
+        load_words(s_begin + 2, w2, v2);
+        load_list(s_begin, l0);
+        load_list(s_begin + 1, l1);
+        load_list(s_begin + 2, l2);
+        stage(s_begin, l0, 0);
         cp_commit();
-        Sm m1 = fetch(s1, r1, r0, 1);
+        stage(s_begin + 1, l1, 1);
         cp_commit();
         int slot = 0;
-        while (s0.meta & 1) {
-            const St s3 = step_next(s2, it1);
-            const Sr r3 = load_streams(s3);
-            const int slot2 = slot + 2 >= kLeanSlots ? slot + 2 - kLeanSlots : slot + 2;
-            const Sm m2 = fetch(s2, r2, r1, slot2);
+        for (int s = s_begin; s < s_end; ++s) {
+            if (s + 3 - wb >= 32) window(s);
+            uint32_t w3;
+            float v3;
+            int l3;
+            load_words(s + 3, w3, v3);
+            load_list(s + 3, l3);
+            stage(s + 2, l2, slot + 2 >= kLeanSlots ? slot + 2 - kLeanSlots : slot + 2);
             cp_commit();
             cp_wait<kLeanSlots - 1>();
             __syncwarp();
-            // ---------------------------------------------------------- compute step s0
-            const float *rows = ring + slot * lp.slot_floats;
-            const int j = s0.j0 + lane;
-            if (j < s0.jend) {
-                if ((m0.nx >> lane) & 1u) {
+            // ---------------------------------------------------------- compute step s
+            const uint32_t inf = info_of(s);
+            const int j0 = __shfl_sync(0xFFFFFFFFu, rec.j0, s - wb);
+            const unsigned pool = ring_s + 4u * (unsigned)(slot * lp.slot_floats);
+            if (lane >= (int)((inf >> 22) & 31u) && lane < (int)(inf & 63u)) {
+                const uint32_t locR = w0 >> 16, locV = w0 & 0xFFFFu;
+                if (locR != kKeep) {
                     u64 xr[2 * NVR];
-                    const int k = __popc(m0.hR & le_mask) - 1;
-                    if (r0.iR < RR) {
-                        const unsigned p = cacheR + 4u * (unsigned)(r0.iR * CSR);
+                    const unsigned p = (locR & kPoolBit) ? pool + 4u * (unsigned)((locR & 0x7FFFu) * CSP)
+                                                         : cacheR + 4u * (unsigned)(locR * CSR);
 #pragma unroll
-                        for (int v = 0; v < NVR; ++v) lds2(p + 16 * v, xr[2 * v], xr[2 * v + 1]);
-                    } else if (k < capR) {
-                        const unsigned p = saddr(rows + run_off) + 4u * (unsigned)(k * CSR);
-#pragma unroll
-                        for (int v = 0; v < NVR; ++v) lds2(p + 16 * v, xr[2 * v], xr[2 * v + 1]);
-                    } else {
-                        const float *p = ZR + (int64_t)r0.iR * W;
-#pragma unroll
-                        for (int v = 0; v < NVR; ++v) ldg2(p + 4 * v, xr[2 * v], xr[2 * v + 1]);
-                    }
+                    for (int v = 0; v < NVR; ++v) lds2(p + 16 * v, xr[2 * v], xr[2 * v + 1]);
 #pragma unroll
                     for (int q = 0; q < H; ++q) wc[q] = xr[q];
                     if constexpr (FIRST) {
-                        const unsigned o = saddr(ring + lp.own_off + (s0.it & 3) * 2 * CM);
+                        const unsigned o = ring_s + 4u * (unsigned)(lp.own_off + (int)((inf >> 8) & 3u) * 2 * CM);
 #pragma unroll
                         for (int q = 0; q < H; ++q) {
                             wp[q] = mul2(lds1(o + 8 * q), xr[H + q]);
-                            wo[q] = mul2(lds1(o + 8 * (H + q)), LOR ? xr[(LOR ? 2 * H : 0) + q] : xr[q]);
+                            wo[q] = mul2(lds1(o + 8 * (H + q)), xr[(LOR ? 2 * H : 0) + q]);
                         }
                     }
                 }
                 u64 y[2 * NVV];
                 {
-                    const int k = __popc(m0.hV & le_mask) - 1;
-                    if (r0.iV < RV) {
-                        const unsigned p = cacheV + 4u * (unsigned)(r0.iV * CSV);
+                    const unsigned p = (locV & kPoolBit) ? pool + 4u * (unsigned)((locV & 0x7FFFu) * CSP)
+                                                         : cacheV + 4u * (unsigned)(locV * CSV);
 #pragma unroll
-                        for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
-                    } else if (k < capV) {
-                        const unsigned p = saddr(rows) + 4u * (unsigned)(k * CSV);
-#pragma unroll
-                        for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
-                    } else {
-                        const float *p = ZV + (int64_t)r0.iV * W;
-#pragma unroll
-                        for (int v = 0; v < NVV; ++v) ldg2(p + 4 * v, y[2 * v], y[2 * v + 1]);
-                    }
+                    for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
                 }
                 u64 h[H];
 #pragma unroll
                 for (int q = 0; q < H; ++q) h[q] = mul2(wc[q], y[q]);
-                float v = r0.rv;
+                float v = v0;
                 if constexpr (FIRST) {
                     // R-hat of this split from the copy's R-hat of the previous one:
                     // v - sum_Q prod prev + sum_S prod old (Algorithm 1, Eq. 5); modes
                     // after n still hold their old columns in cur
-                    u64 pp = 0ull, po = 0ull;
+                    u64 pp0 = 0ull, po0 = 0ull, pp1 = 0ull, po1 = 0ull;
 #pragma unroll
-                    for (int q = 0; q < H; ++q) {
-                        pp = fma2(wp[q], y[H + q], pp);
-                        po = fma2(wo[q], LOV ? y[(LOV ? 2 * H : 0) + q] : y[q], po);
+                    for (int q = 0; q < H; q += 2) {
+                        pp0 = fma2(wp[q], y[H + q], pp0);
+                        po0 = fma2(wo[q], y[(LOV ? 2 * H : 0) + q], po0);
+                        if (q + 1 < H) {
+                            pp1 = fma2(wp[q + 1], y[H + q + 1], pp1);
+                            po1 = fma2(wo[q + 1], y[(LOV ? 2 * H : 0) + q + 1], po1);
+                        }
                     }
-                    v = v - hsum(pp) + hsum(po);
-                    a.res[j] = v;
+                    v = v - (hsum(pp0) + hsum(pp1)) + (hsum(po0) + hsum(po1));
+                    a.res[j0 + lane] = v;
                 }
                 const u64 vv = pk(v, v);
 #pragma unroll
@@ -401,7 +466,7 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
                 for (int I = 0; I < H; ++I)
                     acc[2 * G::NBLK + I] = fma2(h[I], vv, acc[2 * G::NBLK + I]);
             }
-            if (s0.meta & 4) {
+            if (inf & 128u) {
                 // ------------------------------------------------------ end of item
                 // reduce-scatter of the 2 NACC floats over the warp (halving exchanges);
                 // the lane's segment of the sums is [base, base + cnt), in f[0 .. cnt)
@@ -432,7 +497,8 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
                 level(std::integral_constant<int, L2>{}, std::integral_constant<int, L3>{}, 4);
                 level(std::integral_constant<int, L3>{}, std::integral_constant<int, L4>{}, 2);
                 level(std::integral_constant<int, L4>{}, std::integral_constant<int, L5>{}, 1);
-                float *p = a.partials + (int64_t)s0.slot * (G::NT + CM);
+                const int pslot = __shfl_sync(0xFFFFFFFFu, rec.slot, s - wb);
+                float *p = a.partials + (int64_t)pslot * (G::NT + CM);
 #pragma unroll
                 for (int k = 0; k < L5; ++k) {
                     if (k < cnt) {
@@ -444,14 +510,9 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
                 for (int k = 0; k < NACC; ++k) acc[k] = 0ull;
             }
             __syncwarp();
-            s0 = s1;
-            s1 = s2;
-            s2 = s3;
-            r0 = r1;
-            r1 = r2;
-            r2 = r3;
-            m0 = m1;
-            m1 = m2;
+            w0 = w1, w1 = w2, w2 = w3;
+            v0 = v1, v1 = v2, v2 = v3;
+            l1 = l2, l2 = l3;
             slot = slot + 1 >= kLeanSlots ? 0 : slot + 1;
         }
         cp_wait<0>();
@@ -475,30 +536,34 @@ static void lean_geo(int CM, bool first, int n, int t, int &nv, int &cs) {
 // The other mode whose index forms runs along mode n's rows: entries of a row are sorted
 // by (i_{n+1}, i_{n+2}) (mode numbers mod 3), and other mode t = 0 / 1 is the lower /
 // higher of the two mode numbers.
-static int lean_run_mode(int n) { return n == 1 ? 1 : 0; }
+int lean_run_mode(int n) { return n == 1 ? 1 : 0; }
 
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int ring_cap) {
+                        int max_cache_rows, int pool_rows, int warps) {
     int dev = 0, smem_blk = 0;
     TFS_CUDA(cudaGetDevice(&dev));
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     LeanPlan pl;
     LeanParams &lp = pl.p;
-    int nv[2], cs[2];
-    for (int t = 0; t < 2; ++t) lean_geo(CM, first, n, t, nv[t], cs[t]);
-    const int run = lean_run_mode(n), var = 1 - run;
-    // staged rows per step: the varying mode's cold rows every step, the run mode's only
-    // where a lane's run index changes
-    lp.cap[var] = ring_cap;
-    lp.cap[run] = std::max(1, ring_cap / 3);
-    lp.slot_floats = lp.cap[var] * cs[var] + lp.cap[run] * cs[run];
+    // row counts and pool positions are planned for the refreshing pass's rows (the widest),
+    // so the plain inner iterations (narrower rows in the same counts) share its plan
+    int nv[2], cs[2], nvw[2], csw[2];
+    for (int t = 0; t < 2; ++t) {
+        lean_geo(CM, first, n, t, nv[t], cs[t]);
+        lean_geo(CM, true, n, t, nvw[t], csw[t]);
+    }
+    const int csp = std::max(cs[0], cs[1]);
+    lp.cap[0] = lp.cap[1] = pool_rows;
+    lp.slot_floats = pool_rows * csp;
     lp.own_off = kLeanSlots * lp.slot_floats;
     lp.list_off = lp.own_off + 4 * 2 * CM;
-    lp.ring_floats = (lp.list_off + 64 + 3) / 4 * 4;
-    pl.warps = kLeanWarps;
+    lp.ring_floats = (lp.list_off + 3) / 4 * 4;
+    pl.warps = std::max(1, std::min(warps > 0 ? warps : kLeanWarps, kLeanWarps));
     const size_t kStatic = 2048;  // the kernel's static shared memory (target table) + slack
-    const size_t ring_bytes = (size_t)pl.warps * lp.ring_floats * 4;
+    const int cspw = std::max(csw[0], csw[1]);
+    const size_t ring_bytes =
+        (size_t)pl.warps * (((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) * 4;
     const size_t avail =
         (size_t)smem_blk > ring_bytes + kStatic ? smem_blk - ring_bytes - kStatic : 0;
     // cache rows: greedy in chunks of 32 rows by entries covered per byte
@@ -506,14 +571,15 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     size_t used = 0;
     int64_t lim[2];
     for (int t = 0; t < 2; ++t)
-        lim[t] = std::min<int64_t>(dims_o[t], max_cache_rows < 0 ? INT32_MAX : max_cache_rows);
+        lim[t] = std::min<int64_t>(std::min<int64_t>(dims_o[t], 0x7FFF),
+                                   max_cache_rows < 0 ? INT32_MAX : max_cache_rows);
     for (;;) {
         int best = -1, best_rows = 0;
         double best_gain = 0.0;
         for (int t = 0; t < 2; ++t) {
             if (R[t] >= lim[t]) continue;
             const int rows = (int)std::min<int64_t>(32, lim[t] - R[t]);
-            const size_t bytes = (size_t)rows * cs[t] * 4;
+            const size_t bytes = (size_t)rows * csw[t] * 4;
             if (used + bytes > avail) continue;
             const std::vector<int64_t> &dc = *deg_cum[t];
             const double gain = (double)(dc[R[t] + rows] - dc[R[t]]) / (double)bytes;
@@ -525,7 +591,7 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
         }
         if (best < 0) break;
         R[best] += best_rows;
-        used += (size_t)best_rows * cs[best] * 4;
+        used += (size_t)best_rows * csw[best] * 4;
     }
     (void)nnz;
     lp.R[0] = R[0];
@@ -538,38 +604,74 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     return pl;
 }
 
+size_t gather_plan_step_bytes() { return sizeof(GStep) + sizeof(int32_t); }
+
+void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,
+                        const int32_t *ixV, const int32_t *rank_n, int RR, int RV, int cap,
+                        int first, uint32_t *cnt, const uint32_t *step_ptr,
+                        const uint32_t *list_ptr, void *steps, int32_t *rank, int32_t *list,
+                        uint32_t *word, int emit, cudaStream_t st) {
+    GPlanArgs g{};
+    g.items = items;
+    g.bin_ptr = bin_ptr;
+    g.P = P;
+    g.ixR = ixR;
+    g.ixV = ixV;
+    g.rank_n = rank_n;
+    g.RR = RR;
+    g.RV = RV;
+    g.cap = cap;
+    g.first = first;
+    g.cnt = cnt;
+    g.step_ptr = step_ptr;
+    g.list_ptr = list_ptr;
+    g.steps = static_cast<GStep *>(steps);
+    g.rank = rank;
+    g.list = list;
+    g.word = word;
+    g.emit = emit;
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)P * 32 + threads - 1) / threads);
+    k_gather_plan<<<blocks, threads, 0, st>>>(g);
+    TFS_CUDA(cudaGetLastError());
+}
+
 template <int CM, bool FIRST, int NLO, int RUN>
-static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, cudaStream_t st) {
+static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
+                          cudaStream_t st) {
     auto kern = k_lean_pass<CM, FIRST, NLO, RUN>;
     TFS_CUDA(raise_smem_limit((const void *)kern, (int)pl.smem));
-    kern<<<pl.grid, kLeanThreads, pl.smem, st>>>(a, pl.p);
+    kern<<<pl.grid, pl.warps * kWarp, pl.smem, st>>>(
+        a, pl.p, static_cast<const GStep *>(gp.steps), gp.rank, gp.step_ptr, gp.list, gp.word);
     TFS_CUDA(cudaGetLastError());
 }
 
 template <int CM>
-static void launch_lean_cm(const PassArgs<float> &a, const LeanPlan &pl, cudaStream_t st) {
+static void launch_lean_cm(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
+                           cudaStream_t st) {
     if (!a.first) {
         if (a.n == 1)
-            launch_lean_t<CM, false, 0, 1>(a, pl, st);
+            launch_lean_t<CM, false, 0, 1>(a, pl, gp, st);
         else
-            launch_lean_t<CM, false, 0, 0>(a, pl, st);
+            launch_lean_t<CM, false, 0, 0>(a, pl, gp, st);
         return;
     }
     switch (a.n) {
-        case 0: launch_lean_t<CM, true, 0, 0>(a, pl, st); return;
-        case 1: launch_lean_t<CM, true, 1, 1>(a, pl, st); return;
-        default: launch_lean_t<CM, true, 2, 0>(a, pl, st); return;
+        case 0: launch_lean_t<CM, true, 0, 0>(a, pl, gp, st); return;
+        case 1: launch_lean_t<CM, true, 1, 1>(a, pl, gp, st); return;
+        default: launch_lean_t<CM, true, 2, 0>(a, pl, gp, st); return;
     }
 }
 
-void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl, cudaStream_t st) {
+void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl,
+                      const GatherPlanDev &gp, cudaStream_t st) {
     switch (CM) {
-        case 2: launch_lean_cm<2>(a, pl, st); return;
-        case 4: launch_lean_cm<4>(a, pl, st); return;
-        case 6: launch_lean_cm<6>(a, pl, st); return;
-        case 8: launch_lean_cm<8>(a, pl, st); return;
-        case 10: launch_lean_cm<10>(a, pl, st); return;
-        case 12: launch_lean_cm<12>(a, pl, st); return;
+        case 2: launch_lean_cm<2>(a, pl, gp, st); return;
+        case 4: launch_lean_cm<4>(a, pl, gp, st); return;
+        case 6: launch_lean_cm<6>(a, pl, gp, st); return;
+        case 8: launch_lean_cm<8>(a, pl, gp, st); return;
+        case 10: launch_lean_cm<10>(a, pl, gp, st); return;
+        case 12: launch_lean_cm<12>(a, pl, gp, st); return;
         default: throw ApiError{TF_EINVAL, "no lean mode-pass instance for this C"};
     }
 }

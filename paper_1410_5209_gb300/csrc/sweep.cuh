@@ -267,13 +267,13 @@ size_t foldin_smem_bytes(int K);
 // Per-launch parameters of the lean pass (host plan -> kernel).
 struct LeanParams {
     int R[2];          // cached rows of each other mode (slice rows 0 .. R-1)
-    int cap[2];        // ring rows of each other mode per step
+    int cap[2];        // staging pool rows per step (both modes together: cap[0])
     int cache_off[2];  // float offsets of the caches in dynamic shared memory
     int ring_off;      // float offset of warp 0's ring
-    int ring_floats;   // floats per warp ring (staged rows, own rows, index lists)
-    int slot_floats;   // floats of one ring slot (the varying mode's rows, then the run mode's)
-    int own_off;       // float offset of the own-row slots within a warp ring
-    int list_off;      // float offset of the index lists within a warp ring
+    int ring_floats;   // floats per warp ring (pool slots, own-row buffers)
+    int slot_floats;   // floats of one pool slot
+    int own_off;       // float offset of the own-row buffers within a warp ring
+    int list_off;      // end of the own-row buffers within a warp ring
 };
 
 struct LeanPlan {
@@ -281,15 +281,37 @@ struct LeanPlan {
     int warps = 0, grid = 0;
     size_t smem = 0;
 };
+
+// Device arrays of a gather plan (lean_pass.cu): per bin its steps step_ptr[b] ..
+// step_ptr[b + 1] - 1 (16-byte records), the own-row rank of each step, the steps'
+// cold-row lists and one location word per entry.
+struct GatherPlanDev {
+    const void *steps = nullptr;
+    const int32_t *rank = nullptr;
+    const uint32_t *step_ptr = nullptr;
+    const int32_t *list = nullptr;
+    const uint32_t *word = nullptr;
+};
+
 // Lean float pass (lean_pass.cu): three-way tensors, even register widths up to 12.
 bool lean_pass_supported(int CM, int N);
+int lean_run_mode(int n);  // the other mode (0 / 1) whose index forms runs in mode n's rows
 // Plan of mode n's lean pass: cached rows of the two other modes chosen by entries covered
 // (deg_cum[t][R] = entries whose mode-t row is among that slice's first R rows), at most
-// max_cache_rows each (< 0: no limit), ring_cap staged cold rows per other mode per step.
+// max_cache_rows each (< 0: no limit), pool_rows staged cold rows per step, warps per block
+// (0: default).
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int ring_cap);
-void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl, cudaStream_t st);
+                        int max_cache_rows, int pool_rows, int warps);
+size_t gather_plan_step_bytes();  // bytes per step record (+ its own-row rank)
+// emit = 0: per-bin step and list counts into cnt[b] / cnt[P + b]; emit = 1: the plan.
+void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,
+                        const int32_t *ixV, const int32_t *rank_n, int RR, int RV, int cap,
+                        int first, uint32_t *cnt, const uint32_t *step_ptr,
+                        const uint32_t *list_ptr, void *steps, int32_t *rank, int32_t *list,
+                        uint32_t *word, int emit, cudaStream_t st);
+void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl,
+                      const GatherPlanDev &gp, cudaStream_t st);
 
 // TMA-fed mode pass (float, N = 3, CM <= 10; tma_pass.cuh).  A plan fixes the gather
 // box width per other mode, the rows of each other mode's slice held in the block's

@@ -333,14 +333,14 @@ def test_lean_pass_matches_oracle_and_cp_async_pass(C):
 
 @pytest.mark.parametrize("C", [4, 10])
 def test_lean_pass_row_sources_bit_identical(C):
-    """Where the lean pass reads a slice row (the shared-memory cache, the staged ring, or
-    global memory when a step has more distinct cold rows than the ring holds) does not
-    change the arithmetic: identical bits for every cache and ring setting."""
+    """Where the lean pass reads a slice row (the shared-memory cache or the staging pool,
+    steps cut short where their cold rows would not fit) and how many warps share a block
+    do not change the arithmetic: identical bits for every setting."""
     p = synth.small(70 + C, (2000, 1500, 80), 150_000, 4, 20, modes=["zipf", "zipf", "uniform"])
     out = []
-    for max_rows, ring in ((-1, 16), (0, 32), (0, 1), (48, 4), (300, 16)):
+    for max_rows, pool, warps in ((-1, 24, 0), (0, 32, 0), (0, 2, 0), (48, 4, 5), (300, 16, 12)):
         f, _, _ = make(p, tf.F32)
-        f.set_pass_cache(max_rows, ring)
+        f.set_pass_cache(max_rows, pool, warps)
         for s in range(2):
             f.sweep(C, 0.1, 1 + s, p.column_order(s, C))
         assert f.counters()["pass_path"] & 8

@@ -60,11 +60,12 @@ def test_budget_and_slots():
 
 def test_estimate_covers_the_resident_arrays():
     """The estimate is at least what a context keeps resident: values, N residual copies,
-    N sorted orders, N(N-1) other-mode index streams, the factors."""
+    N sorted orders, N(N-1) other-mode index streams, the factors, and for float
+    three-way tensors the lean pass's gather plans (a location word per entry and mode)."""
     dims, nnz, K = (100_000, 100_000, 1_000), 100_000_000, 100
     est = tf.estimate_bytes(dims, nnz, K, 10, tf.F32, num_sms=152)
     N = 3
-    resident = nnz * 4 * (1 + N + N + N * (N - 1)) + sum(dims) * K * 4
+    resident = nnz * 4 * (1 + N + N + N * (N - 1) + N) + sum(dims) * K * 4
     assert resident <= est <= 1.5 * resident
     # and at least the layout build's peak: values, SoA coordinates, a key array and the
     # sort's two alternate arrays beside the per-mode orders and index streams
@@ -79,7 +80,10 @@ def test_estimate_grows_with_the_problem():
     assert tf.estimate_bytes(base["dims"], 4_000_000, 32, 8, num_sms=152) > e0
     assert tf.estimate_bytes(base["dims"], 2_000_000, 64, 8, num_sms=152) > e0
     assert tf.estimate_bytes(base["dims"], 2_000_000, 32, 30, num_sms=152) > e0
-    assert tf.estimate_bytes(base["dims"], 2_000_000, 32, 8, tf.F64, num_sms=152) > e0
+    # wider values (four-way, where neither dtype has gather plans)
+    d4 = (5000, 4000, 300, 20)
+    assert tf.estimate_bytes(d4, 2_000_000, 32, 8, tf.F64, num_sms=152) > \
+        tf.estimate_bytes(d4, 2_000_000, 32, 8, tf.F32, num_sms=152)
     # device-resident input needs no host-copy staging
     assert tf.estimate_bytes(base["dims"], 2_000_000, 32, 8, device_input=True,
                              num_sms=152) <= e0
