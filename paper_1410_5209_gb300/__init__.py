@@ -360,7 +360,8 @@ class Factorization:
         self._check(self._lib.tf_set_stream(self._ctx, ctypes.c_void_p(handle or 0)))
 
     def set_precision(self, mode):
-        """0: FP32-level Gram; 1: single-TF32 tensor-core Gram for wide subsets."""
+        """0: FP32-level Gram; 1: single-TF32 tensor-core Gram (wide subsets, and narrow
+        ones of three-way float tensors)."""
         self._check(self._lib.tf_set_precision(self._ctx, int(mode)))
 
     def set_schedule(self, policy=SCHED_LPT, P=0):

@@ -211,7 +211,8 @@ struct Impl : CtxBase {
     double prof_ms[TF_KIND_COUNT] = {0};
 
     int path = 0;                  // 0 auto, 1 cp.async SIMT pass, 2 TMA pass when supported,
-                                   // 3 lean float pass (three-way tensors)
+                                   // 3 lean float pass (three-way tensors), 4 the lean pass
+                                   // with its Gram on the tensor cores
     int lean_cache_rows = -1;      // lean pass: cached rows per other mode (< 0: as fit)
     int lean_ring_cap = 32;        // lean pass: staged cold rows per step (both modes)
     int lean_warps = 0;            // lean pass: warps per block (0: default)
@@ -826,9 +827,9 @@ struct Impl : CtxBase {
         if (path == 2 && !use_tma && !(wide && sizeof(T) == 4))
             throw ApiError{TF_EINVAL, "TMA mode pass not available here"};
         // the lean float pass wherever it exists (three-way tensors, even widths <= 12)
-        const bool use_lean = sizeof(T) == 4 && !wide && (path == 0 || path == 3) &&
+        const bool use_lean = sizeof(T) == 4 && !wide && (path == 0 || path >= 3) &&
                               lean_pass_supported(CM, N);
-        if (path == 3 && !use_lean && !wide)
+        if (path >= 3 && !use_lean && !wide)
             throw ApiError{TF_EINVAL, "lean mode pass not available here"};
         last_path = 0;
         const int nsplit = (K + C - 1) / C;
@@ -930,9 +931,13 @@ struct Impl : CtxBase {
                                 const std::vector<int64_t> *dc[2] = {&mode[L.omode[0]].deg_cum,
                                                                      &mode[L.omode[1]].deg_cum};
                                 const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                                // Gram flavour: TF32 x 1 on the tensor cores for the
+                                // reduced-precision form; FP32-level otherwise (packed FMAs,
+                                // or three TF32 products on the tensor cores on path 4)
+                                const int gk = precision == 1 ? 1 : (path == 4 ? 3 : 0);
                                 const LeanPlan plan =
                                     lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
-                                                   lean_cache_rows, lean_ring_cap, lean_warps);
+                                                   lean_cache_rows, lean_ring_cap, lean_warps, gk);
                                 const int run = lean_run_mode(n);
                                 const GatherPlanDev gp =
                                     gather_plan(n, plan.p.R[run], plan.p.R[1 - run],
@@ -2039,7 +2044,7 @@ tf_status tf_solve_info(tf_ctx *ctx, int64_t *fp64_rows) {
 }
 
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
-    if (path < 0 || path > 3) return TF_EINVAL;
+    if (path < 0 || path > 4) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         c.path = path;
         c.drop_graphs();
@@ -2047,7 +2052,7 @@ tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
 }
 
 tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int pool_rows, int warps) {
-    if (pool_rows < 2 || pool_rows > 32 || warps < 0 || warps > 12) return TF_EINVAL;
+    if (pool_rows < 2 || pool_rows > 32 || warps < 0 || warps > 16) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         c.lean_cache_rows = max_rows;
         c.lean_ring_cap = pool_rows;

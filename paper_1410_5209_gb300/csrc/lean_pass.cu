@@ -83,6 +83,29 @@ __device__ __forceinline__ void cp16(unsigned dst, const void *src) {
 __device__ __forceinline__ void cp4(unsigned dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void ldsm4(unsigned addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                      uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+// D (16 x 8, FP32) += A (16 x 8, TF32, row-major) * B (8 x 8, TF32, column-major)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void sts32(unsigned a, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -227,8 +250,18 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
 }
 
 // ---------------------------------------------------------------------------- the pass
-template <int CM, bool FIRST, int NLO, int RUN>
-__global__ void __launch_bounds__(kLeanThreads, 1)
+// GK: how the Gram matrix and right-hand side are accumulated.  0: per lane, packed
+// two-wide FP32 FMAs (a lane sums its own entries; the warp's sums are combined at the
+// end of an item).  1 / 3: on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
+// accumulation): the warp writes the step's H' = [h | r_hat] (columns 0 .. CM-1 and 15)
+// transposed into shared memory, loads it as A fragments, and since the product is
+// H'^T H' the B fragments are the same registers; the 16 x 16 sums are spread over the
+// warp, 8 per lane, so no end-of-item reduction is needed.  1: one TF32 product per term;
+// 3: three (h = hi + lo, hi hi + hi lo + lo hi), FP32-level.
+constexpr int kLeanStageStride = 36;  // floats per staged H' row (conflict-free)
+
+template <int CM, bool FIRST, int NLO, int RUN, int GK>
+__global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
     k_lean_pass(const PassArgs<float> a, const LeanParams lp, const GStep *__restrict__ steps,
                 const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_ptr,
                 const int32_t *__restrict__ list, const uint32_t *__restrict__ word) {
@@ -280,9 +313,19 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
     const unsigned cacheR = saddr(sm + lp.cache_off[RUN]), cacheV = saddr(sm + lp.cache_off[VAR]);
     const unsigned ring_s = saddr(sm + lp.ring_off + warp * lp.ring_floats);
 
-    u64 acc[NACC];
+    u64 acc[GK == 0 ? NACC : 1];
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = 0ull;
+    for (int k = 0; k < (GK == 0 ? NACC : 1); ++k) acc[k] = 0ull;
+    float dg[2][4];  // tensor-core sums: columns 0-7 and 8-15 of H'^T H'
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dg[0][q] = dg[1][q] = 0.f;
+    const unsigned stage_hi = ring_s + 4u * (unsigned)lp.list_off;
+    const unsigned stage_lo = stage_hi + 4u * 16u * kLeanStageStride;
+    if (GK != 0) {  // staged H' rows CM .. 14 stay zero
+        for (int q = lane; q < 16 * kLeanStageStride * (GK == 3 ? 2 : 1); q += 32)
+            sts32(stage_hi + 4u * (unsigned)q, 0u);
+        __syncwarp();
+    }
     // Per lane, products of the run-mode row (and the own row) that stay fixed while the
     // lane's run index does: wc = cur, wp = own prev * prev, wo = own old * old.
     u64 wc[H], wp[H], wo[H];
@@ -404,7 +447,12 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
             const uint32_t inf = info_of(s);
             const int j0 = __shfl_sync(0xFFFFFFFFu, rec.j0, s - wb);
             const unsigned pool = ring_s + 4u * (unsigned)(slot * lp.slot_floats);
-            if (lane >= (int)((inf >> 22) & 31u) && lane < (int)(inf & 63u)) {
+            u64 h[H];
+#pragma unroll
+            for (int q = 0; q < H; ++q) h[q] = 0ull;
+            float v = 0.f;
+            const bool act = lane >= (int)((inf >> 22) & 31u) && lane < (int)(inf & 63u);
+            if (act) {
                 const uint32_t locR = w0 >> 16, locV = w0 & 0xFFFFu;
                 if (locR != kKeep) {
                     u64 xr[2 * NVR];
@@ -430,10 +478,9 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
 #pragma unroll
                     for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
                 }
-                u64 h[H];
 #pragma unroll
                 for (int q = 0; q < H; ++q) h[q] = mul2(wc[q], y[q]);
-                float v = v0;
+                v = v0;
                 if constexpr (FIRST) {
                     // R-hat of this split from the copy's R-hat of the previous one:
                     // v - sum_Q prod prev + sum_S prod old (Algorithm 1, Eq. 5); modes
@@ -451,22 +498,82 @@ __global__ void __launch_bounds__(kLeanThreads, 1)
                     v = v - (hsum(pp0) + hsum(pp1)) + (hsum(po0) + hsum(po1));
                     a.res[j0 + lane] = v;
                 }
-                const u64 vv = pk(v, v);
+                if constexpr (GK == 0) {
+                    const u64 vv = pk(v, v);
 #pragma unroll
-                for (int J = 0; J < H; ++J) {
-                    const u64 hs = swp(h[J]);
+                    for (int J = 0; J < H; ++J) {
+                        const u64 hs = swp(h[J]);
 #pragma unroll
-                    for (int I = J; I < H; ++I) {
-                        const int b = I * (I + 1) / 2 + J;
-                        acc[2 * b] = fma2(h[I], h[J], acc[2 * b]);
-                        acc[2 * b + 1] = fma2(h[I], hs, acc[2 * b + 1]);
+                        for (int I = J; I < H; ++I) {
+                            const int b = I * (I + 1) / 2 + J;
+                            acc[2 * b] = fma2(h[I], h[J], acc[2 * b]);
+                            acc[2 * b + 1] = fma2(h[I], hs, acc[2 * b + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int I = 0; I < H; ++I)
+                        acc[2 * G::NBLK + I] = fma2(h[I], vv, acc[2 * G::NBLK + I]);
+                }
+            }
+            if constexpr (GK != 0) {
+                // H' of the step (idle lanes: zeros), transposed: row f holds feature f of
+                // the 32 entries; then per 8 entries one A-fragment load and two MMAs
+                // (three products each for GK 3)
+                {
+                    float hf[2 * H];
+#pragma unroll
+                    for (int q = 0; q < H; ++q) upk(h[q], hf[2 * q], hf[2 * q + 1]);
+#pragma unroll
+                    for (int f = 0; f <= CM; ++f) {
+                        const float x = f < CM ? hf[f < CM ? f : 0] : v;
+                        const int row = f < CM ? f : 15;
+                        const uint32_t hi = to_tf32(x);
+                        sts32(stage_hi + 4u * (unsigned)(row * kLeanStageStride + lane), hi);
+                        if (GK == 3)
+                            sts32(stage_lo + 4u * (unsigned)(row * kLeanStageStride + lane),
+                                  to_tf32(x - __uint_as_float(hi)));
                     }
                 }
+                __syncwarp();
+                const int t = lane >> 3, r = lane & 7;
+                const unsigned tile = 4u * (unsigned)((r + 8 * (t & 1)) * kLeanStageStride + 4 * (t >> 1));
 #pragma unroll
-                for (int I = 0; I < H; ++I)
-                    acc[2 * G::NBLK + I] = fma2(h[I], vv, acc[2 * G::NBLK + I]);
+                for (int kb = 0; kb < 4; ++kb) {
+                    uint32_t a0, a1, a2, a3;
+                    ldsm4(stage_hi + tile + 32u * kb, a0, a1, a2, a3);
+                    mma_tf32(dg[0], a0, a1, a2, a3, a0, a2);
+                    mma_tf32(dg[1], a0, a1, a2, a3, a1, a3);
+                    if constexpr (GK == 3) {
+                        uint32_t c0, c1, c2, c3;
+                        ldsm4(stage_lo + tile + 32u * kb, c0, c1, c2, c3);
+                        mma_tf32(dg[0], a0, a1, a2, a3, c0, c2);
+                        mma_tf32(dg[1], a0, a1, a2, a3, c1, c3);
+                        mma_tf32(dg[0], c0, c1, c2, c3, a0, a2);
+                        mma_tf32(dg[1], c0, c1, c2, c3, a1, a3);
+                    }
+                }
+                __syncwarp();  // the staging buffer is rewritten by the next step
             }
-            if (inf & 128u) {
+            if (GK != 0 && (inf & 128u)) {
+                // end of item: each sum is held by one lane (the C-fragment layout)
+                const int pslot = __shfl_sync(0xFFFFFFFFu, rec.slot, s - wb);
+                float *p = a.partials + (int64_t)pslot * (G::NT + CM);
+                const int g = lane >> 2, tg = lane & 3;
+#pragma unroll
+                for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int i = g + 8 * (q >> 1), jj = 2 * tg + (q & 1) + 8 * nb;
+                        if (i < CM) {
+                            if (jj == 15)
+                                p[G::NT + i] = dg[nb][q];
+                            else if (jj <= i)
+                                p[i * (i + 1) / 2 + jj] = dg[nb][q];
+                        }
+                        dg[nb][q] = 0.f;
+                    }
+            }
+            if (GK == 0 && (inf & 128u)) {
                 // ------------------------------------------------------ end of item
                 // reduce-scatter of the 2 NACC floats over the warp (halving exchanges);
                 // the lane's segment of the sums is [base, base + cnt), in f[0 .. cnt)
@@ -540,7 +647,7 @@ int lean_run_mode(int n) { return n == 1 ? 1 : 0; }
 
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int pool_rows, int warps) {
+                        int max_cache_rows, int pool_rows, int warps, int gk) {
     int dev = 0, smem_blk = 0;
     TFS_CUDA(cudaGetDevice(&dev));
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -555,15 +662,22 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     }
     const int csp = std::max(cs[0], cs[1]);
     lp.cap[0] = lp.cap[1] = pool_rows;
+    pl.gk = gk;
+    const int stage = gk == 0 ? 0 : 16 * kLeanStageStride * (gk == 3 ? 2 : 1);
     lp.slot_floats = pool_rows * csp;
     lp.own_off = kLeanSlots * lp.slot_floats;
-    lp.list_off = lp.own_off + 4 * 2 * CM;
-    lp.ring_floats = (lp.list_off + 3) / 4 * 4;
-    pl.warps = std::max(1, std::min(warps > 0 ? warps : kLeanWarps, kLeanWarps));
+    lp.list_off = (lp.own_off + 4 * 2 * CM + 3) / 4 * 4;  // the tensor-core staging follows
+    lp.ring_floats = lp.list_off + stage;
     const size_t kStatic = 2048;  // the kernel's static shared memory (target table) + slack
     const int cspw = std::max(csw[0], csw[1]);
-    const size_t ring_bytes =
-        (size_t)pl.warps * (((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) * 4;
+    const size_t warp_bytes =
+        ((((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) + stage) * 4;
+    // as many warps as asked for (default: the most the registers allow) whose rings fit
+    const int max_warps = gk == 0 ? kLeanWarps : 16;
+    const int fit = (int)std::min<size_t>(max_warps, ((size_t)smem_blk - kStatic) / warp_bytes);
+    if (fit < 1) throw ApiError{TF_EINVAL, "lean mode pass: staging pool does not fit"};
+    pl.warps = std::max(1, std::min(warps > 0 ? warps : max_warps, fit));
+    const size_t ring_bytes = (size_t)pl.warps * warp_bytes;
     const size_t avail =
         (size_t)smem_blk > ring_bytes + kStatic ? smem_blk - ring_bytes - kStatic : 0;
     // cache rows: greedy in chunks of 32 rows by entries covered per byte
@@ -636,42 +750,52 @@ void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, con
     TFS_CUDA(cudaGetLastError());
 }
 
-template <int CM, bool FIRST, int NLO, int RUN>
+template <int CM, bool FIRST, int NLO, int RUN, int GK>
 static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                           cudaStream_t st) {
-    auto kern = k_lean_pass<CM, FIRST, NLO, RUN>;
+    auto kern = k_lean_pass<CM, FIRST, NLO, RUN, GK>;
     TFS_CUDA(raise_smem_limit((const void *)kern, (int)pl.smem));
     kern<<<pl.grid, pl.warps * kWarp, pl.smem, st>>>(
         a, pl.p, static_cast<const GStep *>(gp.steps), gp.rank, gp.step_ptr, gp.list, gp.word);
     TFS_CUDA(cudaGetLastError());
 }
 
-template <int CM>
+template <int CM, int GK>
 static void launch_lean_cm(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                            cudaStream_t st) {
     if (!a.first) {
         if (a.n == 1)
-            launch_lean_t<CM, false, 0, 1>(a, pl, gp, st);
+            launch_lean_t<CM, false, 0, 1, GK>(a, pl, gp, st);
         else
-            launch_lean_t<CM, false, 0, 0>(a, pl, gp, st);
+            launch_lean_t<CM, false, 0, 0, GK>(a, pl, gp, st);
         return;
     }
     switch (a.n) {
-        case 0: launch_lean_t<CM, true, 0, 0>(a, pl, gp, st); return;
-        case 1: launch_lean_t<CM, true, 1, 1>(a, pl, gp, st); return;
-        default: launch_lean_t<CM, true, 2, 0>(a, pl, gp, st); return;
+        case 0: launch_lean_t<CM, true, 0, 0, GK>(a, pl, gp, st); return;
+        case 1: launch_lean_t<CM, true, 1, 1, GK>(a, pl, gp, st); return;
+        default: launch_lean_t<CM, true, 2, 0, GK>(a, pl, gp, st); return;
+    }
+}
+
+template <int CM>
+static void launch_lean_gk(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
+                           cudaStream_t st) {
+    switch (pl.gk) {
+        case 1: launch_lean_cm<CM, 1>(a, pl, gp, st); return;
+        case 3: launch_lean_cm<CM, 3>(a, pl, gp, st); return;
+        default: launch_lean_cm<CM, 0>(a, pl, gp, st); return;
     }
 }
 
 void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl,
                       const GatherPlanDev &gp, cudaStream_t st) {
     switch (CM) {
-        case 2: launch_lean_cm<2>(a, pl, gp, st); return;
-        case 4: launch_lean_cm<4>(a, pl, gp, st); return;
-        case 6: launch_lean_cm<6>(a, pl, gp, st); return;
-        case 8: launch_lean_cm<8>(a, pl, gp, st); return;
-        case 10: launch_lean_cm<10>(a, pl, gp, st); return;
-        case 12: launch_lean_cm<12>(a, pl, gp, st); return;
+        case 2: launch_lean_gk<2>(a, pl, gp, st); return;
+        case 4: launch_lean_gk<4>(a, pl, gp, st); return;
+        case 6: launch_lean_gk<6>(a, pl, gp, st); return;
+        case 8: launch_lean_gk<8>(a, pl, gp, st); return;
+        case 10: launch_lean_gk<10>(a, pl, gp, st); return;
+        case 12: launch_lean_gk<12>(a, pl, gp, st); return;
         default: throw ApiError{TF_EINVAL, "no lean mode-pass instance for this C"};
     }
 }

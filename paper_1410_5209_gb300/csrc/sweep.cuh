@@ -279,6 +279,7 @@ struct LeanParams {
 struct LeanPlan {
     LeanParams p;
     int warps = 0, grid = 0;
+    int gk = 0;  // Gram: 0 packed FP32 FMAs, 1 one TF32 MMA product, 3 three (FP32-level)
     size_t smem = 0;
 };
 
@@ -299,10 +300,10 @@ int lean_run_mode(int n);  // the other mode (0 / 1) whose index forms runs in m
 // Plan of mode n's lean pass: cached rows of the two other modes chosen by entries covered
 // (deg_cum[t][R] = entries whose mode-t row is among that slice's first R rows), at most
 // max_cache_rows each (< 0: no limit), pool_rows staged cold rows per step, warps per block
-// (0: default).
+// (0: default), gk the Gram flavour (LeanPlan::gk).
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int pool_rows, int warps);
+                        int max_cache_rows, int pool_rows, int warps, int gk);
 size_t gather_plan_step_bytes();  // bytes per step record (+ its own-row rank)
 // emit = 0: per-bin step and list counts into cnt[b] / cnt[P + b]; emit = 1: the plan.
 void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,

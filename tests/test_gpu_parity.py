@@ -331,6 +331,66 @@ def test_lean_pass_matches_oracle_and_cp_async_pass(C):
     assert abs(rmse - rmseo) <= 1e-4 * rmseo
 
 
+@pytest.mark.parametrize("C", [2, 5, 10, 12])
+def test_lean_tensor_core_gram_fp32_level(C):
+    """The lean pass with its Gram on the tensor cores (path 4: three TF32 products per
+    term, FP32 accumulation) against the FP64 oracle and the packed-FMA lean pass: the first
+    split's mode-1 rows within 1e-5 (or their FP32 forward-error bound), and two sweeps
+    (T_in = 1 then 2) within FP32-level error."""
+    p = synth.small(80 + C, (900, 700, 60), 120_000, 4, 24, modes=["zipf", "zipf", "uniform"])
+    f, t, A = make(p, tf.F32)
+    f.set_kernel_path(4)
+    g, _, _ = make(p, tf.F32)
+    A_in = [a.copy() for a in A]
+    r = oracle.residual(t, A)
+    order = p.column_order(0, C)
+    f.sweep(C, 0.2, 1, order)
+    g.sweep(C, 0.2, 1, order)
+    oracle.sals_sweep(t, A, r, C, 0.2, 1, order)
+    S = order[:C]
+    got, ref = f.factors(0)[:, S].astype(np.float64), A[0][:, S]
+    assert rel(got, ref) <= 1e-5
+    num, den = np.linalg.norm(got - ref, axis=1), np.linalg.norm(ref, axis=1)
+    for i in np.nonzero(num > 1e-5 * den)[0]:
+        assert num[i] <= fp32_row_bound(t, 0, i, A_in, S, t.x, 0.2, ref[i]), i
+    order = p.column_order(1, C)
+    f.sweep(C, 0.2, 2, order)
+    g.sweep(C, 0.2, 2, order)
+    oracle.sals_sweep(t, A, r, C, 0.2, 2, order)
+    for n in range(3):
+        assert rel(f.factors(n).astype(np.float64), A[n]) < 2e-4, n
+        assert rel(f.factors(n), g.factors(n)) < 2e-4, n
+    _, rmse = f.loss(0.2)
+    _, rmseo = oracle.loss(t, r, A, 0.2)
+    assert abs(rmse - rmseo) <= 1e-4 * rmseo
+
+
+@pytest.mark.parametrize("C", [4, 10])
+def test_lean_tf32_gram_precision_form(C):
+    """The reduced-precision form (tf_set_precision(1): one TF32 product per Gram term on
+    the tensor cores): its error against the FP64 oracle after three sweeps is stated by
+    this test -- factors within 5e-2 normwise, training RMSE within 1e-3 -- and the run is
+    deterministic."""
+    p = synth.small(90 + C, (900, 700, 60), 120_000, 4, 20, modes=["zipf", "zipf", "uniform"])
+    out = []
+    for _ in range(2):
+        f, t, A = make(p, tf.F32)
+        f.set_precision(1)
+        r = oracle.residual(t, A)
+        for s in range(3):
+            order = p.column_order(s, C)
+            f.sweep(C, 0.3, 1, order)
+            oracle.sals_sweep(t, A, r, C, 0.3, 1, order)
+        out.append([f.factors(n) for n in range(3)])
+        for n in range(3):
+            assert rel(f.factors(n).astype(np.float64), A[n]) < 5e-2, n
+        _, rmse = f.loss(0.3)
+        _, rmseo = oracle.loss(t, r, A, 0.3)
+        assert abs(rmse - rmseo) <= 1e-3 * rmseo
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("C", [4, 10])
 def test_lean_pass_row_sources_bit_identical(C):
     """Where the lean pass reads a slice row (the shared-memory cache or the staging pool,
