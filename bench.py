@@ -41,10 +41,10 @@ NCU_SOURCE_HASH = "f6a7e3dc3356da9b"
 
 
 def kernel_source_hash():
-    """Hash of the source of the dominant kernel (k_mode_pass and its device code) and of
-    the header that sets its launch shape (the default bin count)."""
+    """Hash of the source of the dominant kernel (k_lean_pass and its plan) and of the
+    header that sets its launch shape (the default bin count)."""
     h = hashlib.sha256()
-    for f in ("mode_pass.cuh", "sweep.cuh"):
+    for f in ("lean_pass.cu", "sweep.cuh"):
         with open(os.path.join(ROOT, "paper_1410_5209_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -402,6 +402,135 @@ def fiveway(args, rank, world):
     return 0
 
 
+def precision_forms(args, p, K, C, lam, sweeps=3):
+    """The Gram flavours of the mode pass on the same tensor from the same initial factors
+    (a fresh context each, the same column orders): device ms per sweep (sweeps after the
+    first, which also builds the pass's gather plans) and training RMSE after `sweeps`."""
+    import torch
+    import paper_1410_5209_gb300 as tf
+    forms = {"fp32_packed_fma": (0, 0), "tf32x1_tensor_core": (0, 1),
+             "tf32x3_tensor_core": (4, 0), "cp_async_pass": (1, 0)}
+    out = {}
+    for name, (path, prec) in forms.items():
+        s = torch.cuda.Stream()
+        g = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+                             stream=s.cuda_stream, device_input=True)
+        g.set_kernel_path(path)
+        g.set_precision(prec)
+        ms = []
+        for it in range(sweeps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.sweep(C, lam, 1)
+            e1.record(s)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        _, rmse = g.loss(lam)
+        g.close()
+        t = sum(ms[1:]) / max(len(ms) - 1, 1)
+        out[name] = {"ms_per_sweep": t, "nnz_rank_per_s": p.nnz * K / (t / 1e3),
+                     "train_rmse": rmse}
+    base = out["fp32_packed_fma"]["train_rmse"]
+    for v in out.values():
+        v["rmse_rel_to_fp32"] = (v["train_rmse"] - base) / base
+    out["what"] = (f"{sweeps} sweeps from the same initial factors, C={C}, lambda={lam}; "
+                   "ms per sweep over sweeps 2..; equal RMSE means |rmse_rel_to_fp32| <= 1e-3")
+    return out
+
+
+def batched_config(args, tensors, hbm):
+    """The batch of many small tensors (mode lengths 50..5,000 and 1e3..1e6 entries,
+    log-uniform, capped at half the cells; rank-16 truth; K = 16, C = 4) as one
+    block-diagonal tensor, each sweep one CUDA-graph launch; ms per sweep against the
+    sweep's algorithmic HBM bytes."""
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    K, C, lam = 16, 4, 0.1
+    t0 = time.perf_counter()
+    p, _, _ = synth.batched(tensors, seed=args.seed, K=K, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    s = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+                         stream=s.cuda_stream, device_input=True)
+    f.sync()
+    create_s = time.perf_counter() - t0
+    del p
+    f.set_graphs(True)
+    for _ in range(3):
+        f.sweep(C, lam, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 3
+    e0.record(s)
+    for _ in range(steps):
+        f.sweep(C, lam, 1)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nnz = f.nnz
+    _, rmse = f.loss(lam)
+    cnt, gi = f.counters(), f.graph_info()
+    f.close()
+    N = 3
+    sweep_bytes = nnz * (N * (4 * (N - 1) + 4) + 4) * math.ceil(K / C)
+    achieved = sweep_bytes / (ms / 1e3) / 1e9
+    return {"tensors": tensors, "nnz": nnz, "K": K, "C": C, "ms_per_sweep": ms,
+            "nnz_rank_per_s": nnz * K / (ms / 1e3), "train_rmse": rmse,
+            "kernels_per_sweep": cnt["last_sweep_launches"],
+            "graph_launches_per_sweep": 1 if gi["replays"] else None,
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": sweep_bytes,
+                         "floor_ms": sweep_bytes / (hbm * 1e9) * 1e3, "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
+            "generate_s": gen_s, "create_s": create_s}
+
+
+def fiveway_config(args, nnz, hbm):
+    """The five-way tensor (mode lengths 1e6, uniform-random distinct entries, rank-20
+    truth + N(0, 0.1^2), FP32; K = 1000, C = 10, lambda = 1): one sweep, against its
+    algorithmic bytes -- the streams and the factor-row gathers, which go to HBM here
+    (each 1e6-row slice is larger than a share of L2)."""
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    K, C, lam, dims = 1000, 10, 1.0, (1_000_000,) * 5
+    t0 = time.perf_counter()
+    p = synth.make_problem(dims, nnz, 20, K, args.seed, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    s = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed, dtype=tf.F32,
+                         stream=s.cuda_stream, device_input=True)
+    f.sync()
+    create_s = time.perf_counter() - t0
+    nnz = p.nnz
+    del p
+    torch.cuda.empty_cache()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    f.sweep(C, lam, 1)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, rmse = f.loss(lam)
+    f.close()
+    N = 5
+    splits = math.ceil(K / C)
+    stream = nnz * (N * (4 * (N - 1) + 4) + 4) * splits
+    gathers = nnz * N * (N - 1) * 4 * C * splits
+    achieved = (stream + gathers) / (ms / 1e3) / 1e9
+    return {"nnz": nnz, "dims": list(dims), "K": K, "C": C, "ms_per_sweep": ms,
+            "nnz_rank_per_s": nnz * K / (ms / 1e3), "train_rmse_after": rmse,
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": stream + gathers,
+                         "stream_bytes": stream, "gather_bytes": gathers,
+                         "floor_ms": (stream + gathers) / (hbm * 1e9) * 1e3,
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm},
+            "generate_s": gen_s, "create_s": create_s}
+
+
 def small_sweeps(args):
     """The 1e5-entry FP64 parity workload (1000 x 1000 x 100, K = 10), C = 1 (CDTF) and
     C = 5: device time per sweep with eager launches and with the sweep replayed as a
@@ -530,6 +659,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=400_000)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-parallel", type=int, default=8_000_000)
+    ap.add_argument("--configs", type=int, default=1,
+                    help="also run the precision forms, the batched and the five-way configs")
+    ap.add_argument("--batched-tensors", type=int, default=4096)
+    ap.add_argument("--fiveway-nnz", type=int, default=500_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nnz", type=int, default=WORKLOAD["nnz"])
@@ -724,6 +857,8 @@ def main():
             out["serving_server"] = serve_with_jobs(args, f, p, lam)
     f.close()
     del f
+    if args.configs and rank == 0 and world == 1:
+        out["precision"] = precision_forms(args, p, K, C, lam)
     if args.small_sweeps:
         out["small_sweeps"] = small_sweeps(args)
 
@@ -763,6 +898,14 @@ def main():
                   "what": "tf_create from pinned host COO + 1 sweep + tf_loss + factors to "
                           "pinned host memory + tf_destroy, mean over the timed steps"}
 
+    if args.configs and rank == 0 and world == 1:
+        torch.cuda.empty_cache()
+        if args.batched_tensors > 0:
+            out["batched"] = batched_config(args, args.batched_tensors, hbm)
+            torch.cuda.empty_cache()
+        if args.fiveway_nnz > 0:
+            out["fiveway"] = fiveway_config(args, args.fiveway_nnz, hbm)
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle as it stands, after the timed region: its OpenMP build on every host
         # core over a larger prefix, the serial build over a smaller one, and the parity

@@ -698,23 +698,15 @@ struct Impl : CtxBase {
                 d.word = g->word.p;
                 return d;
             }
-        // drop plans of an old schedule, then the least recently used beyond one per mode
+        // drop plans of an old schedule and this mode's plan for other cache sizes; sweep
+        // graphs captured with a dropped plan go too (they hold its addresses)
+        const size_t before = gplans.size();
         gplans.erase(std::remove_if(gplans.begin(), gplans.end(),
                                     [&](const std::unique_ptr<GatherPlan> &g) {
-                                        return g->layout_gen != layout_gen;
+                                        return g->layout_gen != layout_gen || g->n == n;
                                     }),
                      gplans.end());
-        {
-            int cnt = 0;
-            for (auto &g : gplans) cnt += g->n == n;
-            if (cnt >= 1) {
-                size_t victim = gplans.size();
-                for (size_t i = 0; i < gplans.size(); ++i)
-                    if (gplans[i]->n == n && (victim == gplans.size() || gplans[i]->used < gplans[victim]->used))
-                        victim = i;
-                gplans.erase(gplans.begin() + (long)victim);
-            }
-        }
+        if (gplans.size() != before) drop_graphs();
         auto g = std::make_unique<GatherPlan>();
         g->n = n, g->RR = RR, g->RV = RV, g->cap = cap, g->first = first;
         g->layout_gen = layout_gen;
@@ -927,17 +919,25 @@ struct Impl : CtxBase {
                             continue;
                         }
                         if constexpr (sizeof(T) == 4) {
-                            if (use_lean) {
-                                const std::vector<int64_t> *dc[2] = {&mode[L.omode[0]].deg_cum,
-                                                                     &mode[L.omode[1]].deg_cum};
-                                const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
-                                // Gram flavour: TF32 x 1 on the tensor cores for the
-                                // reduced-precision form; FP32-level otherwise (packed FMAs,
-                                // or three TF32 products on the tensor cores on path 4)
-                                const int gk = precision == 1 ? 1 : (path == 4 ? 3 : 0);
-                                const LeanPlan plan =
-                                    lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
-                                                   lean_cache_rows, lean_ring_cap, lean_warps, gk);
+                            // the lean pass where its shared-memory cache serves at
+                            // least a quarter of the varying mode's gathers (measured
+                            // slower than the cp.async pass on tensors without hot rows:
+                            // a batch of 4,096 small tensors, uniform 1e5^3)
+                            const std::vector<int64_t> *dc[2] = {&mode[L.omode[0]].deg_cum,
+                                                                 &mode[L.omode[1]].deg_cum};
+                            const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                            // Gram flavour: TF32 x 1 on the tensor cores for the
+                            // reduced-precision form; FP32-level otherwise (packed FMAs,
+                            // or three TF32 products on the tensor cores on path 4)
+                            const int gk = precision == 1 ? 1 : (path == 4 ? 3 : 0);
+                            LeanPlan plan{};
+                            bool lean_here = use_lean;
+                            if (lean_here) {
+                                plan = lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
+                                                      lean_cache_rows, lean_ring_cap, lean_warps, gk);
+                                lean_here = path != 0 || plan.coverage >= 0.25;
+                            }
+                            if (lean_here) {
                                 const int run = lean_run_mode(n);
                                 const GatherPlanDev gp =
                                     gather_plan(n, plan.p.R[run], plan.p.R[1 - run],

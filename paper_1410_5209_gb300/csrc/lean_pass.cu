@@ -707,7 +707,11 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
         R[best] += best_rows;
         used += (size_t)best_rows * csw[best] * 4;
     }
-    (void)nnz;
+    {
+        const int var = 1 - lean_run_mode(n);
+        const std::vector<int64_t> &dc = *deg_cum[var];
+        pl.coverage = nnz > 0 ? (double)dc[R[var]] / (double)nnz : 1.0;
+    }
     lp.R[0] = R[0];
     lp.R[1] = R[1];
     lp.cache_off[0] = 0;

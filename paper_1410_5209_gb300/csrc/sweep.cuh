@@ -281,6 +281,7 @@ struct LeanPlan {
     int warps = 0, grid = 0;
     int gk = 0;  // Gram: 0 packed FP32 FMAs, 1 one TF32 MMA product, 3 three (FP32-level)
     size_t smem = 0;
+    double coverage = 0;  // entries whose varying-mode row is cached, fraction of all
 };
 
 // Device arrays of a gather plan (lean_pass.cu): per bin its steps step_ptr[b] ..

@@ -400,6 +400,7 @@ def test_lean_pass_row_sources_bit_identical(C):
     out = []
     for max_rows, pool, warps in ((-1, 24, 0), (0, 32, 0), (0, 2, 0), (48, 4, 5), (300, 16, 12)):
         f, _, _ = make(p, tf.F32)
+        f.set_kernel_path(tf.Factorization.PATH_LEAN)   # also where the cache covers little
         f.set_pass_cache(max_rows, pool, warps)
         for s in range(2):
             f.sweep(C, 0.1, 1 + s, p.column_order(s, C))
