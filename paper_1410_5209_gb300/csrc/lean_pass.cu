@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
     }
     const unsigned cacheR = saddr(sm + lp.cache_off[RUN]), cacheV = saddr(sm + lp.cache_off[VAR]);
     const unsigned ring_s = saddr(sm + lp.ring_off + warp * lp.ring_floats);
+    const unsigned str_s = ring_s + 4u * (unsigned)lp.str_off;
 
     u64 acc[GK == 0 ? NACC : 1];
 #pragma unroll
@@ -361,30 +362,35 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
         auto info_of = [&](int s) -> uint32_t {
             return s < s_end ? __shfl_sync(0xFFFFFFFFu, rec.info, s - wb) : 0u;
         };
-        auto load_words = [&](int s, uint32_t &w, float &rv) {
-            w = kKeep | (kKeep << 16);
-            rv = 0.f;
+        // Streams in the warp's shared-memory ring (slot = step mod 4: word [32],
+        // residual [32], list entries [32]), copied in with 4-byte cp.async so that no
+        // register waits on a load before its step comes up.
+        auto str_at = [&](int s, int arr) -> unsigned {
+            return str_s + 4u * (unsigned)(((s & 3) * 3 + arr) * 32 + lane);
+        };
+        auto load_words = [&](int s) {
             if (s >= s_end) return;
             const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
             const int j0 = __shfl_sync(0xFFFFFFFFu, rec.j0, s - wb);
             const int hi = (int)(inf & 63u), lo = (int)((inf >> 22) & 31u);
             if (lane >= lo && lane < hi) {
-                w = __ldg(word + j0 + lane);
-                rv = a.res[j0 + lane];
+                cp4(str_at(s, 0), word + j0 + lane);
+                cp4(str_at(s, 1), a.res + j0 + lane);
             }
         };
-        auto load_list = [&](int s, int &li) {
-            li = 0;
+        auto load_list = [&](int s) {
             if (s >= s_end) return;
             const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
             const int loff = __shfl_sync(0xFFFFFFFFu, rec.list_off, s - wb);
             const int nlist = (int)((inf >> 10) & 63u) + (int)((inf >> 16) & 63u);
-            if (lane < nlist) li = __ldg(list + loff + lane);
+            if (lane < nlist) cp4(str_at(s, 2), list + loff + lane);
         };
         // stages step s's cold rows (list entries held by its lanes) into pool slot `slot`,
         // and on an item's first step the own row's prev | old regions
-        auto stage = [&](int s, int li, int slot) {
+        auto stage = [&](int s, int slot) {
             if (s >= s_end) return;
+            int li = 0;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(li) : "r"(str_at(s, 2)));
             const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
             const int nV = (int)((inf >> 10) & 63u), nR = (int)((inf >> 16) & 63u);
             const unsigned pool = ring_s + 4u * (unsigned)(slot * lp.slot_floats);
@@ -416,33 +422,36 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
             }
         };
 
-        // Pipeline: words, residuals and list entries three steps ahead, rows two steps
-        // ahead.
-        uint32_t w0, w1, w2;
-        float v0, v1, v2;
-        int l0, l1, l2;
-        load_words(s_begin, w0, v0);
-        load_words(s_begin + 1, w1, v1);
-        load_words(s_begin + 2, w2, v2);
-        load_list(s_begin, l0);
-        load_list(s_begin + 1, l1);
-        load_list(s_begin + 2, l2);
-        stage(s_begin, l0, 0);
+        // Pipeline (one cp.async group per step): words and residuals three steps ahead,
+        // list entries four ahead, rows two ahead.  At the top of step s the group of step
+        // s - 2 is complete: the rows of s, the words of s + 1 and the list of s + 2.
+        load_words(s_begin);
+        load_list(s_begin);
+        load_list(s_begin + 1);
+        load_list(s_begin + 2);
         cp_commit();
-        stage(s_begin + 1, l1, 1);
+        cp_wait<0>();
+        __syncwarp();
+        stage(s_begin, 0);
+        load_words(s_begin + 1);
+        load_words(s_begin + 2);
+        cp_commit();
+        stage(s_begin + 1, 1);
+        load_list(s_begin + 3);
         cp_commit();
         int slot = 0;
         for (int s = s_begin; s < s_end; ++s) {
-            if (s + 3 - wb >= 32) window(s);
-            uint32_t w3;
-            float v3;
-            int l3;
-            load_words(s + 3, w3, v3);
-            load_list(s + 3, l3);
-            stage(s + 2, l2, slot + 2 >= kLeanSlots ? slot + 2 - kLeanSlots : slot + 2);
-            cp_commit();
-            cp_wait<kLeanSlots - 1>();
+            if (s + 4 - wb >= 32) window(s);
+            cp_wait<1>();
             __syncwarp();
+            stage(s + 2, slot + 2 >= kLeanSlots ? slot + 2 - kLeanSlots : slot + 2);
+            load_words(s + 3);
+            load_list(s + 4);
+            cp_commit();
+            uint32_t w0;
+            float v0;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w0) : "r"(str_at(s, 0)));
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v0) : "r"(str_at(s, 1)));
             // ---------------------------------------------------------- compute step s
             const uint32_t inf = info_of(s);
             const int j0 = __shfl_sync(0xFFFFFFFFu, rec.j0, s - wb);
@@ -617,9 +626,6 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
                 for (int k = 0; k < NACC; ++k) acc[k] = 0ull;
             }
             __syncwarp();
-            w0 = w1, w1 = w2, w2 = w3;
-            v0 = v1, v1 = v2, v2 = v3;
-            l1 = l2, l2 = l3;
             slot = slot + 1 >= kLeanSlots ? 0 : slot + 1;
         }
         cp_wait<0>();
@@ -667,11 +673,12 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     lp.slot_floats = pool_rows * csp;
     lp.own_off = kLeanSlots * lp.slot_floats;
     lp.list_off = (lp.own_off + 4 * 2 * CM + 3) / 4 * 4;  // the tensor-core staging follows
-    lp.ring_floats = lp.list_off + stage;
+    lp.str_off = lp.list_off + stage;  // stream ring: 4 slots x (words, residuals, lists)
+    lp.ring_floats = lp.str_off + 4 * 3 * 32;
     const size_t kStatic = 2048;  // the kernel's static shared memory (target table) + slack
     const int cspw = std::max(csw[0], csw[1]);
     const size_t warp_bytes =
-        ((((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) + stage) * 4;
+        ((((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) + stage + 4 * 3 * 32) * 4;
     // as many warps as asked for (default: the most the registers allow) whose rings fit
     const int max_warps = gk == 0 ? kLeanWarps : 16;
     const int fit = (int)std::min<size_t>(max_warps, ((size_t)smem_blk - kStatic) / warp_bytes);

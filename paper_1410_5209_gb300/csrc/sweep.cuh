@@ -273,7 +273,8 @@ struct LeanParams {
     int ring_floats;   // floats per warp ring (pool slots, own-row buffers)
     int slot_floats;   // floats of one pool slot
     int own_off;       // float offset of the own-row buffers within a warp ring
-    int list_off;      // end of the own-row buffers within a warp ring
+    int list_off;      // end of the own-row buffers within a warp ring (tensor-core staging)
+    int str_off;       // stream ring (words, residuals, list entries) within a warp ring
 };
 
 struct LeanPlan {
