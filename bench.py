@@ -649,6 +649,74 @@ def serve_with_jobs(args, f, p, lam):
                     "against free device memory, in real time"}
 
 
+def serve_beside_large_job(args, f, p, K, C, lam, sm_limits=(0, 144)):
+    """Fold-ins against the frozen model `f` (through the serving loop, continuous batching
+    on a high-priority stream) while a second context of the same size (the 1e8-entry
+    tensor, K = 100, C = 10) sweeps back to back on its own low-priority stream from another
+    host thread: fold-in p50 / p99 and the concurrent sweep's rate, for each SM limit of
+    the sweeping context (0: every SM)."""
+    import numpy as np
+    import torch
+    import paper_1410_5209_gb300 as tf
+    import synth
+    reqs = synth.foldin_requests(p, args.serve_large_requests, args.seed + 61)
+    js = torch.cuda.Stream(priority=0)   # the least urgent priority
+    g = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed + 1, dtype=tf.F32,
+                         stream=js.cuda_stream, device_input=True)
+    g.sweep(C, lam, 1)
+    g.sync()
+    out = {}
+    for lim in sm_limits:
+        g.set_sm_limit(max(lim, 0))
+        g.sweep(C, lam, 1)
+        g.sync()
+        srv = tf.Server(f, max_batch=args.serve_batch, reserve_sms=-1)
+        for o, v in reqs[:8]:
+            srv.wait_foldin(srv.submit_foldin(0, o, v, lam))
+        stop = threading.Event()
+        sweeps = []
+
+        def sweeper():
+            while not stop.is_set():
+                t0 = time.perf_counter()
+                g.sweep(C, lam, 1)
+                g.sync()
+                sweeps.append(time.perf_counter() - t0)
+
+        th = threading.Thread(target=sweeper)
+        if lim >= 0:
+            th.start()
+            time.sleep(0.05)
+        rng = np.random.default_rng(args.seed + 67)
+        ta = np.cumsum(rng.exponential(1.0 / args.serve_large_rate, len(reqs)))
+        t0 = time.perf_counter()
+        ids = []
+        for i, t in enumerate(ta):
+            while time.perf_counter() - t0 < t:
+                pass
+            ids.append(srv.submit_foldin(0, reqs[i][0], reqs[i][1], lam))
+        lat = np.array([srv.wait_foldin(r)[2] for r in ids])
+        t_f = time.perf_counter() - t0
+        stop.set()
+        if lim >= 0:
+            th.join()
+        srv.close()
+        ms = float(np.median(sweeps) * 1e3) if sweeps else None
+        key = "no_concurrent_sweep" if lim < 0 else f"sm_limit_{lim or 'all'}"
+        out[key] = {
+            "foldin_p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "foldin_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "foldin_req_per_s": len(ids) / t_f, "offered_req_per_s": args.serve_large_rate,
+            "concurrent_sweeps": len(sweeps), "concurrent_sweep_ms_p50": ms,
+            "concurrent_nnz_rank_per_s": (p.nnz * K / (ms / 1e3)) if ms else None}
+    g.close()
+    out["what"] = ("Poisson fold-ins (new mode-1 slices of 10-10,000 entries, K=100) through "
+                   "tf_server against the frozen model while a second 1e8-entry context "
+                   "(K=100, C=10) sweeps back to back on another stream; sm_limit = blocks of "
+                   "its persistent mode passes (tf_set_sm_limit)")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -662,6 +730,10 @@ def main():
     ap.add_argument("--configs", type=int, default=1,
                     help="also run the precision forms, the batched and the five-way configs")
     ap.add_argument("--batched-tensors", type=int, default=4096)
+    ap.add_argument("--serve-large-requests", type=int, default=1500)
+    ap.add_argument("--serve-large-rate", type=float, default=5000.0)
+    ap.add_argument("--serve-large-sm-limits", default="-1,0,144,112,96",
+                    help="SM limits of the concurrently sweeping context (-1: no sweep)")
     ap.add_argument("--fiveway-nnz", type=int, default=500_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -855,6 +927,9 @@ def main():
                           "through tf_foldin_batch (latency = arrival -> rows on host)"}
         if args.serve_jobs > 0:
             out["serving_server"] = serve_with_jobs(args, f, p, lam)
+    if args.serve_large_requests > 0 and world == 1:
+        out["serving_beside_large_job"] = serve_beside_large_job(
+            args, f, p, K, C, lam, [int(v) for v in args.serve_large_sm_limits.split(",")])
     f.close()
     del f
     if args.configs and rank == 0 and world == 1:

@@ -308,6 +308,13 @@ tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
  * tensor-core Gram rounds its products differently, both agreeing to FP32 rounding. */
 tf_status tf_set_kernel_path(tf_ctx *ctx, int path);
 
+/* Blocks of this context's persistent mode passes (each holds an SM for the whole pass):
+ * at most `sms` (0 = one per SM, the default).  A serving process gives its factorisation
+ * jobs a limit below the SM count so that kernels on other streams (fold-ins) find SMs
+ * free at any time instead of waiting for a pass to end.  Results do not depend on it.
+ * TF_EINVAL for sms < 0.  No counterpart in the paper. */
+tf_status tf_set_sm_limit(tf_ctx *ctx, int sms);
+
 /* Shared-memory layout of the lean pass (kernel path 0 or 3): at most max_rows rows of
  * each other mode's slice are held in shared memory per launch (< 0: as many as fit, the
  * rows with the most entries first; 0: none); the distinct rows outside that cache that a

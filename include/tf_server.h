@@ -46,6 +46,9 @@ typedef struct {
     int max_bypass;      /* times a queued job may be passed by later jobs that fit when it
                             does not (first fit in arrival order); then admission waits for
                             it.  0 = 8, < 0 = never pass (strict arrival order) */
+    int reserve_sms;     /* SMs the jobs' persistent mode passes leave free (tf_set_sm_limit)
+                            so that fold-in kernels start without waiting for a pass to end;
+                            0 = 8 when a model is served (none otherwise), < 0 = none */
 } tf_server_config;
 
 typedef struct {

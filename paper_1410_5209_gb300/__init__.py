@@ -81,6 +81,7 @@ def load():
         "tf_set_schedule": [P, i32, i32],
         "tf_set_kernel_path": [P, i32],
         "tf_set_pass_cache": [P, i32, i32, i32],
+        "tf_set_sm_limit": [P, i32],
         "tf_set_precision": [P, i32],
         "tf_set_stream": [P, P],
         "tf_profile": [P, i32],
@@ -316,6 +317,10 @@ class Factorization:
     def set_kernel_path(self, path):
         self._check(self._lib.tf_set_kernel_path(self._ctx, int(path)))
 
+    def set_sm_limit(self, sms=0):
+        """Blocks of the persistent mode passes (0: one per SM); leaves SMs to other streams."""
+        self._check(self._lib.tf_set_sm_limit(self._ctx, int(sms)))
+
     def set_pass_cache(self, max_rows=-1, pool_rows=32, warps=0):
         """Lean pass: cached rows per other mode (< 0 as fit, 0 none), staged rows per
         step, warps per block (0 default)."""
@@ -472,7 +477,7 @@ def pool_trim(keep_bytes=0):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("hbm_reserve", ctypes.c_int64),
                 ("max_running", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("max_bypass", ctypes.c_int)]
+                ("max_bypass", ctypes.c_int), ("reserve_sms", ctypes.c_int)]
 
 
 class JobDesc(ctypes.Structure):
@@ -512,10 +517,10 @@ class Server:
     requests against `model` (a Factorization, owned by the server until close())."""
 
     def __init__(self, model=None, hbm_budget=0, hbm_reserve=0, max_running=0, max_batch=0,
-                 max_bypass=0):
+                 max_bypass=0, reserve_sms=0):
         self._lib = load()
         cfg = ServerConfig(int(hbm_budget), int(hbm_reserve), int(max_running),
-                           int(max_batch), int(max_bypass))
+                           int(max_batch), int(max_bypass), int(reserve_sms))
         self._srv = ctypes.c_void_p()
         self.model = model
         st = self._lib.tf_server_create(ctypes.byref(cfg), model._ctx if model else None,

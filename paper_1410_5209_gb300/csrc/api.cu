@@ -176,6 +176,8 @@ struct Impl : CtxBase {
     cudaStream_t st = nullptr;
     uint64_t seed = 0;
     int num_sms = 0;
+    int sm_limit = 0;  // blocks of the persistent mode passes (0: one per SM)
+    int pass_sms() const { return sm_limit > 0 && sm_limit < num_sms ? sm_limit : num_sms; }
     tf_sched_policy policy = TF_SCHED_LPT;
     int P = 0;
 
@@ -889,7 +891,7 @@ struct Impl : CtxBase {
                             const bool tc = sizeof(T) == 4 && path != 1 &&
                                             (path == 2 || precision == 1 ||
                                              wide_split_width(Cs, CM) == 128);
-                            const int wgrid = pass_wide_grid<T>(num_sms, L.P, Cs, CM, tc, t == 0);
+                            const int wgrid = pass_wide_grid<T>(pass_sms(), L.P, Cs, CM, tc, t == 0);
                             // every block takes one ticket past the last bin
                             ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
                             timed(TF_KIND_MODE_PASS,
@@ -933,7 +935,7 @@ struct Impl : CtxBase {
                             LeanPlan plan{};
                             bool lean_here = use_lean;
                             if (lean_here) {
-                                plan = lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, num_sms, L.P,
+                                plan = lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, pass_sms(), L.P,
                                                       lean_cache_rows, lean_ring_cap, lean_warps, gk);
                                 lean_here = path != 0 || plan.coverage >= 0.25;
                             }
@@ -955,7 +957,7 @@ struct Impl : CtxBase {
                                 const bool before[2] = {L.omode[0] < n, L.omode[1] < n};
                                 const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
                                 const TmaPlan plan =
-                                    tma_pass_plan(CM, t == 0, before, dims_o, num_sms, L.P);
+                                    tma_pass_plan(CM, t == 0, before, dims_o, pass_sms(), L.P);
 
                                 const int bidx[2] = {
                                     plan.box[0] == 8 ? 0 : (plan.box[0] == 24 ? 1 : 2),
@@ -973,7 +975,7 @@ struct Impl : CtxBase {
                             }
                         }
                     {
-                        const PassPlan plan = mode_pass_plan<T>(CM, N, n, t == 0, num_sms, L.P);
+                        const PassPlan plan = mode_pass_plan<T>(CM, N, n, t == 0, pass_sms(), L.P);
                         // every launched warp takes one ticket past the last bin
                         ticket_base += (unsigned long long)L.P +
                                        (unsigned long long)plan.grid * plan.warps;
@@ -2047,6 +2049,14 @@ tf_status tf_set_kernel_path(tf_ctx *ctx, int path) {
     if (path < 0 || path > 4) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         c.path = path;
+        c.drop_graphs();
+    });
+}
+
+tf_status tf_set_sm_limit(tf_ctx *ctx, int sms) {
+    if (sms < 0) return TF_EINVAL;
+    return dispatch(ctx, [&](auto &c) {
+        c.sm_limit = sms;
         c.drop_graphs();
     });
 }

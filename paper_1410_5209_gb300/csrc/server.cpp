@@ -179,6 +179,11 @@ void tf_server::run_job(std::shared_ptr<Job> j) {
     if (s == TF_OK)
         s = tf_create(j->coords.data(), j->values.data(), j->d.dtype, j->dims.data(), j->d.N,
                       j->d.nnz, j->d.K, j->d.seed, j->stream, 0, &ctx);
+    if (s == TF_OK && cfg.reserve_sms > 0) {  // SMs left free for the fold-ins
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        s = tf_set_sm_limit(ctx, std::max(1, sms - cfg.reserve_sms));
+    }
     // the host copies of the inputs are no longer needed
     std::vector<int32_t>().swap(j->coords);
     std::vector<char>().swap(j->values);
@@ -353,6 +358,7 @@ tf_status tf_server_create(const tf_server_config *cfg, tf_ctx *model, tf_server
     if (c.max_running == 0) c.max_running = 8;
     if (c.max_batch == 0) c.max_batch = 256;
     if (c.max_bypass == 0) c.max_bypass = 8;
+    if (c.reserve_sms == 0) c.reserve_sms = model ? 8 : -1;
     auto s = std::make_unique<tf_server>();
     s->cfg = c;
     s->t0 = Clock::now();

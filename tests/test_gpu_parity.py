@@ -411,6 +411,26 @@ def test_lean_pass_row_sources_bit_identical(C):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("dt", [tf.F32, tf.F64])
+def test_sm_limit_does_not_change_results(dt):
+    """tf_set_sm_limit only caps how many blocks the persistent mode passes launch: the
+    same bins are processed, each by one warp, so results are bit-identical."""
+    p = synth.small(77, (900, 700, 60), 80_000, 4, 20, modes=["zipf", "zipf", "uniform"])
+    out = []
+    for lim in (0, 7, 1):
+        f, _, _ = make(p, dt)
+        f.set_sm_limit(lim)
+        for s in range(2):
+            f.sweep(10 if s == 0 else 20, 0.1, 1, p.column_order(s, 10 if s == 0 else 20))
+        out.append([f.factors(n) for n in range(3)] + [np.array(f.loss(0.1))])
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
+    f, _, _ = make(p, dt)
+    with pytest.raises(tf.TFError):
+        f.set_sm_limit(-1)
+
+
 def test_deterministic_rerun_fp32():
     p = synth.small(34, (300, 300, 30), 50_000, 3, 10, modes=["zipf", "uniform", "uniform"])
     res = []
