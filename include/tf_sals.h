@@ -52,6 +52,9 @@ typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
 
 /* tf_create flags */
 #define TF_INPUT_DEVICE 1u  /* coords and values are device pointers (same device) */
+#define TF_LAYOUT_FIELD_SORTS 2u  /* build the layout by per-mode sorts of gathered
+                                     coordinates even where one 64-bit key holds them
+                                     all (same layout, slower; for comparison) */
 #define TF_KEEP_DEFAULT_INIT 0u
 
 /* per-sweep flags (tf_sals_sweep_ex) */
@@ -92,7 +95,11 @@ typedef struct {
  * Builds, on the device, the per-mode sorted layout (Omega_i^(n) of the table of
  * symbols, entries of a row in lexicographic order of the remaining coordinates taken
  * cyclically from mode n), with bit-exact row offsets; validates coordinates
- * (TF_ERANGE) and the set property (TF_EDUP); schedules rows onto bins (LPT).
+ * (TF_ERANGE) and the set property (TF_EDUP); schedules rows onto bins (LPT).  Where
+ * the modes' index widths, ceil(log2 I_n), sum to at most 64, every entry's coordinates
+ * travel as one 64-bit key through the sorts; otherwise (or with TF_LAYOUT_FIELD_SORTS)
+ * each sort gathers one mode's indices through the permutation so far.  Both give the
+ * same layout.  flags: TF_INPUT_DEVICE, TF_LAYOUT_FIELD_SORTS; other bits TF_EINVAL.
  * Initialises the factors as Algorithm 1 does: A^(1) = 0 and A^(n>1) i.i.d. normal
  * with std K^(-1/(2N)) from `seed`, so that R = X.  *out is NULL on failure. */
 tf_status tf_create(const int32_t *coords, const void *values, tf_dtype dtype,
@@ -392,7 +399,8 @@ tf_status tf_plan_mode(const int64_t *off, int64_t I, int P, int64_t cap,
  * sweeps, whichever is larger), counting the stream-ordered pool's rounding.  Fold-in and
  * predict staging are not included (they grow with the requests).  No counterpart in the
  * paper: a serving process admits jobs against free device memory with it.
- *   dims [N], N, nnz, K, dtype, flags   as for tf_create (flags: TF_INPUT_DEVICE or 0)
+ *   dims [N], N, nnz, K, dtype, flags   as for tf_create (TF_INPUT_DEVICE,
+ *                                       TF_LAYOUT_FIELD_SORTS)
  *   C_max    largest C of the sweeps to come, 1..min(K, 127)
  *   num_sms  the device's SM count (> 0: no device needed), <= 0: asked of the device
  * TF_EINVAL for arguments tf_create or tf_sals_sweep would refuse. */

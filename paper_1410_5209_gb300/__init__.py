@@ -23,6 +23,7 @@ STATUS_NAMES = ["TF_OK", "TF_EINVAL", "TF_ERANGE", "TF_EDUP", "TF_ENOMEM", "TF_E
                 "TF_ETIMEOUT", "TF_EBUSY"]
 F32, F64 = 0, 1
 INPUT_DEVICE = 1
+LAYOUT_FIELD_SORTS = 2   # tf_create: per-mode sorts of gathered coordinates
 WEIGHTED_LAMBDA = 1
 SCHED_LPT, SCHED_GREEDY, SCHED_SEQ, SCHED_RAN = 0, 1, 2, 3
 
@@ -156,10 +157,12 @@ class Factorization:
 
     coords [nnz, N] int32 and values [nnz] as numpy arrays (host) or, with
     device_input=True, as CUDA torch tensors.  dtype F32 or F64 selects the device
-    arithmetic.  stream: a cudaStream_t handle as int (None = default stream)."""
+    arithmetic.  stream: a cudaStream_t handle as int (None = default stream).
+    field_sorts=True builds the layout by per-mode sorts of gathered coordinates
+    (TF_LAYOUT_FIELD_SORTS) instead of packed keys; the layout is the same."""
 
     def __init__(self, coords, values, dims, K, seed=0, dtype=F32, stream=None,
-                 device_input=False):
+                 device_input=False, field_sorts=False):
         self._lib = load()
         self.dims = [int(d) for d in dims]
         self.N = len(self.dims)
@@ -184,6 +187,8 @@ class Factorization:
             flags = 0
             keep = (coords, values)
         self.nnz = nnz
+        if field_sorts:
+            flags |= LAYOUT_FIELD_SORTS
         st = self._lib.tf_create(cp, vp, int(dtype), _ptr(dims_a), self.N, nnz, self.K,
                                  ctypes.c_uint64(seed), ctypes.c_void_p(stream or 0), flags,
                                  ctypes.byref(ctx))

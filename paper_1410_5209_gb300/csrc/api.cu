@@ -17,6 +17,7 @@
 
 #include <cuda.h>
 
+#include "layout.cuh"
 #include "sweep.cuh"
 
 namespace tfs {
@@ -160,6 +161,11 @@ struct ModeLayout {
             f(id_of), f(groups);
     }
 };
+
+// The packed-key layout build applies when one 64-bit key holds every coordinate.
+inline bool packed_layout_applies(const int64_t *dims, int N, int64_t nnz, uint32_t flags) {
+    return !(flags & TF_LAYOUT_FIELD_SORTS) && nnz > 0 && packed_key_bits(dims, N) <= 64;
+}
 
 struct CtxBase {
     std::string err;
@@ -331,6 +337,23 @@ struct Impl : CtxBase {
         }
     }
 
+    // A mode's row schedule on the host (items grouped by bin, split and single rows).
+    struct PlanHost {
+        std::vector<tf_item> items;
+        std::vector<int64_t> bin_ptr;
+        std::vector<SplitRow> split, single;
+        std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
+        int64_t n_slots = 0;
+    };
+
+    // Host vectors whose device copies are queued on st during the build: they live
+    // until create synchronises.
+    struct BuildHost {
+        std::vector<PlanHost> plans;
+        std::vector<std::vector<int64_t>> offs;
+        std::vector<std::vector<int32_t>> ids, ranks;
+    };
+
     // ------------------------------------------------------------ construction
     void create(const int32_t *coords, const void *values, const int64_t *dims_in, int N_,
                 int64_t nnz_, int K_, uint64_t seed_, cudaStream_t st_, uint32_t flags) {
@@ -362,9 +385,44 @@ struct Impl : CtxBase {
         const bool on_dev = flags & TF_INPUT_DEVICE;
         const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         x.alloc(nnz, st);
-        if (nnz > 0)
-            TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), kind, st));
+        const bool packed = packed_layout_applies(dims.data(), N, nnz, flags);
+        BuildHost bh;
+        if (packed) {
+            build_packed(coords, values, on_dev, bh);
+        } else {
+            if (nnz > 0) TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), kind, st));
+            build_general(coords, on_dev, bh);
+        }
+        for (int n = 0; n < N; ++n) plan_upload(n, bh.plans[n]);
 
+        // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
+        const double std = pow((double)K, -1.0 / (2.0 * N));
+        for (int n = 0; n < N; ++n) {
+            A[n].alloc((size_t)dims[n] * K, st);
+            if (n == 0)
+                TFS_CUDA(cudaMemsetAsync(A[n].p, 0, (size_t)dims[n] * K * sizeof(T), st));
+            else
+                launch_init_normal<T>(A[n].p, dims[n] * K, seed, (uint64_t)n, std, st);
+        }
+        a0_zero = true;
+        if (packed) {  // the sorts carried X into every residual copy (R = X)
+            Cq = 0;
+            dirty = false;
+        } else {
+            for (int n = 0; n < N; ++n) {
+                res[n].alloc(nnz + 64, st);
+                TFS_CUDA(cudaMemsetAsync(res[n].p, 0, (nnz + 64) * sizeof(T), st));
+            }
+            rebuild_residuals();
+        }
+        TFS_CUDA(cudaStreamSynchronize(st));  // host copies of the schedules and tables read
+    }
+
+    // Per-mode sorted layout by key sorts of gathered coordinates: mode 0's order by N
+    // stable sorts of one mode's indices each (least significant mode first), every other
+    // mode's by one stable sort of the next mode's order; used where the coordinates do
+    // not fit one 64-bit key (or on request, TF_LAYOUT_FIELD_SORTS).
+    void build_general(const int32_t *coords, bool on_dev, BuildHost &bh) {
         // canonical coordinates -> SoA with range check
         Buf<int32_t> soa;
         soa.alloc((size_t)N * nnz, st);
@@ -424,27 +482,15 @@ struct Impl : CtxBase {
             // degree ranks: slices are stored with each mode's rows in decreasing order of
             // their entry counts (equal counts by row id); one host thread per mode
             offs = download_offsets();
-            std::vector<std::vector<int32_t>> ids((size_t)N), ranks((size_t)N);
-            {
-                std::vector<std::thread> th;
-                for (int n = 0; n < N; ++n)
-                    th.emplace_back([&, n] {
-                        const int64_t I = mode[n].I;
-                        std::vector<int64_t> cnt((size_t)I);
-                        for (int64_t i = 0; i < I; ++i) cnt[i] = offs[n][i + 1] - offs[n][i];
-                        const std::vector<int64_t> order = rows_by_degree(cnt);
-                        ids[n].resize((size_t)I);
-                        ranks[n].resize((size_t)I);
-                        std::vector<int64_t> &dc = mode[n].deg_cum;
-                        dc.assign((size_t)I + 1, 0);
-                        for (int64_t r = 0; r < I; ++r) {
-                            ids[n][r] = (int32_t)order[r];
-                            ranks[n][order[r]] = (int32_t)r;
-                            dc[r + 1] = dc[r] + cnt[order[r]];
-                        }
-                    });
-                for (auto &t : th) t.join();
-            }
+            std::vector<std::vector<int32_t>> &ids = bh.ids, &ranks = bh.ranks;
+            ids.assign((size_t)N, {});
+            ranks.assign((size_t)N, {});
+            run_per_mode([&](int n) {
+                const int64_t I = mode[n].I;
+                std::vector<int64_t> cnt((size_t)I);
+                for (int64_t i = 0; i < I; ++i) cnt[i] = offs[n][i + 1] - offs[n][i];
+                degree_order(n, cnt, ids[n], ranks[n]);
+            });
             for (int n = 0; n < N; ++n) {
                 ModeLayout &L = mode[n];
                 L.id_of.alloc(L.I, st);
@@ -473,7 +519,6 @@ struct Impl : CtxBase {
             }
             // the row schedules, on the host while the device gathers the index streams
             plans = plan_all_host(offs);
-            TFS_CUDA(cudaStreamSynchronize(st));  // ids / ranks uploaded
         } catch (...) {
             ws.release(st);
             throw;
@@ -482,34 +527,255 @@ struct Impl : CtxBase {
         keys.reset();
         soa.reset();
 
-        for (int n = 0; n < N; ++n) plan_upload(n, plans[n]);
+        bh.plans = std::move(plans);
+        bh.offs = std::move(offs);
+    }
 
-        // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
-        const double std = pow((double)K, -1.0 / (2.0 * N));
-        for (int n = 0; n < N; ++n) {
-            A[n].alloc((size_t)dims[n] * K, st);
-            if (n == 0)
-                TFS_CUDA(cudaMemsetAsync(A[n].p, 0, (size_t)dims[n] * K * sizeof(T), st));
-            else
-                launch_init_normal<T>(A[n].p, dims[n] * K, seed, (uint64_t)n, std, st);
-            res[n].alloc(nnz + 64, st);
-            TFS_CUDA(cudaMemsetAsync(res[n].p, 0, (nnz + 64) * sizeof(T), st));
+    // Per-mode sorted layout from packed 64-bit keys (layout.cu).  The row counts come
+    // from the packing pass; while the device sorts mode 0's keys the host turns them
+    // into row offsets and degree ranks (one thread per mode), then schedules the rows
+    // while the device sorts the other modes and extracts every mode's arrays.
+    void build_packed(const int32_t *coords, const void *values, bool on_dev, BuildHost &bh) {
+        const KeyFields f = key_fields(dims.data(), N);
+        const int total_bits = packed_key_bits(dims.data(), N);
+        int64_t sum_I = 0;
+        for (int n = 0; n < N; ++n) sum_I += dims[n];
+        Buf<uint64_t> kb[3];
+        Buf<uint32_t> cnt;
+        kb[0].alloc(nnz, st);
+        cnt.alloc(sum_I, st);
+        TFS_CUDA(cudaMemsetAsync(cnt.p, 0, sum_I * sizeof(uint32_t), st));
+        Buf<int32_t> rowmajor;
+        // Host inputs: the coordinates go up in chunks on a side stream and each chunk is
+        // packed on st as soon as it has landed; the values go up behind them and are
+        // first needed by mode 0's extraction, after mode 0's sort.  The side stream is
+        // drained before anything it writes is freed (also when the build fails).
+        struct Side {
+            cudaStream_t s = nullptr;
+            std::vector<cudaEvent_t> ev;
+            cudaEvent_t make() {
+                cudaEvent_t e = nullptr;
+                TFS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                ev.push_back(e);
+                return e;
+            }
+            ~Side() {
+                if (s) cudaStreamSynchronize(s);
+                for (cudaEvent_t e : ev) cudaEventDestroy(e);
+                if (s) cudaStreamDestroy(s);
+            }
+        } side;
+        cudaEvent_t x_ready = nullptr;
+        if (on_dev) {
+            TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            launch_pack_count(coords, 0, nnz, f, kb[0].p, cnt.p, stat.p, st);
+        } else {
+            rowmajor.alloc((size_t)N * nnz, st);
+            TFS_CUDA(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+            cudaEvent_t allocated = side.make();
+            TFS_CUDA(cudaEventRecord(allocated, st));  // x and rowmajor exist from here on
+            TFS_CUDA(cudaStreamWaitEvent(side.s, allocated, 0));
+            constexpr int64_t kChunks = 8;
+            const int64_t tile = pack_count_tile();
+            const int64_t chunk = std::max<int64_t>(tile, ceil_div(ceil_div(nnz, kChunks), tile) * tile);
+            for (int64_t e0 = 0; e0 < nnz; e0 += chunk) {
+                const int64_t ne = std::min(chunk, nnz - e0);
+                TFS_CUDA(cudaMemcpyAsync(rowmajor.p + (size_t)e0 * N, coords + (size_t)e0 * N,
+                                         (size_t)ne * N * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                         side.s));
+                cudaEvent_t landed = side.make();
+                TFS_CUDA(cudaEventRecord(landed, side.s));
+                TFS_CUDA(cudaStreamWaitEvent(st, landed, 0));
+                launch_pack_count(rowmajor.p + (size_t)e0 * N, e0, ne, f, kb[0].p, cnt.p, stat.p, st);
+            }
+            TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), cudaMemcpyHostToDevice, side.s));
+            x_ready = side.make();
+            TFS_CUDA(cudaEventRecord(x_ready, side.s));
         }
-        a0_zero = true;
-        rebuild_residuals();
-        TFS_CUDA(cudaStreamSynchronize(st));
+        rowmajor.reset();  // st has waited for every chunk
+        // page-locked landing block of the counts; it goes back to the cache only after
+        // the copy into it has completed (also when the build fails)
+        struct CountsHost {
+            uint32_t *p = nullptr;
+            size_t bytes = 0;
+            cudaEvent_t done = nullptr;
+            ~CountsHost() {
+                if (done) cudaEventSynchronize(done);
+                if (p) pinned_cache().put(p, bytes);
+                if (done) cudaEventDestroy(done);
+            }
+        } hc;
+        TFS_CUDA(cudaEventCreateWithFlags(&hc.done, cudaEventDisableTiming));
+        hc.bytes = (size_t)sum_I * sizeof(uint32_t);
+        hc.p = static_cast<uint32_t *>(pinned_cache().get(hc.bytes));
+        uint32_t *h_cnt = hc.p;
+        cudaEvent_t counted = hc.done;
+        TFS_CUDA(cudaMemcpyAsync(h_cnt, cnt.p, sum_I * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        TFS_CUDA(cudaEventRecord(counted, st));
+
+        Buf<int32_t> valt;
+        Buf<T> xalt;
+        KeySortWorkspace ws;
+        struct WsBack {
+            KeySortWorkspace &w;
+            cudaStream_t s;
+            ~WsBack() { w.release(s); }
+        } ws_back{ws, st};
+        for (int n = 0; n < N; ++n) {
+            mode[n].I = dims[n];
+            mode[n].perm.alloc(nnz, st);
+            // residual copies: R = X at the start (A^(1) = 0): mode 0's gathered, the others'
+            // carried with the keys from the previous mode's copy; 64 zero entries after them
+            res[n].alloc(nnz + 64, st);
+            TFS_CUDA(cudaMemsetAsync(res[n].p + nnz, 0, 64 * sizeof(T), st));
+        }
+        kb[1].alloc(nnz, st);
+        kb[2].alloc(nnz, st);
+        valt.alloc(nnz, st);
+        xalt.alloc(nnz, st);
+        // mode 0: the whole key, most significant field i_0
+        radix_sort_keys64(kb[0].p, nullptr, nullptr, kb[1].p, mode[0].perm.p, nullptr, kb[2].p,
+                          valt.p, nullptr, 0, nnz, 0, total_bits, ws, st);
+
+        // row offsets and degree ranks on the host while the sort runs
+        TFS_CUDA(cudaEventSynchronize(counted));
+        bh.offs.assign((size_t)N, {});
+        bh.ids.assign((size_t)N, {});
+        bh.ranks.assign((size_t)N, {});
+        run_per_mode([&](int n) {
+            const int64_t I = dims[n];
+            const uint32_t *c = h_cnt + f.cnt_off[n];
+            std::vector<int64_t> count((size_t)I);
+            std::vector<int64_t> &off = bh.offs[n];
+            off.assign((size_t)I + 1, 0);
+            for (int64_t i = 0; i < I; ++i) {
+                count[i] = c[i];
+                off[i + 1] = off[i] + c[i];
+            }
+            degree_order(n, count, bh.ids[n], bh.ranks[n]);
+        });
+        for (int n = 0; n < N; ++n) {
+            ModeLayout &L = mode[n];
+            L.off.alloc(L.I + 1, st);
+            L.id_of.alloc(L.I, st);
+            L.rank_of.alloc(L.I, st);
+            TFS_CUDA(cudaMemcpyAsync(L.off.p, bh.offs[n].data(), (L.I + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+            TFS_CUDA(cudaMemcpyAsync(L.id_of.p, bh.ids[n].data(), L.I * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+            TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, bh.ranks[n].data(), L.I * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+        }
+        // the schedules on host threads while the device continues
+        bh.plans.assign((size_t)N, {});
+        std::vector<std::exception_ptr> plan_err((size_t)N);
+        std::vector<std::thread> planners;
+        struct Joiner {
+            std::vector<std::thread> &t;
+            ~Joiner() {
+                for (auto &x : t)
+                    if (x.joinable()) x.join();
+            }
+        } join_planners{planners};
+        for (int n = 0; n < N; ++n)
+            planners.emplace_back([&, n] {
+                try {
+                    bh.plans[n] = plan_host(bh.offs[n], dims[n]);
+                } catch (...) {
+                    plan_err[n] = std::current_exception();
+                }
+            });
+
+        for (int n = 0; n < N; ++n) {
+            ModeLayout &L = mode[n];
+            L.ostride = (nnz + 64 + 63) / 64 * 64;
+            L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride, st);
+            TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0,
+                                     (size_t)std::max(N - 1, 1) * L.ostride * sizeof(int32_t), st));
+            int t = 0;
+            for (int l = 0; l < N; ++l)
+                if (l != n) L.omode[t++] = l;
+        }
+        auto extract = [&](int n, const uint64_t *keys) {
+            const ModeLayout &L = mode[n];
+            ExtractArgs a{};
+            a.n_other = N - 1;
+            a.check_dup = n == 0 ? 1 : 0;
+            for (int t = 0; t < N - 1; ++t) {
+                const int l = L.omode[t];
+                a.shift[t] = f.shift[l];
+                a.bits[t] = f.bits[l];
+                a.oidx[t] = L.oidx.p + (size_t)t * L.ostride;
+                a.rank[t] = mode[l].rank_of.p;
+            }
+            if (n == 0) {  // R = X into mode 0's order; later modes' values come with their keys
+                a.perm = L.perm.p;
+                a.x = x.p;
+                a.res = res[0].p;
+                a.xbytes = (int)sizeof(T);
+            }
+            launch_extract(keys, nnz, a, stat.p, st);
+        };
+        if (x_ready) TFS_CUDA(cudaStreamWaitEvent(st, x_ready, 0));
+        int cur = 1;
+        extract(0, kb[cur].p);
+        // mode n from mode n+1: a stable sort by the field i_n
+        for (int n = N - 1; n >= 1; --n) {
+            const int out = cur == 0 ? 1 : 0, alt = 3 - cur - out;
+            radix_sort_keys64(kb[cur].p, mode[(n + 1) % N].perm.p, res[(n + 1) % N].p, kb[out].p,
+                              mode[n].perm.p, res[n].p, kb[alt].p, valt.p, xalt.p, (int)sizeof(T),
+                              nnz, f.shift[n], f.shift[n] + f.bits[n], ws, st);
+            cur = out;
+            extract(n, kb[cur].p);
+        }
+        for (auto &t : planners) t.join();
+        for (auto &e : plan_err)
+            if (e) std::rethrow_exception(e);
+        const DeviceStatus s = read_status();
+        if (s.bits & kStatRange)
+            throw ApiError{TF_ERANGE, "a coordinate is negative or not below its mode length"};
+        if (s.bits & kStatDup)
+            throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
+    }
+
+    // Rows of mode n in decreasing order of entry count, equal counts by row id: ids[r]
+    // is the row at degree rank r, ranks its inverse; also the mode's cumulative counts
+    // in that order (deg_cum).
+    void degree_order(int n, const std::vector<int64_t> &count, std::vector<int32_t> &ids,
+                      std::vector<int32_t> &ranks) {
+        const int64_t I = (int64_t)count.size();
+        const std::vector<int64_t> order = rows_by_degree(count);
+        ids.resize((size_t)I);
+        ranks.resize((size_t)I);
+        std::vector<int64_t> &dc = mode[n].deg_cum;
+        dc.assign((size_t)I + 1, 0);
+        for (int64_t r = 0; r < I; ++r) {
+            ids[r] = (int32_t)order[r];
+            ranks[order[r]] = (int32_t)r;
+            dc[r + 1] = dc[r] + count[order[r]];
+        }
+    }
+
+    // f(n) for every mode on its own host thread; the first exception is rethrown.
+    template <class F>
+    void run_per_mode(F &&f) {
+        std::vector<std::exception_ptr> errs((size_t)N);
+        std::vector<std::thread> th;
+        for (int n = 0; n < N; ++n)
+            th.emplace_back([&, n] {
+                try {
+                    f(n);
+                } catch (...) {
+                    errs[n] = std::current_exception();
+                }
+            });
+        for (auto &t : th) t.join();
+        for (auto &e : errs)
+            if (e) std::rethrow_exception(e);
     }
 
     // Row schedule of one mode, computed on the host from its row offsets (no device call,
     // so the modes' schedules can be computed in parallel threads).
-    struct PlanHost {
-        std::vector<tf_item> items;
-        std::vector<int64_t> bin_ptr;
-        std::vector<SplitRow> split, single;
-        std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
-        int64_t n_slots = 0;
-    };
-
     PlanHost plan_host(const std::vector<int64_t> &off, int64_t I) const {
         PlanHost h;
         tf_status s = plan_mode(off.data(), I, P, 0, policy, seed, h.items, h.n_slots, h.bin_ptr);
@@ -1717,8 +1983,10 @@ tf_status tf_create(const int32_t *coords, const void *values, tf_dtype dtype, c
     *out = nullptr;
     g_create_err.clear();
     if (N < 1 || N > tfs::kMaxModes || nnz < 0 || nnz > INT32_MAX || K < 1 || !dims ||
-        (nnz > 0 && (!coords || !values)) || (dtype != TF_F32 && dtype != TF_F64)) {
-        g_create_err = "invalid argument (N in 1..8, 0 <= nnz < 2^31, K >= 1, buffers non-NULL)";
+        (nnz > 0 && (!coords || !values)) || (dtype != TF_F32 && dtype != TF_F64) ||
+        (flags & ~(TF_INPUT_DEVICE | TF_LAYOUT_FIELD_SORTS))) {
+        g_create_err = "invalid argument (N in 1..8, 0 <= nnz < 2^31, K >= 1, buffers non-NULL, "
+                       "known flags)";
         return TF_EINVAL;
     }
     for (int n = 0; n < N; ++n)
@@ -1917,8 +2185,23 @@ tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int 
     const double base = 4096.0 * 8 + 2.0 * K * 4 + N * 8 + 1024;
     const double x = e * T, soa = (double)N * e * 4;
     const double host_copy = (flags & TF_INPUT_DEVICE) ? 0.0 : (double)N * e * 4;
-    const double transpose = x + soa + host_copy;
-    const double sorting = x + soa + e * 4 + (double)tfs::sort_workspace_bytes(nnz) + layout;
+    double transpose, sorting;
+    if (tfs::packed_layout_applies(dims, N, nnz, flags)) {
+        // packing: the values, the row-major copy, the keys and the row counts; sorting
+        // and extraction: three key buffers, the spare permutation and values, the sort
+        // scratch, the layout and the residual copies
+        double sum_I = 0, res = 0;
+        for (int n = 0; n < N; ++n) {
+            sum_I += (double)dims[n];
+            res += (e + 64) * T;
+        }
+        transpose = x + host_copy + e * 8 + sum_I * 4;
+        sorting = x + 3 * e * 8 + e * 4 + e * T + (double)tfs::key_sort_workspace_bytes(nnz) +
+                  sum_I * 4 + layout + res;
+    } else {
+        transpose = x + soa + host_copy;
+        sorting = x + soa + e * 4 + (double)tfs::sort_workspace_bytes(nnz) + layout;
+    }
     const double partials = (maxI + P) * tfs::partial_stride(CM) * T;
     // gather plans of the lean float pass (three-way tensors), one per mode: a location
     // word per entry, at most two list entries per entry, at most three records per

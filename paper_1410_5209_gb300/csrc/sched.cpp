@@ -38,11 +38,12 @@ struct BinKey {
 };
 using MinHeap = std::priority_queue<BinKey, std::vector<BinKey>, std::greater<BinKey>>;
 
-// Rows in decreasing length, equal lengths in increasing index: one sort of packed keys
-// (length in the high 32 bits, complemented; index in the low 32 bits).
+// Rows in decreasing length, equal lengths in increasing index.  Short lengths take one
+// counting sort; otherwise a least-significant-digit radix sort of the complemented
+// lengths (11-bit digits, stable, so equal lengths stay in index order), skipping digits
+// that every key shares.  Lengths beyond 32 bits take a comparison sort.
 std::vector<int64_t> rows_by_length(const int64_t *len, int64_t I) {
     std::vector<int64_t> order(I);
-    // short lengths (chunked LPT jobs): a counting sort, stable in the index
     int64_t max_len = 0;
     bool nonneg = true;
     for (int64_t i = 0; i < I; ++i) {
@@ -56,19 +57,35 @@ std::vector<int64_t> rows_by_length(const int64_t *len, int64_t I) {
         for (int64_t i = 0; i < I; ++i) order[(size_t)start[(size_t)(max_len - len[i])]++] = i;
         return order;
     }
-    bool packed = I <= (int64_t)UINT32_MAX;
-    for (int64_t i = 0; i < I && packed; ++i) packed = len[i] >= 0 && len[i] <= (int64_t)UINT32_MAX;
-    if (!packed) {
+    if (!nonneg || max_len > (int64_t)UINT32_MAX || I > (int64_t)UINT32_MAX) {
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(),
                          [&](int64_t a, int64_t b) { return len[a] > len[b]; });
         return order;
     }
-    std::vector<uint64_t> key((size_t)I);
-    for (int64_t i = 0; i < I; ++i)
-        key[i] = ((uint64_t)(UINT32_MAX - (uint64_t)len[i]) << 32) | (uint64_t)i;
-    std::sort(key.begin(), key.end());
-    for (int64_t i = 0; i < I; ++i) order[i] = (int64_t)(key[i] & 0xFFFFFFFFull);
+    constexpr int kBits = 11, kBuckets = 1 << kBits;
+    std::vector<uint32_t> key((size_t)I), key2((size_t)I), idx((size_t)I), idx2((size_t)I);
+    for (int64_t i = 0; i < I; ++i) {
+        key[i] = (uint32_t)(UINT32_MAX - (uint64_t)len[i]);
+        idx[i] = (uint32_t)i;
+    }
+    std::vector<int64_t> cnt(kBuckets + 1);
+    for (int shift = 0; shift < 32; shift += kBits) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int64_t i = 0; i < I; ++i) cnt[((key[i] >> shift) & (kBuckets - 1)) + 1] += 1;
+        bool one_bucket = false;
+        for (int d = 0; d < kBuckets; ++d) one_bucket = one_bucket || cnt[d + 1] == I;
+        if (one_bucket) continue;
+        for (int d = 0; d < kBuckets; ++d) cnt[d + 1] += cnt[d];
+        for (int64_t i = 0; i < I; ++i) {
+            const int64_t at = cnt[(key[i] >> shift) & (kBuckets - 1)]++;
+            key2[(size_t)at] = key[i];
+            idx2[(size_t)at] = idx[i];
+        }
+        key.swap(key2);
+        idx.swap(idx2);
+    }
+    for (int64_t i = 0; i < I; ++i) order[i] = (int64_t)idx[i];
     return order;
 }
 

@@ -7,6 +7,8 @@
 #include <map>
 #include <mutex>
 
+#include <type_traits>
+
 #include "sweep.cuh"
 
 namespace tfs {
@@ -125,13 +127,22 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// Box-Muller from two counter-based uniforms per element.  Float factors take 24-bit
+// uniforms and float arithmetic (FP64 transcendentals run at a small fraction of the
+// FP32 rate on this GPU and made the draw a millisecond per 1e7 values).
 template <class T>
 __global__ void k_init_normal(T *A, int64_t count, uint64_t key, double std) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const double u1 = (double)(mix64(key + 2 * (uint64_t)i) >> 11) * 0x1.0p-53;
-    const double u2 = (double)(mix64(key + 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
-    A[i] = (T)(std * sqrt(-2.0 * log1p(-u1)) * cospi(2.0 * u2));
+    if constexpr (std::is_same<T, float>::value) {
+        const float u1 = (float)(mix64(key + 2 * (uint64_t)i) >> 40) * 0x1.0p-24f;
+        const float u2 = (float)(mix64(key + 2 * (uint64_t)i + 1) >> 40) * 0x1.0p-24f;
+        A[i] = (float)std * sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
+    } else {
+        const double u1 = (double)(mix64(key + 2 * (uint64_t)i) >> 11) * 0x1.0p-53;
+        const double u2 = (double)(mix64(key + 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
+        A[i] = (T)(std * sqrt(-2.0 * log1p(-u1)) * cospi(2.0 * u2));
+    }
 }
 
 // One warp per coordinate, lanes over the K columns (coalesced factor rows), FP64 sum.

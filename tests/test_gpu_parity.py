@@ -48,20 +48,91 @@ def ragged_problem(seed=21):
 # --------------------------------------------------------------------------- layout
 
 
+@pytest.mark.parametrize("field_sorts", [False, True])
 @pytest.mark.parametrize("prob", ["parity", "ragged", "skew"])
-def test_grouping_bit_exact(prob):
+def test_grouping_bit_exact(prob, field_sorts):
+    """Both layout builds (packed keys, per-mode sorts of gathered coordinates) against
+    the oracle's grouping."""
     if prob == "parity":
         p = synth.parity_3way()
     elif prob == "ragged":
         p = ragged_problem()
     else:
         p = synth.small(5, (2000, 3000, 50), 60_000, 3, 4, modes=["zipf", "zipf", "uniform"])
-    f, t, _ = make(p)
+    c, x = p.numpy()
+    f = tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F64, field_sorts=field_sorts)
+    t = oracle.Tensor(c, x, p.dims)
     for n in range(p.N):
         off, perm = f.grouping(n)
         ooff, operm = oracle.group(t, n)
         assert np.array_equal(off, ooff)
         assert np.array_equal(perm, operm)
+
+
+@pytest.mark.parametrize("dims,nnz,modes", [
+    # a mode longer than the packing pass's shared count table (8192 rows) with uniform
+    # rows, so a block's table overflows into direct global counts
+    ((100_000, 50, 60), 300_000, ["uniform", "uniform", "uniform"]),
+    # coordinates filling 63 of the key's 64 bits
+    ((1 << 21, 1 << 21, 1 << 21), 40_000, ["uniform", "uniform", "uniform"]),
+    # two modes of one row (no bits in the key) around a third
+    ((1, 7000, 1), 6_000, ["uniform", "uniform", "uniform"]),
+    # four-way with 66 bits of coordinates: the per-mode sorts apply by themselves
+    ((1 << 20, 1 << 20, 1 << 20, 33), 30_000, ["uniform", "zipf", "uniform", "uniform"]),
+])
+def test_layout_extremes_bit_exact(dims, nnz, modes):
+    p = synth.small(61, dims, nnz, 2, 3, modes=modes)
+    c, x = p.numpy()
+    t = oracle.Tensor(c, x, p.dims)
+    f = tf.Factorization(c, x, p.dims, p.K, seed=1, dtype=tf.F64)
+    for n in range(p.N):
+        off, perm = f.grouping(n)
+        ooff, operm = oracle.group(t, n)
+        assert np.array_equal(off, ooff), n
+        assert np.array_equal(perm, operm), n
+    assert np.array_equal(f.residual(), x)
+
+
+def test_layout_builds_give_identical_sweeps():
+    """The packed-key and the per-mode-sort builds give the same layout, so the same
+    sweeps bit for bit (FP32, default schedule, several tiles of every sort)."""
+    p = synth.small(62, (3000, 2500, 80), 250_000, 4, 10, modes=["zipf", "zipf", "uniform"])
+    c, x = p.numpy()
+    out = []
+    for field_sorts in (False, True):
+        f = tf.Factorization(c, x, p.dims, p.K, seed=9, dtype=tf.F32, field_sorts=field_sorts)
+        for s in range(2):
+            f.sweep(5, 0.1, 1, p.column_order(s, 5))
+        out.append(([f.factors(n) for n in range(p.N)], f.residual(), f.loss(0.1)))
+        f.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("field_sorts", [False, True])
+def test_create_errors_across_tiles(field_sorts):
+    """A duplicate pair thousands of entries apart and a coordinate out of range at the
+    last entry, on inputs spanning several tiles of the packing and sorting passes."""
+    p = synth.small(63, (500, 400, 90), 20_000, 2, 3)
+    c, x = p.numpy()
+    d = c.copy()
+    d[17_003] = d[5]
+    with pytest.raises(tf.TFError) as e:
+        tf.Factorization(d, x, p.dims, 3, dtype=tf.F32, field_sorts=field_sorts)
+    assert e.value.status == tf.EDUP
+    r = c.copy()
+    r[-1, 2] = 90
+    with pytest.raises(tf.TFError) as e:
+        tf.Factorization(r, x, p.dims, 3, dtype=tf.F32, field_sorts=field_sorts)
+    assert e.value.status == tf.ERANGE
+    r[-1, 2] = -1
+    with pytest.raises(tf.TFError) as e:
+        tf.Factorization(r, x, p.dims, 3, dtype=tf.F32, field_sorts=field_sorts)
+    assert e.value.status == tf.ERANGE
+    f = tf.Factorization(c, x, p.dims, 3, dtype=tf.F32, field_sorts=field_sorts)
+    assert np.array_equal(f.residual(), x.astype(np.float32))
 
 
 def test_create_validates_coordinates():
