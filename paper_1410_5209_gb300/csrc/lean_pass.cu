@@ -176,17 +176,40 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
     uint32_t ns = 0, nl = 0;
     const uint32_t s0 = g.emit ? g.step_ptr[b] : 0u, l0 = g.emit ? g.list_ptr[b] : 0u;
     const int64_t it0 = g.bin_ptr[b], it1 = g.bin_ptr[b + 1];
-    for (int64_t it = it0; it < it1; ++it) {
-        const tf_item x = g.items[it];
-        const int jend = (int)(x.begin + x.len);
-        int j = (int)x.begin;
+    // The bin's steps in order, the next step's index pair (and the next item's record
+    // and own rank) loaded before the current step is worked on, so a warp keeps two
+    // steps' loads in flight instead of waiting on each.
+    if (it0 < it1) {
+        int64_t it = it0;
+        tf_item x = g.items[it];
+        tf_item xn = it + 1 < it1 ? g.items[it + 1] : x;
+        int own = g.emit && g.first ? g.rank_n[x.row] : 0;
+        int own_n = g.emit && g.first && it + 1 < it1 ? g.rank_n[xn.row] : 0;
+        int j = (int)x.begin, jend = (int)(x.begin + x.len);
         int prevR = -1;  // run index of this lane's previous entry in the item
         bool first = true;
-        const int own = g.emit && g.first ? g.rank_n[x.row] : 0;
-        do {
+        int cV, cR;  // the current step's indices (-1 past its end)
+        {
+            const bool v = lane < min(kWarp, jend - j);
+            cV = v ? g.ixV[j + lane] : -1;
+            cR = v ? g.ixR[j + lane] : -1;
+        }
+        for (;;) {
             const int cmax = min(kWarp, jend - j);
             const bool valid = lane < cmax;
-            const int iV = valid ? g.ixV[j + lane] : -1, iR = valid ? g.ixR[j + lane] : -1;
+            const bool more_in_item = j + cmax < jend;
+            const bool more = more_in_item || it + 1 < it1;
+            // the next step: this item's next 32 entries, or the next item's first
+            int nV = -1, nR = -1;
+            if (more) {
+                const int jn = more_in_item ? j + cmax : (int)xn.begin;
+                const int jnend = more_in_item ? jend : (int)(xn.begin + xn.len);
+                if (lane < min(kWarp, jnend - jn)) {
+                    nV = g.ixV[jn + lane];
+                    nR = g.ixR[jn + lane];
+                }
+            }
+            const int iV = cV, iR = cR;
             const int pV = __shfl_up_sync(0xFFFFFFFFu, iV, 1), pR = __shfl_up_sync(0xFFFFFFFFu, iR, 1);
             const bool coldV = valid && iV >= g.RV;
             const bool need = valid && (first || iR != prevR);
@@ -208,40 +231,57 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
                                                                valid && lane >= lo && upto <= g.cap))
                                    : 0;
                 const uint32_t keep = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & from;
-                const int nV = __popc(hV & keep), nR = __popc(hR & keep);
+                const int nVr = __popc(hV & keep), nRr = __popc(hR & keep);
                 if (g.emit) {
                     if (lane >= lo && lane < hi) {
                         const uint32_t locV =
                             coldV ? (kPoolBit | (uint32_t)(__popc(hV & le) - 1)) : (uint32_t)iV;
                         const uint32_t locR =
                             !need   ? kKeep
-                            : coldR ? (kPoolBit | (uint32_t)(nV + __popc(hR & le) - 1))
+                            : coldR ? (kPoolBit | (uint32_t)(nVr + __popc(hR & le) - 1))
                                     : (uint32_t)iR;
                         g.word[j + lane] = locV | (locR << 16);
                         if ((hV >> lane) & 1u) g.list[l0 + nl + __popc(hV & lt)] = iV;
-                        if ((hR >> lane) & 1u) g.list[l0 + nl + nV + __popc(hR & lt)] = iR;
+                        if ((hR >> lane) & 1u) g.list[l0 + nl + nVr + __popc(hR & lt)] = iR;
                     }
                     if (lane == 0) {
                         GStep st;
                         st.j0 = j;
                         st.list_off = (int32_t)(l0 + nl);
-                        const bool last = hi >= cmax && j + cmax >= jend;
+                        const bool last = hi >= cmax && !more_in_item;
                         st.info = (uint32_t)hi | (first && lo == 0 ? 64u : 0u) | (last ? 128u : 0u) |
-                                  ((uint32_t)((it - it0) & 3) << 8) | ((uint32_t)nV << 10) |
-                                  ((uint32_t)nR << 16) | ((uint32_t)lo << 22);
+                                  ((uint32_t)((it - it0) & 3) << 8) | ((uint32_t)nVr << 10) |
+                                  ((uint32_t)nRr << 16) | ((uint32_t)lo << 22);
                         st.slot = x.slot;
                         g.steps[s0 + ns] = st;
                         g.rank[s0 + ns] = own;
                     }
                 }
                 ++ns;
-                nl += (uint32_t)(nV + nR);
+                nl += (uint32_t)(nVr + nRr);
                 lo = hi;
             } while (lo < cmax);
-            if (valid) prevR = iR;
-            j += cmax;
-            first = false;
-        } while (j < jend);
+            if (!more) break;
+            cV = nV;
+            cR = nR;
+            if (more_in_item) {
+                if (valid) prevR = iR;
+                j += cmax;
+                first = false;
+            } else {
+                ++it;
+                x = xn;
+                own = own_n;
+                if (it + 1 < it1) {
+                    xn = g.items[it + 1];
+                    own_n = g.emit && g.first ? g.rank_n[xn.row] : 0;
+                }
+                j = (int)x.begin;
+                jend = (int)(x.begin + x.len);
+                prevR = -1;
+                first = true;
+            }
+        }
     }
     if (!g.emit && lane == 0) {
         g.cnt[b] = ns;
