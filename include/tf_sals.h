@@ -333,13 +333,20 @@ tf_status tf_set_sm_limit(tf_ctx *ctx, int sms);
  * for values outside these ranges.  No counterpart in the paper. */
 tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int pool_rows, int warps);
 
-/* Precision of the Gram matrix of wide subsets (16 < C < 128) in float contexts:
- * 0 = FP32-level (default; on the tensor cores three TF32 products per term), 1 = the
- * reduced-precision form, one TF32 product per term on the tensor cores for every wide
- * C (B and c carry about 1e-3 relative error, so a row update differs from the FP32
- * one by about cond(B + lambda I) * 1e-3; the training RMSE after a few sweeps stays
- * within 1e-3 of the FP64 oracle's on the tested workloads).  C <= 16 is unaffected.
- * TF_EINVAL for mode 1 on a double context. */
+/* Reduced-precision forms of the sweep in float contexts (no counterpart in the paper):
+ *   0 = FP32-level (default; on the tensor cores three TF32 products per Gram term);
+ *   1 = one TF32 product per Gram term on the tensor cores, for wide subsets (16 < C < 128)
+ *       and for the lean pass (three-way tensors, C <= 12): B and c carry about 1e-3
+ *       relative error, so a row update differs from the FP32 one by about
+ *       cond(B + lambda I) * 1e-3;
+ *   2 = the lean pass reads the varying mode's slice rows (the per-entry gathers) from
+ *       bfloat16 copies of the slices (8 significand bits, rounded to nearest even from
+ *       the FP32 slices after every pack and every mode's solve); run-mode and own rows,
+ *       products, sums and residuals stay FP32.  Other passes run FP32-level.  Adds
+ *       sum_n I_n * ceil(3 C_max / 8) * 16 bytes of copies.
+ * In both reduced forms the training RMSE after a few sweeps stays within 1e-3 of the
+ * FP64 oracle's on the tested workloads.  TF_EINVAL for a mode other than 0 on a double
+ * context, or outside 0..2. */
 tf_status tf_set_precision(tf_ctx *ctx, int mode);
 
 /* ------------------------------------------------------------------ timing */

@@ -237,7 +237,9 @@ struct Impl : CtxBase {
     };
     std::vector<std::unique_ptr<GatherPlan>> gplans;
     uint64_t gplan_clock = 0;
-    int precision = 0;             // 0 FP32-level Gram, 1 single-TF32 tensor-core Gram (wide C)
+    int precision = 0;             // 0 FP32-level, 1 single-TF32 tensor-core Gram, 2 bfloat16
+                                   // varying-mode rows in the lean pass
+    Buf<uint16_t> Zb[kMaxModes];   // bfloat16 copies of the slices (precision 2)
     int solve_refine = 0;          // float: one refinement step of every row solve
     float solve_cond = 0.f;        // float: FP64 solve of rows with pivot ratio < 1 / this
     CUtensorMap tmaps[kMaxModes][3];  // per mode: slice maps with boxes 8, 24, 40 floats
@@ -258,7 +260,7 @@ struct Impl : CtxBase {
         f(f_other), f(f_x), f(f_out), f(f_part), f(f_fac), f(f_rpart), f(f_meta), f(p_coords),
             f(p_out);
         for (int n = 0; n < kMaxModes; ++n) {
-            f(A[n]), f(res[n]), f(Z[n]);
+            f(A[n]), f(res[n]), f(Z[n]), f(Zb[n]);
             mode[n].each_buf(f);
         }
         for (auto &g : gplans) f(g->steps), f(g->step_ptr), f(g->word), f(g->list);
@@ -1091,6 +1093,16 @@ struct Impl : CtxBase {
                               lean_pass_supported(CM, N);
         if (path >= 3 && !use_lean && !wide)
             throw ApiError{TF_EINVAL, "lean mode pass not available here"};
+        // precision 2: the lean pass reads the varying mode's rows from bfloat16 copies of
+        // the slices, refreshed after every pack and every mode's solves
+        const bool bf16_rows = use_lean && precision == 2;
+        const int Wb = slice_bf16_stride(CM);
+        if (bf16_rows)
+            for (int l = 0; l < N; ++l)
+                if (Zb[l].n < (size_t)dims[l] * Wb) {
+                    Zb[l].alloc((size_t)dims[l] * Wb, st);
+                    TFS_CUDA(cudaMemsetAsync(Zb[l].p, 0, Zb[l].n * sizeof(uint16_t), st));
+                }
         last_path = 0;
         const int nsplit = (K + C - 1) / C;
         // every launch of the splits (pack, mode passes, solves) and the copy of the last
@@ -1120,6 +1132,14 @@ struct Impl : CtxBase {
                 pk.Q = Qp;
                 timed(TF_KIND_PACK, [&] { launch_pack<T>(pk, st); });
                 ++launches;
+                if (bf16_rows) {
+                    for (int l = 0; l < N; ++l)
+                        timed(TF_KIND_PACK, [&] {
+                            launch_slice_bf16((const float *)Z[l].p, Zb[l].p, dims[l], W, Wb, 0,
+                                              3 * CM, st);
+                        });
+                    launches += N;
+                }
                 for (int t = 0; t < T_in; ++t) {
                     for (int n = 0; n < N; ++n) {
                         const ModeLayout &L = mode[n];
@@ -1140,7 +1160,9 @@ struct Impl : CtxBase {
                         for (int u = 0; u < N - 1; ++u) {
                             a.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
                             a.Zo[u] = Z[L.omode[u]].p;
+                            a.Zob[u] = Zb[L.omode[u]].p;
                         }
+                        a.Wb = Wb;
                         a.Zn = Z[n].p;
                         a.rank_n = L.rank_of.p;
                         a.res = res[n].p;
@@ -1161,7 +1183,7 @@ struct Impl : CtxBase {
                             // every block takes one ticket past the last bin
                             ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;
                             timed(TF_KIND_MODE_PASS,
-                                  [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, precision == 0, st); });
+                                  [&] { launch_pass_wide<T>(a, CM, W, wgrid, tc, precision != 1, st); });
                             last_path |= tc ? 4 : 1;
                             ++launches;
                             if (L.n_single > 0) {
@@ -1197,12 +1219,13 @@ struct Impl : CtxBase {
                             // Gram flavour: TF32 x 1 on the tensor cores for the
                             // reduced-precision form; FP32-level otherwise (packed FMAs,
                             // or three TF32 products on the tensor cores on path 4)
-                            const int gk = precision == 1 ? 1 : (path == 4 ? 3 : 0);
+                            const int gk = bf16_rows ? 0 : precision == 1 ? 1 : (path == 4 ? 3 : 0);
                             LeanPlan plan{};
                             bool lean_here = use_lean;
                             if (lean_here) {
                                 plan = lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, pass_sms(), L.P,
-                                                      lean_cache_rows, lean_ring_cap, lean_warps, gk);
+                                                      lean_cache_rows, lean_ring_cap, lean_warps, gk,
+                                                      bf16_rows ? 1 : 0);
                                 lean_here = path != 0 || plan.coverage >= 0.25;
                             }
                             if (lean_here) {
@@ -1260,6 +1283,13 @@ struct Impl : CtxBase {
                                   [&] { launch_combine<T>(a, CM, L.split.p, L.n_split, st); });
                             ++launches;
                         }
+                        if (bf16_rows) {  // the rows just solved, into the bfloat16 copy
+                            timed(TF_KIND_PACK, [&] {
+                                launch_slice_bf16((const float *)Z[n].p, Zb[n].p, dims[n], W, Wb,
+                                                  0, CM, st);
+                            });
+                            ++launches;
+                        }
                     }
                 }
                 cq = Cs;
@@ -1280,7 +1310,10 @@ struct Impl : CtxBase {
             gk.precision = precision, gk.use_tma = use_tma, gk.flags = flags;
             gk.refine = solve_refine, gk.cond = solve_cond;
             gk.lambda = lambda, gk.layout_gen = layout_gen, gk.partials = partials.p;
-            for (int l = 0; l < N; ++l) gk.Z[l] = Z[l].p;
+            for (int l = 0; l < N; ++l) {
+                gk.Z[l] = Z[l].p;
+                gk.Zb[l] = Zb[l].p;
+            }
             cq_end = run_splits_graph(gk, run_splits);
         }
         Cq = cq_end;
@@ -1305,6 +1338,7 @@ struct Impl : CtxBase {
         int64_t layout_gen;
         const void *partials;
         const void *Z[kMaxModes];
+        const void *Zb[kMaxModes];
         bool operator==(const GraphKey &o) const {
             if (C != o.C || T_in != o.T_in || CM != o.CM || Cq != o.Cq || path != o.path ||
                 precision != o.precision || refine != o.refine || cond != o.cond ||
@@ -1312,7 +1346,7 @@ struct Impl : CtxBase {
                 lambda != o.lambda || layout_gen != o.layout_gen || partials != o.partials)
                 return false;
             for (int l = 0; l < kMaxModes; ++l)
-                if (Z[l] != o.Z[l]) return false;
+                if (Z[l] != o.Z[l] || Zb[l] != o.Zb[l]) return false;
             return true;
         }
     };
@@ -2278,10 +2312,10 @@ tf_status tf_set_stream(tf_ctx *ctx, void *stream) {
 }
 
 tf_status tf_set_precision(tf_ctx *ctx, int mode) {
-    if (mode < 0 || mode > 1) return TF_EINVAL;
+    if (mode < 0 || mode > 2) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
-        if (mode == 1 && sizeof(*c.x.p) != 4)
-            throw tfs::ApiError{TF_EINVAL, "the reduced-precision Gram needs a float context"};
+        if (mode != 0 && sizeof(*c.x.p) != 4)
+            throw tfs::ApiError{TF_EINVAL, "the reduced-precision forms need a float context"};
         c.precision = mode;
     });
 }

@@ -118,15 +118,22 @@ __device__ __forceinline__ void cp_wait() {
 //   cur | prev | old regions); the others carry cur | prev (FIRST) or cur only.  RUN is
 //   the other mode whose index forms runs along a row's entries (the first key of the
 //   row's sort order), VAR the one that varies from entry to entry.
-template <int CM, bool FIRST, int NLO, int RUN>
+//   VB = 1: the varying mode's rows come from a bfloat16 copy of its slice (16-byte
+//   vectors of 8 values, widened to FP32 in registers); everything else stays FP32.
+template <int CM, bool FIRST, int NLO, int RUN, int VB = 0>
 struct LG {
     static constexpr int H = CM / 2;                          // pairs per region
     static constexpr int W = slice_stride_elems(CM, 4);       // floats per slice row
     static constexpr int V_CUR = (CM + 3) / 4, V_CP = (2 * CM + 3) / 4, V_ALL = (3 * CM + 3) / 4;
-    static constexpr bool lo(int t) { return FIRST && t < NLO; }
-    static constexpr int nv(int t) { return FIRST ? (lo(t) ? V_ALL : V_CP) : V_CUR; }
-    static constexpr int cs(int t) { return (nv(t) | 1) * 4; }  // staged row stride, floats
     static constexpr int VAR = 1 - RUN;
+    static constexpr bool lo(int t) { return FIRST && t < NLO; }
+    static constexpr bool half(int t) { return VB != 0 && t == VAR; }
+    static constexpr int ncols(int t) { return FIRST ? (lo(t) ? 3 * CM : 2 * CM) : CM; }
+    // 16-byte vectors fetched per row: 4 floats, or 8 bfloat16 values
+    static constexpr int nv(int t) {
+        return half(t) ? (ncols(t) + 7) / 8 : (FIRST ? (lo(t) ? V_ALL : V_CP) : V_CUR);
+    }
+    static constexpr int cs(int t) { return (nv(t) | 1) * 4; }  // staged row stride, floats
     static constexpr int NBLK = H * (H + 1) / 2;                  // 2 x 2 blocks of B
     static constexpr int NACC = 2 * NBLK + H;                     // packed accumulators
     static constexpr int NT = CM * (CM + 1) / 2;
@@ -300,12 +307,12 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
 // 3: three (h = hi + lo, hi hi + hi lo + lo hi), FP32-level.
 constexpr int kLeanStageStride = 36;  // floats per staged H' row (conflict-free)
 
-template <int CM, bool FIRST, int NLO, int RUN, int GK>
+template <int CM, bool FIRST, int NLO, int RUN, int GK, int VB>
 __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
     k_lean_pass(const PassArgs<float> a, const LeanParams lp, const GStep *__restrict__ steps,
                 const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_ptr,
                 const int32_t *__restrict__ list, const uint32_t *__restrict__ word) {
-    using G = LG<CM, FIRST, NLO, RUN>;
+    using G = LG<CM, FIRST, NLO, RUN, VB>;
     constexpr int H = G::H, W = G::W, NACC = G::NACC, VAR = G::VAR;
     constexpr int NVR = G::nv(RUN), NVV = G::nv(VAR), CSR = G::cs(RUN), CSV = G::cs(VAR);
     constexpr int CSP = CSR > CSV ? CSR : CSV;  // pool row stride
@@ -314,6 +321,7 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
     __shared__ short tgt[2 * NACC];  // partial-slot index of each accumulator float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float *ZR = a.Zo[RUN], *ZV = a.Zo[VAR];
+    const uint16_t *ZVb = a.Zob[VAR];  // bfloat16 copy of the varying mode's slice (VB)
 
     // accumulator layout -> partial slot index (B lower triangle, then c); -1 = unused
     for (int q = threadIdx.x; q < 2 * NACC; q += blockDim.x) {
@@ -340,10 +348,14 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
         for (int q = threadIdx.x; q < n0 + n1; q += blockDim.x) {
             if (q < n0) {
                 const int r = q / NV0, v = q - r * NV0;
-                cp16(saddr(c0 + r * CS0 + 4 * v), Z0 + (int64_t)r * W + 4 * v);
+                cp16(saddr(c0 + r * CS0 + 4 * v),
+                     G::half(0) ? (const void *)(a.Zob[0] + (int64_t)r * a.Wb + 8 * v)
+                                : (const void *)(Z0 + (int64_t)r * W + 4 * v));
             } else {
                 const int qq = q - n0, r = qq / NV1, v = qq - r * NV1;
-                cp16(saddr(c1 + r * CS1 + 4 * v), Z1 + (int64_t)r * W + 4 * v);
+                cp16(saddr(c1 + r * CS1 + 4 * v),
+                     G::half(1) ? (const void *)(a.Zob[1] + (int64_t)r * a.Wb + 8 * v)
+                                : (const void *)(Z1 + (int64_t)r * W + 4 * v));
             }
         }
         cp_commit();
@@ -441,7 +453,9 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
                     const int k = k0 + sub;
                     const int row = __shfl_sync(0xFFFFFFFFu, li, k & 31);
                     if (sub < RPR && k < nV)
-                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part), ZV + (int64_t)row * W + 4 * part);
+                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part),
+                             G::half(VAR) ? (const void *)(ZVb + (int64_t)row * a.Wb + 8 * part)
+                                          : (const void *)(ZV + (int64_t)row * W + 4 * part));
                 }
             }
             {
@@ -520,12 +534,28 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
                         }
                     }
                 }
-                u64 y[2 * NVV];
+                u64 y[G::half(VAR) ? 4 * NVV : 2 * NVV];
                 {
                     const unsigned p = (locV & kPoolBit) ? pool + 4u * (unsigned)((locV & 0x7FFFu) * CSP)
                                                          : cacheV + 4u * (unsigned)(locV * CSV);
+                    if constexpr (G::half(VAR)) {
+                        // 8 bfloat16 values per vector; a bfloat16 is the top half of the
+                        // float it widens to
 #pragma unroll
-                    for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
+                        for (int v = 0; v < NVV; ++v) {
+                            uint32_t w[4];
+                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                                         : "r"(p + 16 * v));
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                y[4 * v + k] = pk(__uint_as_float(w[k] << 16),
+                                                  __uint_as_float(w[k] & 0xFFFF0000u));
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NVV; ++v) lds2(p + 16 * v, y[2 * v], y[2 * v + 1]);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < H; ++q) h[q] = mul2(wc[q], y[q]);
@@ -679,21 +709,23 @@ bool lean_pass_supported(int CM, int N) {
     return N == 3 && (CM == 2 || CM == 4 || CM == 6 || CM == 8 || CM == 10 || CM == 12);
 }
 
-// Row geometry of other mode t (0 or 1) of mode n's pass: vectors fetched, staged stride.
-static void lean_geo(int CM, bool first, int n, int t, int &nv, int &cs) {
-    const int vc = (CM + 3) / 4, vcp = (2 * CM + 3) / 4, vall = (3 * CM + 3) / 4;
-    nv = first ? (t < n ? vall : vcp) : vc;
-    cs = (nv | 1) * 4;
-}
-
 // The other mode whose index forms runs along mode n's rows: entries of a row are sorted
 // by (i_{n+1}, i_{n+2}) (mode numbers mod 3), and other mode t = 0 / 1 is the lower /
 // higher of the two mode numbers.
 int lean_run_mode(int n) { return n == 1 ? 1 : 0; }
 
+// Row geometry of other mode t (0 or 1) of mode n's pass: 16-byte vectors fetched, staged
+// stride in floats (the kernel's LG); vb: the varying mode's rows in bfloat16.
+static void lean_geo(int CM, bool first, int n, int t, int vb, int &nv, int &cs) {
+    const int cols = first ? (t < n ? 3 * CM : 2 * CM) : CM;
+    const bool half = vb != 0 && t == 1 - lean_run_mode(n);
+    nv = half ? (cols + 7) / 8 : (cols + 3) / 4;
+    cs = (nv | 1) * 4;
+}
+
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int pool_rows, int warps, int gk) {
+                        int max_cache_rows, int pool_rows, int warps, int gk, int vb) {
     int dev = 0, smem_blk = 0;
     TFS_CUDA(cudaGetDevice(&dev));
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -703,12 +735,13 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     // so the plain inner iterations (narrower rows in the same counts) share its plan
     int nv[2], cs[2], nvw[2], csw[2];
     for (int t = 0; t < 2; ++t) {
-        lean_geo(CM, first, n, t, nv[t], cs[t]);
-        lean_geo(CM, true, n, t, nvw[t], csw[t]);
+        lean_geo(CM, first, n, t, vb, nv[t], cs[t]);
+        lean_geo(CM, true, n, t, vb, nvw[t], csw[t]);
     }
     const int csp = std::max(cs[0], cs[1]);
     lp.cap[0] = lp.cap[1] = pool_rows;
     pl.gk = gk;
+    pl.vb = vb;
     const int stage = gk == 0 ? 0 : 16 * kLeanStageStride * (gk == 3 ? 2 : 1);
     lp.slot_floats = pool_rows * csp;
     lp.own_off = kLeanSlots * lp.slot_floats;
@@ -801,40 +834,45 @@ void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, con
     TFS_CUDA(cudaGetLastError());
 }
 
-template <int CM, bool FIRST, int NLO, int RUN, int GK>
+template <int CM, bool FIRST, int NLO, int RUN, int GK, int VB>
 static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                           cudaStream_t st) {
-    auto kern = k_lean_pass<CM, FIRST, NLO, RUN, GK>;
+    auto kern = k_lean_pass<CM, FIRST, NLO, RUN, GK, VB>;
     TFS_CUDA(raise_smem_limit((const void *)kern, (int)pl.smem));
     kern<<<pl.grid, pl.warps * kWarp, pl.smem, st>>>(
         a, pl.p, static_cast<const GStep *>(gp.steps), gp.rank, gp.step_ptr, gp.list, gp.word);
     TFS_CUDA(cudaGetLastError());
 }
 
-template <int CM, int GK>
+template <int CM, int GK, int VB>
 static void launch_lean_cm(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                            cudaStream_t st) {
     if (!a.first) {
         if (a.n == 1)
-            launch_lean_t<CM, false, 0, 1, GK>(a, pl, gp, st);
+            launch_lean_t<CM, false, 0, 1, GK, VB>(a, pl, gp, st);
         else
-            launch_lean_t<CM, false, 0, 0, GK>(a, pl, gp, st);
+            launch_lean_t<CM, false, 0, 0, GK, VB>(a, pl, gp, st);
         return;
     }
     switch (a.n) {
-        case 0: launch_lean_t<CM, true, 0, 0, GK>(a, pl, gp, st); return;
-        case 1: launch_lean_t<CM, true, 1, 1, GK>(a, pl, gp, st); return;
-        default: launch_lean_t<CM, true, 2, 0, GK>(a, pl, gp, st); return;
+        case 0: launch_lean_t<CM, true, 0, 0, GK, VB>(a, pl, gp, st); return;
+        case 1: launch_lean_t<CM, true, 1, 1, GK, VB>(a, pl, gp, st); return;
+        default: launch_lean_t<CM, true, 2, 0, GK, VB>(a, pl, gp, st); return;
     }
 }
 
 template <int CM>
 static void launch_lean_gk(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                            cudaStream_t st) {
+    if (pl.vb) {
+        if (pl.gk != 0) throw ApiError{TF_EINVAL, "bfloat16 rows take the packed FMA Gram"};
+        launch_lean_cm<CM, 0, 1>(a, pl, gp, st);
+        return;
+    }
     switch (pl.gk) {
-        case 1: launch_lean_cm<CM, 1>(a, pl, gp, st); return;
-        case 3: launch_lean_cm<CM, 3>(a, pl, gp, st); return;
-        default: launch_lean_cm<CM, 0>(a, pl, gp, st); return;
+        case 1: launch_lean_cm<CM, 1, 0>(a, pl, gp, st); return;
+        case 3: launch_lean_cm<CM, 3, 0>(a, pl, gp, st); return;
+        default: launch_lean_cm<CM, 0, 0>(a, pl, gp, st); return;
     }
 }
 

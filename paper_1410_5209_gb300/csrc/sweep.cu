@@ -207,6 +207,29 @@ void launch_predict(const PredictArgs<T> &a, cudaStream_t st) {
     TFS_CUDA(cudaGetLastError());
 }
 
+// Bfloat16 copy of a slice's columns, two values per thread (round to nearest even).
+__global__ void k_slice_bf16(const float *__restrict__ Z, uint32_t *__restrict__ Zb, int64_t rows,
+                             int W, int Wb, int col0, int npairs) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= rows * npairs) return;
+    const int64_t i = q / npairs;
+    const int c = col0 + 2 * (int)(q - i * npairs);
+    const float2 v = *reinterpret_cast<const float2 *>(Z + i * W + c);
+    uint32_t packed;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(packed) : "f"(v.y), "f"(v.x));
+    Zb[(i * Wb + c) / 2] = packed;
+}
+
+void launch_slice_bf16(const float *Z, uint16_t *Zb, int64_t rows, int W, int Wb, int col0,
+                       int ncols, cudaStream_t st) {
+    if (rows <= 0 || ncols <= 0) return;
+    if ((col0 | ncols | W | Wb) & 1) throw ApiError{TF_EINVAL, "bfloat16 slice copy: odd column"};
+    const int npairs = ncols / 2;
+    k_slice_bf16<<<blocks_for(rows * npairs, 256), 256, 0, st>>>(
+        Z, reinterpret_cast<uint32_t *>(Zb), rows, W, Wb, col0, npairs);
+    TFS_CUDA(cudaGetLastError());
+}
+
 template <class T>
 void launch_init_normal(T *A, int64_t count, uint64_t seed, uint64_t stream_id, double std,
                         cudaStream_t st) {

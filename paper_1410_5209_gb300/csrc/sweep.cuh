@@ -40,6 +40,8 @@ struct PassArgs {
     T lambda;
     const int32_t *oidx[kMaxModes - 1];  // other-mode indices, mode-n order
     const T *Zo[kMaxModes - 1];          // packed slices of those modes
+    const uint16_t *Zob[kMaxModes - 1];  // their bfloat16 copies (lean pass, precision 2)
+    int Wb;                              // values per row of the bfloat16 copies
     T *Zn;                               // packed slice of mode n (rows in rank order)
     const int32_t *rank_n;               // row id of mode n -> slice row (degree rank)
     T *res;                              // residual copy of mode n
@@ -281,6 +283,7 @@ struct LeanPlan {
     LeanParams p;
     int warps = 0, grid = 0;
     int gk = 0;  // Gram: 0 packed FP32 FMAs, 1 one TF32 MMA product, 3 three (FP32-level)
+    int vb = 0;  // 1: the varying mode's rows from its bfloat16 slice copy
     size_t smem = 0;
     double coverage = 0;  // entries whose varying-mode row is cached, fraction of all
 };
@@ -302,10 +305,15 @@ int lean_run_mode(int n);  // the other mode (0 / 1) whose index forms runs in m
 // Plan of mode n's lean pass: cached rows of the two other modes chosen by entries covered
 // (deg_cum[t][R] = entries whose mode-t row is among that slice's first R rows), at most
 // max_cache_rows each (< 0: no limit), pool_rows staged cold rows per step, warps per block
-// (0: default), gk the Gram flavour (LeanPlan::gk).
+// (0: default), gk the Gram flavour (LeanPlan::gk), vb the varying rows' type (LeanPlan::vb).
 LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
                         const std::vector<int64_t> *deg_cum[2], int64_t nnz, int num_sms, int P,
-                        int max_cache_rows, int pool_rows, int warps, int gk);
+                        int max_cache_rows, int pool_rows, int warps, int gk, int vb);
+// Values per row of a slice's bfloat16 copy (all three regions, 16-byte rows).
+inline int slice_bf16_stride(int CM) { return (3 * CM + 7) / 8 * 8; }
+// Zb[i][col0 .. col0 + ncols) = Z[i][same columns] rounded to bfloat16 (nearest even), i < rows.
+void launch_slice_bf16(const float *Z, uint16_t *Zb, int64_t rows, int W, int Wb, int col0,
+                       int ncols, cudaStream_t st);
 size_t gather_plan_step_bytes();  // bytes per step record (+ its own-row rank)
 // emit = 0: per-bin step and list counts into cnt[b] / cnt[P + b]; emit = 1: the plan.
 void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,
