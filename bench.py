@@ -32,12 +32,43 @@ WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=
                 K=100, C=10, T_in=1, lam=0.1, rank_truth=50, zipf=1.1)
 
 # DRAM traffic (read + write) of one mode-pass launch from the ncu capture summarised in
-# profiles/k_mode_pass_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
+# profiles/k_lean_pass_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
 # 1e8-entry launch), and the hash of the kernel sources it was taken with; the bench
 # reports traffic as null once the sources differ or the entry count is not 1e8.
-NCU_TRAFFIC = 1.716e9
+NCU_TRAFFIC = 1.711e9
 NCU_TRAFFIC_NNZ = 100_000_000
-NCU_SOURCE_HASH = "0e70ba200474fea2"
+NCU_SOURCE_HASH = "8f54465d411fa74e"
+
+
+# Utilisation of the L1 data pipe (shared-memory and L1 wavefronts) of the mode pass in the
+# same capture, averaged over the three modes' launches; null once the sources differ.
+NCU_L1_PIPE_PCT = 71.0
+
+
+def pass_units(nnz, N, C, avg_launch_ms):
+    """The mode pass against the on-chip units that bind it, with this device's measured
+    peaks (tf_device_peaks): FP32 FMA throughput, for the algorithmic FLOPs of a pass
+    (Eq. 4's Gram lower triangle and right-hand side, the Hadamard products of the other
+    modes' rows, and the R-hat refresh over the previous and current columns), and
+    shared-memory bandwidth, for the varying-mode slice row every entry reads from on-chip
+    copies (C values of each region it needs: two regions where that mode is updated after
+    the pass's mode in the split, three where before; averaged over the three modes' passes
+    of a three-way tensor)."""
+    import paper_1410_5209_gb300 as tf
+    dp = tf.device_peaks()
+    flops = nnz * (C * (C + 1) + 2 * C + (N - 2) * C + 2 * C * N)
+    v_floats = (2 + 3 + 3) * C / 3.0 if N == 3 else 2.0 * C
+    sbytes = nnz * 4.0 * v_floats
+    s = avg_launch_ms / 1e3
+    pct = NCU_L1_PIPE_PCT if NCU_SOURCE_HASH == kernel_source_hash() else None
+    return {"fp32": {"peak_tflops": dp["fp32x2_tflops"], "peak_tflops_plain_fma": dp["fp32_tflops"],
+                     "algorithmic_flops_per_launch": flops, "achieved_tflops": flops / s / 1e12,
+                     "frac": flops / s / 1e12 / dp["fp32x2_tflops"]},
+            "shared_memory": {"peak_tbs": dp["smem_tbytes"], "algorithmic_bytes_per_launch": sbytes,
+                              "achieved_tbs": sbytes / s / 1e12,
+                              "frac": sbytes / s / 1e12 / dp["smem_tbytes"],
+                              "ncu_l1_data_pipe_pct": pct},
+            "peak_source": "measured on this device (tf_device_peaks, CUDA events)"}
 
 
 def kernel_source_hash():
@@ -858,6 +889,7 @@ def main():
     with_g = (bytes_per_launch + gather_bytes) / (mp_avg_ms / 1e3) / 1e9
     roofline["with_gathers"] = {"achieved": with_g, "frac": with_g / hbm,
                                 "gather_bytes_per_launch": gather_bytes}
+    roofline["units"] = pass_units(nnz, N, C, mp_avg_ms)
     nsplit = math.ceil(K / C)
     sweep_bytes = nnz * (T_in * N * (4 * (N - 1) + 4) + 4) * nsplit
     sweep_ms = sum(v[1] for k, v in prof.items()

@@ -351,6 +351,16 @@ tf_status tf_set_precision(tf_ctx *ctx, int mode);
 
 /* ------------------------------------------------------------------ timing */
 
+/* Measured peaks of the current device's units that bind the narrow mode passes (not of
+ * the method): FP32 FMA throughput in TFLOP/s, plain (fp32_tflops) and with packed two-wide
+ * FMAs (fp32x2_tflops), and shared-memory load bandwidth in TB/s (16-byte loads without
+ * bank conflicts; smem_tbytes).  Each is timed with CUDA events over five launches of a
+ * microbenchmark kernel after one warm-up, on a stream of its own; it allocates and frees
+ * a small device buffer (cudaMalloc / cudaFree, which synchronise the device).  Any
+ * output may be NULL.  TF_ECUDA on a CUDA failure. */
+tf_status tf_device_peaks(double *fp32_tflops, double *fp32x2_tflops, double *smem_tbytes);
+
+
 /* Kernel kinds reported by tf_get_profile. */
 typedef enum {
     TF_KIND_PACK = 0,      /* slice packing of a split (Theorem 3's C resident columns) */

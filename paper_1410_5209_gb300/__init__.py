@@ -84,6 +84,7 @@ def load():
         "tf_set_pass_cache": [P, i32, i32, i32],
         "tf_set_sm_limit": [P, i32],
         "tf_set_precision": [P, i32],
+        "tf_device_peaks": [P, P, P],
         "tf_set_stream": [P, P],
         "tf_profile": [P, i32],
         "tf_get_profile": [P, P, P],
@@ -445,6 +446,17 @@ def plan_mode(off, P, cap=0, policy=SCHED_LPT, seed=0):
 
 def version():
     return load().tf_version().decode()
+
+
+def device_peaks():
+    """Measured FP32 FMA rates (plain, packed two-wide; TFLOP/s) and shared-memory load
+    bandwidth (TB/s) of the current device (tf_device_peaks)."""
+    lib = load()
+    v = [ctypes.c_double() for _ in range(3)]
+    st = lib.tf_device_peaks(*[ctypes.byref(x) for x in v])
+    if st != OK:
+        raise TFError(st, "tf_device_peaks failed")
+    return {"fp32_tflops": v[0].value, "fp32x2_tflops": v[1].value, "smem_tbytes": v[2].value}
 
 
 def estimate_bytes(dims, nnz, K, C_max, dtype=F32, device_input=False, num_sms=0):

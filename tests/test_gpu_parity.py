@@ -1224,3 +1224,12 @@ def test_solve_options_leave_double_contexts_alone():
         assert np.array_equal(out[0][n], out[1][n])
     with pytest.raises(tf.TFError):   # a negative limit is refused
         tf.Factorization(c, x, p.dims, p.K, seed=p.seed, dtype=tf.F64).set_solve(False, -1.0)
+
+
+def test_device_peaks_plausible():
+    """tf_device_peaks measures this GPU's FP32 FMA rates and shared-memory bandwidth:
+    positive, within physical bounds, the packed FMA at least as fast as the plain one."""
+    d = tf.device_peaks()
+    assert 5.0 < d["fp32_tflops"] < 1000.0
+    assert d["fp32x2_tflops"] >= 0.8 * d["fp32_tflops"]
+    assert 1.0 < d["smem_tbytes"] < 1000.0
