@@ -437,11 +437,12 @@ def precision_forms(args, p, K, C, lam, sweeps=3):
     """The precision forms of the mode pass on the same tensor from the same initial factors
     (a fresh context each, the same column orders): device ms per sweep (sweeps after the
     first, which also builds the pass's gather plans) and training RMSE after `sweeps`.
-    Forms: FP32 with packed FMAs (the default), bfloat16 varying-mode rows
-    (tf_set_precision(2)), TF32 x 1 and x 3 tensor-core Grams, and the cp.async pass."""
+    Forms: FP32 with packed FMAs (the default), bfloat16 slice rows of the varying mode
+    (tf_set_precision(2)) or of both other modes (3), TF32 x 1 and x 3 tensor-core Grams,
+    and the cp.async pass."""
     import torch
     import paper_1410_5209_gb300 as tf
-    forms = {"fp32_packed_fma": (0, 0), "bf16_varying_rows": (0, 2),
+    forms = {"fp32_packed_fma": (0, 0), "bf16_varying_rows": (0, 2), "bf16_other_rows": (0, 3),
              "tf32x1_tensor_core": (0, 1), "tf32x3_tensor_core": (4, 0), "cp_async_pass": (1, 0)}
     out = {}
     for name, (path, prec) in forms.items():

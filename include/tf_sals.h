@@ -339,13 +339,16 @@ tf_status tf_set_pass_cache(tf_ctx *ctx, int max_rows, int pool_rows, int warps)
  *       and for the lean pass (three-way tensors, C <= 12): B and c carry about 1e-3
  *       relative error, so a row update differs from the FP32 one by about
  *       cond(B + lambda I) * 1e-3;
- *   2 = the lean pass reads the varying mode's slice rows (the per-entry gathers) from
- *       bfloat16 copies of the slices (8 significand bits, rounded to nearest even from
- *       the FP32 slices after every pack and every mode's solve); run-mode and own rows,
- *       products, sums and residuals stay FP32.  Other passes run FP32-level.  Adds
- *       sum_n I_n * ceil(3 C_max / 8) * 16 bytes of copies.
- * In both reduced forms the training RMSE after a few sweeps stays within 1e-3 of the
- * FP64 oracle's on the tested workloads.  TF_EINVAL for a mode other than 0 on a double
+ *   2 = the lean pass reads the varying mode's slice rows (one of the two per-entry
+ *       gathers) from bfloat16 copies of the slices (8 significand bits, rounded to nearest
+ *       even from the FP32 slices after every pack and every mode's solve); run-mode and
+ *       own rows, products, sums and residuals stay FP32.  Other passes run FP32-level.
+ *       Adds sum_n I_n * ceil(3 C_max / 8) * 16 bytes of copies;
+ *   3 = as 2 for both other modes' rows (the R-hat refresh products then carry two
+ *       rounded factors: the training RMSE moved by up to 2e-3 relative on a low-noise
+ *       test tensor, by 6e-6 on the skewed 1e8-entry workload).
+ * In forms 1 and 2 the training RMSE after a few sweeps stays within 1e-3 of the FP64
+ * oracle's on the tested workloads.  TF_EINVAL for a mode other than 0 on a double
  * context, or outside 0..2. */
 tf_status tf_set_precision(tf_ctx *ctx, int mode);
 

@@ -373,7 +373,8 @@ class Factorization:
     def set_precision(self, mode):
         """0: FP32-level Gram; 1: single-TF32 tensor-core Gram (wide subsets, and narrow
         ones of three-way float tensors); 2: the lean pass reads the varying mode's slice
-        rows from bfloat16 copies (narrow subsets of three-way float tensors)."""
+        rows from bfloat16 copies; 3: both other modes' rows (narrow subsets of three-way
+        float tensors)."""
         self._check(self._lib.tf_set_precision(self._ctx, int(mode)))
 
     def set_schedule(self, policy=SCHED_LPT, P=0):

@@ -237,8 +237,8 @@ struct Impl : CtxBase {
     };
     std::vector<std::unique_ptr<GatherPlan>> gplans;
     uint64_t gplan_clock = 0;
-    int precision = 0;             // 0 FP32-level, 1 single-TF32 tensor-core Gram, 2 bfloat16
-                                   // varying-mode rows in the lean pass
+    int precision = 0;             // 0 FP32-level, 1 single-TF32 tensor-core Gram, 2 / 3
+                                   // bfloat16 varying-mode / other-mode rows in the lean pass
     Buf<uint16_t> Zb[kMaxModes];   // bfloat16 copies of the slices (precision 2)
     int solve_refine = 0;          // float: one refinement step of every row solve
     float solve_cond = 0.f;        // float: FP64 solve of rows with pivot ratio < 1 / this
@@ -1093,9 +1093,9 @@ struct Impl : CtxBase {
                               lean_pass_supported(CM, N);
         if (path >= 3 && !use_lean && !wide)
             throw ApiError{TF_EINVAL, "lean mode pass not available here"};
-        // precision 2: the lean pass reads the varying mode's rows from bfloat16 copies of
-        // the slices, refreshed after every pack and every mode's solves
-        const bool bf16_rows = use_lean && precision == 2;
+        // precision 2 / 3: the lean pass reads the varying mode's / both other modes' rows
+        // from bfloat16 copies of the slices, refreshed after every pack and every solve
+        const bool bf16_rows = use_lean && precision >= 2;
         const int Wb = slice_bf16_stride(CM);
         if (bf16_rows)
             for (int l = 0; l < N; ++l)
@@ -1225,7 +1225,7 @@ struct Impl : CtxBase {
                             if (lean_here) {
                                 plan = lean_pass_plan(CM, t == 0, n, dims_o, dc, nnz, pass_sms(), L.P,
                                                       lean_cache_rows, lean_ring_cap, lean_warps, gk,
-                                                      bf16_rows ? 1 : 0);
+                                                      bf16_rows ? precision - 1 : 0);
                                 lean_here = path != 0 || plan.coverage >= 0.25;
                             }
                             if (lean_here) {
@@ -2312,7 +2312,7 @@ tf_status tf_set_stream(tf_ctx *ctx, void *stream) {
 }
 
 tf_status tf_set_precision(tf_ctx *ctx, int mode) {
-    if (mode < 0 || mode > 2) return TF_EINVAL;
+    if (mode < 0 || mode > 3) return TF_EINVAL;
     return dispatch(ctx, [&](auto &c) {
         if (mode != 0 && sizeof(*c.x.p) != 4)
             throw tfs::ApiError{TF_EINVAL, "the reduced-precision forms need a float context"};

@@ -119,7 +119,8 @@ __device__ __forceinline__ void cp_wait() {
 //   the other mode whose index forms runs along a row's entries (the first key of the
 //   row's sort order), VAR the one that varies from entry to entry.
 //   VB = 1: the varying mode's rows come from a bfloat16 copy of its slice (16-byte
-//   vectors of 8 values, widened to FP32 in registers); everything else stays FP32.
+//   vectors of 8 values, widened to FP32 in registers); VB = 2: both other modes' rows;
+//   the own row, products, sums and residuals stay FP32.
 template <int CM, bool FIRST, int NLO, int RUN, int VB = 0>
 struct LG {
     static constexpr int H = CM / 2;                          // pairs per region
@@ -127,7 +128,7 @@ struct LG {
     static constexpr int V_CUR = (CM + 3) / 4, V_CP = (2 * CM + 3) / 4, V_ALL = (3 * CM + 3) / 4;
     static constexpr int VAR = 1 - RUN;
     static constexpr bool lo(int t) { return FIRST && t < NLO; }
-    static constexpr bool half(int t) { return VB != 0 && t == VAR; }
+    static constexpr bool half(int t) { return VB == 2 || (VB == 1 && t == VAR); }
     static constexpr int ncols(int t) { return FIRST ? (lo(t) ? 3 * CM : 2 * CM) : CM; }
     // 16-byte vectors fetched per row: 4 floats, or 8 bfloat16 values
     static constexpr int nv(int t) {
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
     __shared__ short tgt[2 * NACC];  // partial-slot index of each accumulator float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float *ZR = a.Zo[RUN], *ZV = a.Zo[VAR];
-    const uint16_t *ZVb = a.Zob[VAR];  // bfloat16 copy of the varying mode's slice (VB)
+    const uint16_t *ZVb = a.Zob[VAR], *ZRb = a.Zob[RUN];  // bfloat16 slice copies (VB)
 
     // accumulator layout -> partial slot index (B lower triangle, then c); -1 = unused
     for (int q = threadIdx.x; q < 2 * NACC; q += blockDim.x) {
@@ -465,7 +466,9 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
                     const int k = nV + k0 + sub;
                     const int row = __shfl_sync(0xFFFFFFFFu, li, k & 31);
                     if (sub < RPR && k0 + sub < nR)
-                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part), ZR + (int64_t)row * W + 4 * part);
+                        cp16(pool + 4u * (unsigned)(k * CSP + 4 * part),
+                             G::half(RUN) ? (const void *)(ZRb + (int64_t)row * a.Wb + 8 * part)
+                                          : (const void *)(ZR + (int64_t)row * W + 4 * part));
                 }
             }
             if (FIRST && (inf & 64u)) {
@@ -518,11 +521,25 @@ __global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
             if (act) {
                 const uint32_t locR = w0 >> 16, locV = w0 & 0xFFFFu;
                 if (locR != kKeep) {
-                    u64 xr[2 * NVR];
+                    u64 xr[G::half(RUN) ? 4 * NVR : 2 * NVR];
                     const unsigned p = (locR & kPoolBit) ? pool + 4u * (unsigned)((locR & 0x7FFFu) * CSP)
                                                          : cacheR + 4u * (unsigned)(locR * CSR);
+                    if constexpr (G::half(RUN)) {
 #pragma unroll
-                    for (int v = 0; v < NVR; ++v) lds2(p + 16 * v, xr[2 * v], xr[2 * v + 1]);
+                        for (int v = 0; v < NVR; ++v) {
+                            uint32_t w[4];
+                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                                         : "r"(p + 16 * v));
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                xr[4 * v + k] = pk(__uint_as_float(w[k] << 16),
+                                                   __uint_as_float(w[k] & 0xFFFF0000u));
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NVR; ++v) lds2(p + 16 * v, xr[2 * v], xr[2 * v + 1]);
+                    }
 #pragma unroll
                     for (int q = 0; q < H; ++q) wc[q] = xr[q];
                     if constexpr (FIRST) {
@@ -715,10 +732,11 @@ bool lean_pass_supported(int CM, int N) {
 int lean_run_mode(int n) { return n == 1 ? 1 : 0; }
 
 // Row geometry of other mode t (0 or 1) of mode n's pass: 16-byte vectors fetched, staged
-// stride in floats (the kernel's LG); vb: the varying mode's rows in bfloat16.
+// stride in floats (the kernel's LG); vb: bfloat16 rows of the varying mode (1) or of both
+// other modes (2).
 static void lean_geo(int CM, bool first, int n, int t, int vb, int &nv, int &cs) {
     const int cols = first ? (t < n ? 3 * CM : 2 * CM) : CM;
-    const bool half = vb != 0 && t == 1 - lean_run_mode(n);
+    const bool half = vb == 2 || (vb == 1 && t == 1 - lean_run_mode(n));
     nv = half ? (cols + 7) / 8 : (cols + 3) / 4;
     cs = (nv | 1) * 4;
 }
@@ -866,7 +884,10 @@ static void launch_lean_gk(const PassArgs<float> &a, const LeanPlan &pl, const G
                            cudaStream_t st) {
     if (pl.vb) {
         if (pl.gk != 0) throw ApiError{TF_EINVAL, "bfloat16 rows take the packed FMA Gram"};
-        launch_lean_cm<CM, 0, 1>(a, pl, gp, st);
+        if (pl.vb == 2)
+            launch_lean_cm<CM, 0, 2>(a, pl, gp, st);
+        else
+            launch_lean_cm<CM, 0, 1>(a, pl, gp, st);
         return;
     }
     switch (pl.gk) {

@@ -283,7 +283,7 @@ struct LeanPlan {
     LeanParams p;
     int warps = 0, grid = 0;
     int gk = 0;  // Gram: 0 packed FP32 FMAs, 1 one TF32 MMA product, 3 three (FP32-level)
-    int vb = 0;  // 1: the varying mode's rows from its bfloat16 slice copy
+    int vb = 0;  // bfloat16 slice rows: 1 of the varying mode, 2 of both other modes
     size_t smem = 0;
     double coverage = 0;  // entries whose varying-mode row is cached, fraction of all
 };
