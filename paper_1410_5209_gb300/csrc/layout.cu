@@ -153,8 +153,9 @@ struct XWord<8> {
 // the tile's staging area (keys, permutation, payload), then the tile's digit bases.
 template <int DB, int XB>
 struct ScatterLayout {
+    static constexpr bool kRecords = XB == 4;  // staged as one 16-byte record per key
     static constexpr int kCounters = kSortWarps * (1 << DB) * 2;
-    static constexpr int kStaging = kTile * (8 + 4 + XB);
+    static constexpr int kStaging = kRecords ? kTile * 16 : kTile * (8 + 4 + XB);
     static constexpr int kRegion = kCounters > kStaging ? kCounters : kStaging;
     static constexpr int kBytes = kRegion + 2 * (1 << DB) * 4 + kSortWarps * 4;
 };
@@ -256,23 +257,50 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_scatter64(
         if (base + r * kWarp + lane < n) loc[r] += tstart[d] + mycnt[d];
     }
     __syncthreads();  // the counters are dead: the staging area takes their place
+    // one base per digit from here on: the output position of tile position i is
+    // gbase[d] - tstart[d] + i (modulo 2^32)
+    for (int d = threadIdx.x; d < nb; d += kSortThreads) gbase[d] -= tstart[d];
+    const unsigned stage_s = (unsigned)__cvta_generic_to_shared(smem_raw);
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (base + r * kWarp + lane < n) {
-            skey[loc[r]] = key[r];
-            sval[loc[r]] = val[r];
-            if (XB > 0) sx[loc[r]] = xv[r];
+            if constexpr (L::kRecords) {
+                const uint32_t xw = XB > 0 ? (uint32_t)xv[r] : 0u;
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stage_s + 16u * loc[r]),
+                             "r"((uint32_t)key[r]), "r"((uint32_t)(key[r] >> 32)),
+                             "r"((uint32_t)val[r]), "r"(xw)
+                             : "memory");
+            } else {
+                skey[loc[r]] = key[r];
+                sval[loc[r]] = val[r];
+                sx[loc[r]] = xv[r];
+            }
         }
     }
     __syncthreads();
     const int tile_n = (int)(n - tile0 < kTile ? n - tile0 : kTile);
     for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
-        const uint64_t k = skey[i];
+        uint64_t k;
+        int32_t v;
+        XT xw = XT(0);
+        if constexpr (L::kRecords) {
+            uint32_t w0, w1, w2, w3;
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3)
+                         : "r"(stage_s + 16u * (unsigned)i));
+            k = (uint64_t)w0 | ((uint64_t)w1 << 32);
+            v = (int32_t)w2;
+            xw = (XT)w3;
+        } else {
+            k = skey[i];
+            v = sval[i];
+            xw = sx[i];
+        }
         const uint32_t d = (uint32_t)((k >> shift) & dmask);
-        const uint32_t dst = gbase[d] + (uint32_t)i - tstart[d];
+        const uint32_t dst = gbase[d] + (uint32_t)i;
         kout[dst] = k;
-        vout[dst] = sval[i];
-        if (XB > 0) xout[dst] = sx[i];
+        vout[dst] = v;
+        if (XB > 0) xout[dst] = xw;
     }
 }
 
