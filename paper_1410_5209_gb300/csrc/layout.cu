@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_scatter64(
             } else {
                 skey[loc[r]] = key[r];
                 sval[loc[r]] = val[r];
-                sx[loc[r]] = xv[r];
+                if constexpr (XB > 0) sx[loc[r]] = xv[r];
             }
         }
     }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_scatter64(
         } else {
             k = skey[i];
             v = sval[i];
-            xw = sx[i];
+            if constexpr (XB > 0) xw = sx[i];
         }
         const uint32_t d = (uint32_t)((k >> shift) & dmask);
         const uint32_t dst = gbase[d] + (uint32_t)i;
