@@ -1174,11 +1174,9 @@ struct Impl : CtxBase {
                         a.ticket = ticket.p;
                         a.ticket_base = ticket_base;
                         if (wide) {
-                            // float: the tensor-core Gram where it measures faster (the
-                            // 128-wide tile, C >= 64) or when requested (path 2); SIMT else
-                            const bool tc = sizeof(T) == 4 && path != 1 &&
-                                            (path == 2 || precision == 1 ||
-                                             wide_split_width(Cs, CM) == 128);
+                            // float: the Gram on the tensor cores (faster than the SIMT
+                            // Gram at every wide C measured) unless path 1 asks for SIMT
+                            const bool tc = sizeof(T) == 4 && path != 1;
                             const int wgrid = pass_wide_grid<T>(pass_sms(), L.P, Cs, CM, tc, t == 0);
                             // every block takes one ticket past the last bin
                             ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;

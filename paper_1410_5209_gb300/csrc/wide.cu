@@ -32,35 +32,87 @@ __device__ __forceinline__ T wsum(T v) {
     return v;
 }
 
-// Columns g, g + 8, ... (< CW) of one entry's H' row: h_c for c < C, and on the first
-// inner iteration the R-hat refresh products po (c < C) and pp (c < Cq).  The loop is
-// unrolled over the compile-time width so all slice-row loads issue together; three
-// modes (two other rows) take a path without the runtime mode loop.
+// 16-byte vector of slice values (4 floats or 2 doubles).
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static void unpack(const float4 &v, float (&x)[4]) {
+        x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+    }
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static void unpack(const double2 &v, double (&x)[2]) { x[0] = v.x, x[1] = v.y; }
+};
+
+// Columns of one entry's H' row taken by lane g of its 8 lanes: h_c for c < C, and on the
+// first inner iteration the R-hat refresh products po (c < C) and pp (c < Cq).  Three-mode
+// tensors (two other rows): lane g takes 16-byte vectors of columns VW g + 8 VW k .. + VW - 1
+// (VW = 4 floats or 2 doubles), so each row region is read with whole-vector loads, all
+// issued together; regions start at multiples of CM, a multiple of VW on this path, and
+// the packed slices hold zeros past C (cur, old) and past Cq (prev).  Other orders take
+// columns g, g + 8, ... one value at a time.
 template <class T, int CW, bool FIRST, class Store>
 __device__ __forceinline__ void wide_entry_columns(const T *const *rows, int no, int n_lo, int C,
                                                    int Cq, int CM, const T *own, bool valid,
                                                    int g, T &pp, T &po, Store store) {
+    if (no == 2) {
+        using V = typename Vec16<T>::type;
+        constexpr int VW = Vec16<T>::n;
+#pragma unroll
+        for (int k = 0; k < CW / (8 * VW); ++k) {
+            const int c0 = VW * g + 8 * VW * k;
+            T x0[VW], x1[VW], o0[VW], o1[VW], p0[VW], p1[VW];
+#pragma unroll
+            for (int u = 0; u < VW; ++u) x0[u] = x1[u] = o0[u] = o1[u] = p0[u] = p1[u] = T(0);
+            if (valid && c0 < CM) {
+                Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[0] + c0), x0);
+                Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[1] + c0), x1);
+                if (FIRST) {
+                    if (n_lo > 0)
+                        Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[0] + 2 * CM + c0), o0);
+                    if (n_lo > 1)
+                        Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[1] + 2 * CM + c0), o1);
+                    if (c0 < Cq) {
+                        Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[0] + CM + c0), p0);
+                        Vec16<T>::unpack(*reinterpret_cast<const V *>(rows[1] + CM + c0), p1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                const int c = c0 + u;
+                T hv = T(0);
+                if (valid && c < C) {
+                    hv = x0[u] * x1[u];
+                    if (FIRST) {
+                        const T a0 = n_lo > 0 ? o0[u] : x0[u];
+                        const T a1 = n_lo > 1 ? o1[u] : x1[u];
+                        po += own[CM + c] * (a0 * a1);
+                    }
+                }
+                if (FIRST && valid && c < Cq) pp += own[c] * (p0[u] * p1[u]);
+                store(c, hv);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < CW / 8; ++k) {
         const int c = g + 8 * k;
         T hv = T(0);
         if (valid && c < C) {
-            if (no == 2) {
-                const T x0 = rows[0][c], x1 = rows[1][c];
-                hv = x0 * x1;
-                if (FIRST) {
-                    const T o0 = n_lo > 0 ? rows[0][2 * CM + c] : x0;
-                    const T o1 = n_lo > 1 ? rows[1][2 * CM + c] : x1;
-                    po += own[CM + c] * (o0 * o1);
-                }
-            } else {
-                hv = T(1);
-                for (int t = 0; t < no; ++t) hv *= rows[t][c];
-                if (FIRST) {
-                    T o = own[CM + c];
-                    for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
-                    po += o;
-                }
+            hv = T(1);
+            for (int t = 0; t < no; ++t) hv *= rows[t][c];
+            if (FIRST) {
+                T o = own[CM + c];
+                for (int t = 0; t < no; ++t) o *= (t < n_lo ? rows[t][2 * CM + c] : rows[t][c]);
+                po += o;
             }
         }
         if (FIRST && valid && c < Cq) {
