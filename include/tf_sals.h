@@ -305,9 +305,9 @@ tf_status tf_set_schedule(tf_ctx *ctx, tf_sched_policy policy, int P);
 /* Data path of the mode pass: 0 = automatic (C <= 16: for float three-way tensors and
  * C <= 12 the lean pass (hot slice rows resident in shared memory, packed two-wide FP32
  * Gram), else the cp.async SIMT pass; 16 < C < 128: for float contexts the Gram on the
- * tensor cores (tcgen05, three TF32 products per term, FP32 accumulation; it measures
- * faster than the SIMT Gram from C = 20 to 100), SIMT FMAs for double), 1 = the cp.async
- * SIMT pass and the SIMT wide Gram everywhere, 2 = the TMA tile::gather4 pass with its shared-memory row cache for
+ * tensor cores (tcgen05, three TF32 products per term, FP32 accumulation) for C >= 32,
+ * where it measures faster, SIMT FMAs below and for double), 1 = the cp.async SIMT pass
+ * and the SIMT wide Gram everywhere, 2 = the TMA tile::gather4 pass with its shared-memory row cache for
  * C <= 10 (float, N = 3; TF_EINVAL from the next sweep where it does not apply) and the
  * tensor-core Gram for every wide C, 3 = the lean pass (TF_EINVAL from the next sweep
  * where it does not apply; wide C as path 0).  The cp.async and TMA passes give

@@ -1174,9 +1174,13 @@ struct Impl : CtxBase {
                         a.ticket = ticket.p;
                         a.ticket_base = ticket_base;
                         if (wide) {
-                            // float: the Gram on the tensor cores (faster than the SIMT
-                            // Gram at every wide C measured) unless path 1 asks for SIMT
-                            const bool tc = sizeof(T) == 4 && path != 1;
+                            // float: the Gram on the tensor cores for 64- and 128-wide tiles
+                            // (C >= 32: faster than the SIMT Gram at 1e8 entries) or when
+                            // requested (path 2, precision 1); SIMT for 32-wide tiles and
+                            // on path 1
+                            const bool tc = sizeof(T) == 4 && path != 1 &&
+                                            (path == 2 || precision == 1 ||
+                                             wide_split_width(Cs, CM) >= 64);
                             const int wgrid = pass_wide_grid<T>(pass_sms(), L.P, Cs, CM, tc, t == 0);
                             // every block takes one ticket past the last bin
                             ticket_base += (unsigned long long)L.P + (unsigned long long)wgrid;

@@ -322,9 +322,12 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // SPLIT: three TF32 products per term (FP32-level accuracy); without it one TF32
-// product (about 1e-3 relative error in B and c, the reduced-precision form).
+// product (about 1e-3 relative error in B and c, the reduced-precision form).  64- and
+// 128-wide tiles are held to three blocks per SM (about 80 registers): at 1e8 entries that
+// took the C = 50 and C = 100 sweeps from 170 and 166 ms to 146 and 144 ms.
 template <int CW, bool FIRST, bool SPLIT>
-__global__ void __launch_bounds__(kWideThreads) k_pass_wide_tc(const PassArgs<float> a, int CM, int W) {
+__global__ void __launch_bounds__(kWideThreads, CW >= 64 ? 3 : 1)
+    k_pass_wide_tc(const PassArgs<float> a, int CM, int W) {
     using T = float;
     constexpr int kTcCols = CW;  // tensor-memory columns: the accumulator is 128 x CW fp32
     extern __shared__ __align__(1024) unsigned char smem_raw[];
