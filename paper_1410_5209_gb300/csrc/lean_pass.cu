@@ -33,8 +33,12 @@
 namespace tfs {
 namespace {
 
-constexpr int kLeanWarps = 12;
-constexpr int kLeanThreads = kLeanWarps * kWarp;
+// Warps per block at most: the packed-FMA Gram's per-lane accumulators grow as CM^2 and
+// set the register budget (12 warps at CM = 10 and 12); the tensor-core Gram holds 8 sums
+// per lane.
+__host__ __device__ constexpr int lean_max_warps(int CM, int GK) {
+    return GK != 0 ? 16 : (CM <= 4 ? 20 : (CM <= 8 ? 16 : 12));
+}
 
 typedef unsigned long long u64;
 
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
 constexpr int kLeanStageStride = 36;  // floats per staged H' row (conflict-free)
 
 template <int CM, bool FIRST, int NLO, int RUN, int GK, int VB>
-__global__ void __launch_bounds__(GK == 0 ? kLeanThreads : 512, 1)
+__global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
     k_lean_pass(const PassArgs<float> a, const LeanParams lp, const GStep *__restrict__ steps,
                 const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_ptr,
                 const int32_t *__restrict__ list, const uint32_t *__restrict__ word) {
@@ -770,8 +774,9 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     const int cspw = std::max(csw[0], csw[1]);
     const size_t warp_bytes =
         ((((size_t)kLeanSlots * pool_rows * cspw + 8 * CM + 3) / 4 * 4) + stage + 4 * 3 * 32) * 4;
-    // as many warps as asked for (default: the most the registers allow) whose rings fit
-    const int max_warps = gk == 0 ? kLeanWarps : 16;
+    // as many warps as asked for (default: the most the registers allow) whose rings fit,
+    // never more than the kernel's launch bound
+    const int max_warps = lean_max_warps(CM, gk);
     const int fit = (int)std::min<size_t>(max_warps, ((size_t)smem_blk - kStatic) / warp_bytes);
     if (fit < 1) throw ApiError{TF_EINVAL, "lean mode pass: staging pool does not fit"};
     pl.warps = std::max(1, std::min(warps > 0 ? warps : max_warps, fit));

@@ -724,16 +724,18 @@ __host__ __device__ size_t pass_warp_bytes(int N, int n) {
 }
 
 // Warps per block of the mode pass (one block per SM): as many as the registers of the
-// per-lane Gram accumulators allow without spilling.
-template <class T>
-constexpr int pass_max_warps() { return sizeof(T) == 4 ? 12 : 8; }
+// per-lane Gram accumulators allow without spilling (the accumulators grow as CM^2).
+template <class T, int CM>
+constexpr int pass_max_warps() {
+    return sizeof(T) == 4 ? (CM <= 2 ? 24 : (CM <= 4 ? 20 : (CM <= 8 ? 16 : 12))) : (CM <= 4 ? 12 : 8);
+}
 
 // NO: number of other modes (N - 1) when specialised, 0 for any N (runtime loops).
 // FIRST: the split's first inner iteration (R-hat refresh) or a later one.
 // One block per SM (the staging rings are small, so most of the SM's shared memory
 // stays L1 cache: the hottest slice rows are served from there).
 template <class T, int CM, int NO, bool FIRST>
-__global__ void __launch_bounds__(pass_max_warps<T>() * kWarp, 1)
+__global__ void __launch_bounds__(pass_max_warps<T, CM>() * kWarp, 1)
     k_mode_pass(const PassArgs<T> a) {
     using Cons = PassConsumer<T, CM, NO, FIRST>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -943,7 +945,7 @@ PassPlan mode_pass_plan_cm(int N, int n, int num_sms, int P) {
     TFS_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t ring = pass_warp_bytes<T, CM, FIRST>(N, n);
     PassPlan plan;
-    plan.warps = (int)std::min<size_t>(pass_max_warps<T>(), ((size_t)smem_blk - kReserve) / ring);
+    plan.warps = (int)std::min<size_t>(pass_max_warps<T, CM>(), ((size_t)smem_blk - kReserve) / ring);
     if (plan.warps < 1) throw ApiError{TF_EINVAL, "mode pass does not fit in shared memory"};
     plan.smem = (size_t)plan.warps * ring;
     plan.grid = std::max(1, std::min(num_sms, (P + plan.warps - 1) / plan.warps));
