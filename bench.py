@@ -556,13 +556,22 @@ def fiveway_config(args, nnz, hbm):
     stream = nnz * (N * (4 * (N - 1) + 4) + 4) * splits
     gathers = nnz * N * (N - 1) * 4 * C * splits
     achieved = (stream + gathers) / (ms / 1e3) / 1e9
+    # the gathers with the R-hat refresh regions every pass reads: each other mode's row
+    # brings its current and previous columns, and for modes updated earlier in the split
+    # its old ones too: (N - 1) * 2.5 * C values per entry and pass on average over the modes
+    gathers_r = nnz * N * (N - 1) * 2.5 * 4 * C * splits
+    achieved_r = (stream + gathers_r) / (ms / 1e3) / 1e9
     return {"nnz": nnz, "dims": list(dims), "K": K, "C": C, "ms_per_sweep": ms,
             "nnz_rank_per_s": nnz * K / (ms / 1e3), "train_rmse_after": rmse,
             "roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": stream + gathers,
                          "stream_bytes": stream, "gather_bytes": gathers,
                          "floor_ms": (stream + gathers) / (hbm * 1e9) * 1e3,
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm},
+                         "frac": achieved / hbm,
+                         "with_refresh_regions": {
+                             "gather_bytes": gathers_r,
+                             "floor_ms": (stream + gathers_r) / (hbm * 1e9) * 1e3,
+                             "achieved": achieved_r, "frac": achieved_r / hbm}},
             "generate_s": gen_s, "create_s": create_s}
 
 
