@@ -73,10 +73,10 @@ def pass_units(nnz, N, C, avg_launch_ms):
 
 
 def kernel_source_hash():
-    """Hash of the source of the dominant kernel (k_lean_pass and its plan) and of the
-    header that sets its launch shape (the default bin count)."""
+    """Hash of the source of the dominant kernel (k_lean_pass), of the plan records it
+    reads and of the header that sets its launch shape (the default bin count)."""
     h = hashlib.sha256()
-    for f in ("lean_pass.cu", "sweep.cuh"):
+    for f in ("lean_pass.cu", "gather_plan.cuh", "sweep.cuh"):
         with open(os.path.join(ROOT, "paper_1410_5209_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -17,6 +17,7 @@
 
 #include <cuda.h>
 
+#include "gather_plan.cuh"
 #include "layout.cuh"
 #include "sweep.cuh"
 
@@ -153,12 +154,15 @@ struct ModeLayout {
     Buf<int32_t> groups;    // slot groups of split rows (first slot, count), wide subsets
     int n_groups = 0;
     std::vector<int64_t> deg_cum;  // host: entries of the first R rows in degree-rank order
+    // per bin, the step units and entries of the bins before it (gather-plan regions)
+    Buf<uint32_t> plan_base;  // [2 (P + 1)]
+    int64_t plan_units = 0;   // step units of all bins
     int P = 0;
     int omode[kMaxModes - 1];
     template <class F>
     void each_buf(F f) {
         f(off), f(perm), f(oidx), f(items), f(bin_ptr), f(split), f(single), f(rank_of),
-            f(id_of), f(groups);
+            f(id_of), f(groups), f(plan_base);
     }
 };
 
@@ -229,8 +233,8 @@ struct Impl : CtxBase {
     struct GatherPlan {
         int n = -1, RR = 0, RV = 0, cap = 0, first = 0;
         int64_t layout_gen = -1;
-        Buf<unsigned char> steps;  // GStep records then the per-step own-row ranks
-        Buf<uint32_t> step_ptr, word;
+        Buf<unsigned char> steps;  // GStep records then the per-record own-row ranks
+        Buf<uint32_t> step_range, word;
         Buf<int32_t> list;
         int64_t nsteps = 0;
         uint64_t used = 0;  // last use (LRU)
@@ -263,7 +267,7 @@ struct Impl : CtxBase {
             f(A[n]), f(res[n]), f(Z[n]), f(Zb[n]);
             mode[n].each_buf(f);
         }
-        for (auto &g : gplans) f(g->steps), f(g->step_ptr), f(g->word), f(g->list);
+        for (auto &g : gplans) f(g->steps), f(g->step_range), f(g->word), f(g->list);
     }
 
     ~Impl() override {
@@ -830,6 +834,31 @@ struct Impl : CtxBase {
                                      cudaMemcpyHostToDevice, st));
         TFS_CUDA(cudaMemcpyAsync(L.bin_ptr.p, h.bin_ptr.data(), h.bin_ptr.size() * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st));
+        {
+            // gather-plan regions: step units (max(1, ceil(len / 32)) per item) and entries
+            // of the bins before each bin
+            const int Pn = (int)h.bin_ptr.size() - 1;
+            std::vector<uint32_t> base((size_t)2 * (Pn + 1), 0u);
+            uint64_t su = 0, se = 0;
+            for (int b = 0; b < Pn; ++b) {
+                base[b] = (uint32_t)su;
+                base[Pn + 1 + b] = (uint32_t)se;
+                for (int64_t it = h.bin_ptr[b]; it < h.bin_ptr[b + 1]; ++it) {
+                    const int64_t len = h.items[it].len;
+                    su += (uint64_t)std::max<int64_t>(1, (len + 31) / 32);
+                    se += (uint64_t)len;
+                }
+            }
+            base[Pn] = (uint32_t)su;
+            base[2 * Pn + 1] = (uint32_t)se;
+            if (su > 0xFFFFFFFFull || se > 0x7FFFFFFFull)
+                throw ApiError{TF_EINVAL, "too many entries for the gather plan's 32-bit offsets"};
+            L.plan_units = (int64_t)su;
+            L.plan_base.alloc(base.size(), st);
+            // pageable source: the call returns once the bytes are staged
+            TFS_CUDA(cudaMemcpyAsync(L.plan_base.p, base.data(), base.size() * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, st));
+        }
         if (!h.split.empty())
             TFS_CUDA(cudaMemcpyAsync(L.split.p, h.split.data(), h.split.size() * sizeof(SplitRow),
                                      cudaMemcpyHostToDevice, st));
@@ -949,24 +978,27 @@ struct Impl : CtxBase {
 
     // ------------------------------------------------------------ lean-pass gather plans
     // The plan of mode n's lean pass for cache rows (RR, RV) of its run / varying modes
-    // and a pool of cap rows: built on the device (a counting pass, two scans, an emitting
-    // pass) the first time a split needs it, then kept (one per mode) until the row
-    // schedule or the cache sizes change.  The refreshing and the plain inner iterations
-    // share it: their cache sizes are both planned for the refreshing pass's wider rows.
+    // and a pool of cap rows: built on the device in one pass (gather_plan.cu) the first
+    // time a split needs it, then kept (one per mode) until the row schedule or the cache
+    // sizes change.  The refreshing and the plain inner iterations share it: their cache
+    // sizes are both planned for the refreshing pass's wider rows.
     GatherPlanDev gather_plan(int n, int RR, int RV, int cap) {
         const int first = 1;
         const ModeLayout &L = mode[n];
+        auto dev_of = [](const GatherPlan &g) {
+            GatherPlanDev d;
+            d.steps = g.steps.p;
+            d.rank = reinterpret_cast<const int32_t *>(g.steps.p + (size_t)g.nsteps * sizeof(GStep));
+            d.step_range = g.step_range.p;
+            d.list = g.list.p;
+            d.word = g.word.p;
+            return d;
+        };
         for (auto &g : gplans)
             if (g->n == n && g->RR == RR && g->RV == RV && g->cap == cap &&
                 g->layout_gen == layout_gen) {
                 g->used = ++gplan_clock;
-                GatherPlanDev d;
-                d.steps = g->steps.p;
-                d.rank = reinterpret_cast<const int32_t *>(g->steps.p + (size_t)g->nsteps * 16);
-                d.step_ptr = g->step_ptr.p;
-                d.list = g->list.p;
-                d.word = g->word.p;
-                return d;
+                return dev_of(*g);
             }
         // drop plans of an old schedule and this mode's plan for other cache sizes; sweep
         // graphs captured with a dropped plan go too (they hold its addresses)
@@ -983,45 +1015,21 @@ struct Impl : CtxBase {
         const int Pn = L.P;
         const int run = lean_run_mode(n), var = 1 - run;
         const int32_t *ixR = L.oidx.p + (size_t)run * L.ostride, *ixV = L.oidx.p + (size_t)var * L.ostride;
-        Buf<uint32_t> cnt, tmp;
-        cnt.alloc((size_t)2 * Pn + 2, st);
-        TFS_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)2 * Pn + 2) * sizeof(uint32_t), st));
-        launch_gather_plan(L.items.p, L.bin_ptr.p, Pn, ixR, ixV, L.rank_of.p, RR, RV, cap, first,
-                           cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, st);
-        // step counts cnt[0 .. P), list counts cnt[P .. 2P): exclusive scans over P + 1
-        g->step_ptr.alloc((size_t)Pn + 1, st);
-        Buf<uint32_t> list_ptr;
-        list_ptr.alloc((size_t)Pn + 1, st);
-        Buf<uint32_t> lcnt;
-        lcnt.alloc((size_t)Pn + 1, st);
-        TFS_CUDA(cudaMemcpyAsync(lcnt.p, cnt.p + Pn, (size_t)Pn * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToDevice, st));
-        TFS_CUDA(cudaMemsetAsync(lcnt.p + Pn, 0, sizeof(uint32_t), st));
-        TFS_CUDA(cudaMemsetAsync(cnt.p + Pn, 0, sizeof(uint32_t), st));
-        tmp.alloc(scan_temp_elems((int64_t)Pn + 1), st);
-        scan_exclusive_u32(cnt.p, g->step_ptr.p, (int64_t)Pn + 1, tmp.p, st);
-        scan_exclusive_u32(lcnt.p, list_ptr.p, (int64_t)Pn + 1, tmp.p, st);
-        uint32_t tot[2];
-        TFS_CUDA(cudaMemcpyAsync(&tot[0], g->step_ptr.p + Pn, sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, st));
-        TFS_CUDA(cudaMemcpyAsync(&tot[1], list_ptr.p + Pn, sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, st));
-        TFS_CUDA(cudaStreamSynchronize(st));
-        g->nsteps = tot[0];
-        g->steps.alloc((size_t)std::max<uint32_t>(tot[0], 1) * gather_plan_step_bytes(), st);
-        g->list.alloc((size_t)std::max<uint32_t>(tot[1], 1), st);
+        // regions from the schedule: plan_records_per_step(cap) records per step unit, two
+        // list entries per entry
+        const int64_t cap_steps = (int64_t)plan_records_per_step(cap) * L.plan_units;
+        if (cap_steps > INT32_MAX)
+            throw ApiError{TF_EINVAL, "gather plan: too many records for this pool size"};
+        g->nsteps = std::max<int64_t>(cap_steps, 1);
+        g->steps.alloc((size_t)g->nsteps * gather_plan_step_bytes(), st);
+        g->step_range.alloc((size_t)2 * std::max(Pn, 1), st);
+        g->list.alloc((size_t)std::max<int64_t>(2 * nnz, 1), st);
         g->word.alloc((size_t)std::max<int64_t>(nnz, 1), st);
-        int32_t *rank = reinterpret_cast<int32_t *>(g->steps.p + (size_t)g->nsteps * 16);
+        GatherPlanDev d = dev_of(*g);
         launch_gather_plan(L.items.p, L.bin_ptr.p, Pn, ixR, ixV, L.rank_of.p, RR, RV, cap, first,
-                           nullptr, g->step_ptr.p, list_ptr.p, g->steps.p, rank, g->list.p,
-                           g->word.p, 1, st);
+                           L.plan_base.p, g->step_range.p, g->steps.p,
+                           const_cast<int32_t *>(d.rank), g->list.p, g->word.p, stat.p, st);
         g->used = ++gplan_clock;
-        GatherPlanDev d;
-        d.steps = g->steps.p;
-        d.rank = rank;
-        d.step_ptr = g->step_ptr.p;
-        d.list = g->list.p;
-        d.word = g->word.p;
         gplans.push_back(std::move(g));
         return d;
     }
@@ -1570,6 +1578,11 @@ struct Impl : CtxBase {
             TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
             TFS_CUDA(cudaStreamSynchronize(st));
             throw ApiError{TF_ETIMEOUT, "a bounded wait in a kernel gave up; results are invalid"};
+        }
+        if (s.bits & kStatPlan) {
+            TFS_CUDA(cudaMemsetAsync(&stat.p->bits, 0, sizeof(int), st));
+            TFS_CUDA(cudaStreamSynchronize(st));
+            throw ApiError{TF_ECUDA, "a gather plan outgrew its bound; results are invalid"};
         }
         if (s.bits & (kStatRange | kStatDup)) throw ApiError{TF_ECUDA, "device status corrupt"};
     }
@@ -2239,15 +2252,17 @@ tf_status tf_estimate_bytes(const int64_t *dims, int N, int64_t nnz, int K, int 
         sorting = x + soa + e * 4 + (double)tfs::sort_workspace_bytes(nnz) + layout;
     }
     const double partials = (maxI + P) * tfs::partial_stride(CM) * T;
-    // gather plans of the lean float pass (three-way tensors), one per mode: a location
-    // word per entry, at most two list entries per entry, at most three records per
-    // 32-entry step (a record holds at least half a pool of rows' worth of lanes)
+    // gather plans of the lean float pass (three-way tensors), one per mode, in the regions
+    // they are built into: a location word and two list entries per entry, and at the
+    // default pool of 32 rows three records per step unit (max(1, ceil(len / 32)) of each
+    // item, at most len / 32 + 1; items are at most the rows plus one chunk per bin)
     double gplans = 0;
     if (dtype == TF_F32 && N == 3)
         for (int n = 0; n < N; ++n)
             gplans += e * 4 + e * 8 +
-                      (3.0 * e / 32 + 3.0 * ((double)dims[n] + P)) * tfs::gather_plan_step_bytes() +
-                      (P + 1) * 4 * 2;
+                      tfs::plan_records_per_step(32) * (e / 32 + (double)dims[n] + P) *
+                          tfs::gather_plan_step_bytes() +
+                      (P + 1) * 4 * 4;
     const double steady = x + layout + plan + factors + partials + gplans;
     // stream-ordered pool rounding: large buffers round up to the pool's 2 MiB mapping
     // granularity (at most 2 MiB each), small ones share chunks

@@ -22,6 +22,7 @@ enum : int {
     kStatFoldPivot = 8,  // fold-in Cholesky pivot <= 0
     kStatTimeout = 16,   // a bounded wait on the device gave up
     kStatPredictRange = 32,  // tf_predict coordinate out of range
+    kStatPlan = 64,          // a gather plan outgrew its bound (internal error)
 };
 
 struct DeviceStatus {

@@ -10,12 +10,13 @@
 //     most entries gather; each pass copies them once per block.  The host picks R per
 //     other mode from the modes' degree sums so that the cached rows cover the most
 //     entries that fit.
-//   * The plan (k_gather_plan) cuts each item (a row or row chunk) into steps of up to 32
-//     consecutive entries, short enough that a step's distinct cold rows (rows outside the
-//     caches; consecutive equal indices are one row) fit a warp's staging pool, lists those
-//     rows per step, and gives every entry one 32-bit word: where its varying-mode row is
-//     (cache row or pool position) and where its run-mode row is, or that the lane already
-//     holds the products of that row (the same run index as the lane's previous entry).
+//   * The plan (k_gather_plan, gather_plan.cu) cuts each item (a row or row chunk) into
+//     steps of up to 32 consecutive entries, short enough that a step's distinct cold rows
+//     (rows outside the caches; consecutive equal indices are one row) fit a warp's staging
+//     pool, lists those rows per step, and gives every entry one 32-bit word: where its
+//     varying-mode row is (cache row or pool position) and where its run-mode row is, or
+//     that the lane already holds the products of that row (the same run index as the
+//     lane's previous entry).
 //   * The pass (k_lean_pass) walks a bin's steps: it loads the entries' words and residuals
 //     and the steps' cold-row lists three steps ahead, stages the listed rows two steps
 //     ahead with 16-byte cp.async (a fixed group of lanes per row), and computes: per lane,
@@ -28,6 +29,7 @@
 #include <algorithm>
 #include <numeric>
 
+#include "gather_plan.cuh"
 #include "sweep.cuh"
 
 namespace tfs {
@@ -145,161 +147,6 @@ struct LG {
 };
 
 constexpr int kLeanSlots = 3;        // pool slots: cold rows are staged two steps ahead
-constexpr uint32_t kPoolBit = 0x8000u, kKeep = 0xFFFFu;
-
-// Step record of a gather plan: lanes [lo, hi) of the 32-entry step starting at entry j0
-// of one item (a step's lanes are split over several records when its distinct cold rows
-// exceed the pool; each lane still takes the same entry as in an unsplit step, so the
-// per-lane sums, and the results, do not depend on the split).  info packs hi (bits 0-5),
-// first record of the item (6), last record of the item (7), own-row buffer (8-9), staged
-// varying-mode rows nV (10-15), run-mode rows nR (16-21) and lo (22-26); the record's cold
-// rows are list[list_off .. + nV + nR) (varying first).
-struct GStep {
-    int32_t j0, list_off;
-    uint32_t info;
-    int32_t slot;  // partial slot of the item
-};
-
-// ---------------------------------------------------------------------------- planning
-// One warp per bin.  emit = 0: counts the bin's records and list entries into cnt[b] and
-// cnt[P + b].  emit = 1: writes them at step_ptr[b] / list_ptr[b] (exclusive scans of the
-// counts) and every entry's word.
-struct GPlanArgs {
-    const tf_item *items;
-    const int64_t *bin_ptr;
-    int P;
-    const int32_t *ixR, *ixV;  // run / varying mode index streams (slice ranks)
-    const int32_t *rank_n;     // own row -> slice rank
-    int RR, RV, cap, first;
-    uint32_t *cnt;
-    const uint32_t *step_ptr, *list_ptr;
-    GStep *steps;
-    int32_t *rank;   // own slice rank per record (first records of items)
-    int32_t *list;
-    uint32_t *word;  // per entry: varying location | run location << 16
-    int emit;
-};
-
-__global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
-    const int lane = threadIdx.x & 31;
-    const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (b >= g.P) return;
-    const uint32_t lt = (1u << lane) - 1u, le = lt | (1u << lane);
-    uint32_t ns = 0, nl = 0;
-    const uint32_t s0 = g.emit ? g.step_ptr[b] : 0u, l0 = g.emit ? g.list_ptr[b] : 0u;
-    const int64_t it0 = g.bin_ptr[b], it1 = g.bin_ptr[b + 1];
-    // The bin's steps in order, the next step's index pair (and the next item's record
-    // and own rank) loaded before the current step is worked on, so a warp keeps two
-    // steps' loads in flight instead of waiting on each.
-    if (it0 < it1) {
-        int64_t it = it0;
-        tf_item x = g.items[it];
-        tf_item xn = it + 1 < it1 ? g.items[it + 1] : x;
-        int own = g.emit && g.first ? g.rank_n[x.row] : 0;
-        int own_n = g.emit && g.first && it + 1 < it1 ? g.rank_n[xn.row] : 0;
-        int j = (int)x.begin, jend = (int)(x.begin + x.len);
-        int prevR = -1;  // run index of this lane's previous entry in the item
-        bool first = true;
-        int cV, cR;  // the current step's indices (-1 past its end)
-        {
-            const bool v = lane < min(kWarp, jend - j);
-            cV = v ? g.ixV[j + lane] : -1;
-            cR = v ? g.ixR[j + lane] : -1;
-        }
-        for (;;) {
-            const int cmax = min(kWarp, jend - j);
-            const bool valid = lane < cmax;
-            const bool more_in_item = j + cmax < jend;
-            const bool more = more_in_item || it + 1 < it1;
-            // the next step: this item's next 32 entries, or the next item's first
-            int nV = -1, nR = -1;
-            if (more) {
-                const int jn = more_in_item ? j + cmax : (int)xn.begin;
-                const int jnend = more_in_item ? jend : (int)(xn.begin + xn.len);
-                if (lane < min(kWarp, jnend - jn)) {
-                    nV = g.ixV[jn + lane];
-                    nR = g.ixR[jn + lane];
-                }
-            }
-            const int iV = cV, iR = cR;
-            const int pV = __shfl_up_sync(0xFFFFFFFFu, iV, 1), pR = __shfl_up_sync(0xFFFFFFFFu, iR, 1);
-            const bool coldV = valid && iV >= g.RV;
-            const bool need = valid && (first || iR != prevR);
-            const bool coldR = need && iR >= g.RR;
-            const uint32_t mV = __ballot_sync(0xFFFFFFFFu, coldV);
-            const uint32_t mR = __ballot_sync(0xFFFFFFFFu, coldR);
-            // records of this step: lanes [lo, hi), the most whose distinct cold rows fit
-            int lo = 0;
-            do {
-                // heads relative to the record's first lane
-                const bool pcV = lane > lo && ((mV >> (lane - 1)) & 1u);
-                const bool pcR = lane > lo && ((mR >> (lane - 1)) & 1u);
-                const uint32_t from = lo >= 32 ? 0u : ~((1u << lo) - 1u);
-                const uint32_t hV = __ballot_sync(0xFFFFFFFFu, coldV && (!pcV || pV != iV)) & from;
-                const uint32_t hR = __ballot_sync(0xFFFFFFFFu, coldR && (!pcR || pR != iR)) & from;
-                const int upto = __popc(hV & le) + __popc(hR & le);
-                const int hi = cmax > 0
-                                   ? lo + __popc(__ballot_sync(0xFFFFFFFFu,
-                                                               valid && lane >= lo && upto <= g.cap))
-                                   : 0;
-                const uint32_t keep = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & from;
-                const int nVr = __popc(hV & keep), nRr = __popc(hR & keep);
-                if (g.emit) {
-                    if (lane >= lo && lane < hi) {
-                        const uint32_t locV =
-                            coldV ? (kPoolBit | (uint32_t)(__popc(hV & le) - 1)) : (uint32_t)iV;
-                        const uint32_t locR =
-                            !need   ? kKeep
-                            : coldR ? (kPoolBit | (uint32_t)(nVr + __popc(hR & le) - 1))
-                                    : (uint32_t)iR;
-                        g.word[j + lane] = locV | (locR << 16);
-                        if ((hV >> lane) & 1u) g.list[l0 + nl + __popc(hV & lt)] = iV;
-                        if ((hR >> lane) & 1u) g.list[l0 + nl + nVr + __popc(hR & lt)] = iR;
-                    }
-                    if (lane == 0) {
-                        GStep st;
-                        st.j0 = j;
-                        st.list_off = (int32_t)(l0 + nl);
-                        const bool last = hi >= cmax && !more_in_item;
-                        st.info = (uint32_t)hi | (first && lo == 0 ? 64u : 0u) | (last ? 128u : 0u) |
-                                  ((uint32_t)((it - it0) & 3) << 8) | ((uint32_t)nVr << 10) |
-                                  ((uint32_t)nRr << 16) | ((uint32_t)lo << 22);
-                        st.slot = x.slot;
-                        g.steps[s0 + ns] = st;
-                        g.rank[s0 + ns] = own;
-                    }
-                }
-                ++ns;
-                nl += (uint32_t)(nVr + nRr);
-                lo = hi;
-            } while (lo < cmax);
-            if (!more) break;
-            cV = nV;
-            cR = nR;
-            if (more_in_item) {
-                if (valid) prevR = iR;
-                j += cmax;
-                first = false;
-            } else {
-                ++it;
-                x = xn;
-                own = own_n;
-                if (it + 1 < it1) {
-                    xn = g.items[it + 1];
-                    own_n = g.emit && g.first ? g.rank_n[xn.row] : 0;
-                }
-                j = (int)x.begin;
-                jend = (int)(x.begin + x.len);
-                prevR = -1;
-                first = true;
-            }
-        }
-    }
-    if (!g.emit && lane == 0) {
-        g.cnt[b] = ns;
-        g.cnt[g.P + b] = nl;
-    }
-}
 
 // ---------------------------------------------------------------------------- the pass
 // GK: how the Gram matrix and right-hand side are accumulated.  0: per lane, packed
@@ -315,7 +162,7 @@ constexpr int kLeanStageStride = 36;  // floats per staged H' row (conflict-free
 template <int CM, bool FIRST, int NLO, int RUN, int GK, int VB>
 __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
     k_lean_pass(const PassArgs<float> a, const LeanParams lp, const GStep *__restrict__ steps,
-                const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_ptr,
+                const int32_t *__restrict__ srank, const uint32_t *__restrict__ step_range,
                 const int32_t *__restrict__ list, const uint32_t *__restrict__ word) {
     using G = LG<CM, FIRST, NLO, RUN, VB>;
     constexpr int H = G::H, W = G::W, NACC = G::NACC, VAR = G::VAR;
@@ -396,7 +243,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
     for (;;) {
         const unsigned long long tk = tk_next;
         if (tk >= (unsigned long long)a.P) break;
-        const int s_begin = (int)step_ptr[tk], s_end = (int)step_ptr[tk + 1];
+        const int s_begin = (int)step_range[2 * tk], s_end = (int)step_range[2 * tk + 1];
         if (lane == 0) tk_next = atomicAdd(a.ticket, 1ull) - a.ticket_base;
         tk_next = __shfl_sync(0xFFFFFFFFu, tk_next, 0);
         // the bin's step records, one per lane (steps wb + lane), reloaded as needed
@@ -405,7 +252,8 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
         int rrank = 0;
         auto window = [&](int base) {
             wb = base;
-            rec.j0 = rec.list_off = rec.slot = 0;
+            rec.j0 = rec.slot = 0;
+            rec.list_off = 0u;
             rec.info = 0u;
             rrank = 0;
             if (base + lane < s_end) {
@@ -438,9 +286,9 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
         auto load_list = [&](int s) {
             if (s >= s_end) return;
             const uint32_t inf = __shfl_sync(0xFFFFFFFFu, rec.info, s - wb);
-            const int loff = __shfl_sync(0xFFFFFFFFu, rec.list_off, s - wb);
+            const uint32_t loff = __shfl_sync(0xFFFFFFFFu, rec.list_off, s - wb);
             const int nlist = (int)((inf >> 10) & 63u) + (int)((inf >> 16) & 63u);
-            if (lane < nlist) cp4(str_at(s, 2), list + loff + lane);
+            if (lane < nlist) cp4(str_at(s, 2), list + (size_t)loff + lane);
         };
         // stages step s's cold rows (list entries held by its lanes) into pool slot `slot`,
         // and on an item's first step the own row's prev | old regions
@@ -825,45 +673,13 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     return pl;
 }
 
-size_t gather_plan_step_bytes() { return sizeof(GStep) + sizeof(int32_t); }
-
-void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,
-                        const int32_t *ixV, const int32_t *rank_n, int RR, int RV, int cap,
-                        int first, uint32_t *cnt, const uint32_t *step_ptr,
-                        const uint32_t *list_ptr, void *steps, int32_t *rank, int32_t *list,
-                        uint32_t *word, int emit, cudaStream_t st) {
-    GPlanArgs g{};
-    g.items = items;
-    g.bin_ptr = bin_ptr;
-    g.P = P;
-    g.ixR = ixR;
-    g.ixV = ixV;
-    g.rank_n = rank_n;
-    g.RR = RR;
-    g.RV = RV;
-    g.cap = cap;
-    g.first = first;
-    g.cnt = cnt;
-    g.step_ptr = step_ptr;
-    g.list_ptr = list_ptr;
-    g.steps = static_cast<GStep *>(steps);
-    g.rank = rank;
-    g.list = list;
-    g.word = word;
-    g.emit = emit;
-    const int threads = 256;
-    const int blocks = (int)(((int64_t)P * 32 + threads - 1) / threads);
-    k_gather_plan<<<blocks, threads, 0, st>>>(g);
-    TFS_CUDA(cudaGetLastError());
-}
-
 template <int CM, bool FIRST, int NLO, int RUN, int GK, int VB>
 static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                           cudaStream_t st) {
     auto kern = k_lean_pass<CM, FIRST, NLO, RUN, GK, VB>;
     TFS_CUDA(raise_smem_limit((const void *)kern, (int)pl.smem));
     kern<<<pl.grid, pl.warps * kWarp, pl.smem, st>>>(
-        a, pl.p, static_cast<const GStep *>(gp.steps), gp.rank, gp.step_ptr, gp.list, gp.word);
+        a, pl.p, static_cast<const GStep *>(gp.steps), gp.rank, gp.step_range, gp.list, gp.word);
     TFS_CUDA(cudaGetLastError());
 }
 

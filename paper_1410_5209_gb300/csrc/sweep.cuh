@@ -288,13 +288,13 @@ struct LeanPlan {
     double coverage = 0;  // entries whose varying-mode row is cached, fraction of all
 };
 
-// Device arrays of a gather plan (lean_pass.cu): per bin its steps step_ptr[b] ..
-// step_ptr[b + 1] - 1 (16-byte records), the own-row rank of each step, the steps'
+// Device arrays of a gather plan (gather_plan.cu): per bin its records step_range[2b] ..
+// step_range[2b + 1] - 1 (16-byte records), the own-row rank of each record, the records'
 // cold-row lists and one location word per entry.
 struct GatherPlanDev {
     const void *steps = nullptr;
     const int32_t *rank = nullptr;
-    const uint32_t *step_ptr = nullptr;
+    const uint32_t *step_range = nullptr;
     const int32_t *list = nullptr;
     const uint32_t *word = nullptr;
 };
@@ -315,12 +315,17 @@ inline int slice_bf16_stride(int CM) { return (3 * CM + 7) / 8 * 8; }
 void launch_slice_bf16(const float *Z, uint16_t *Zb, int64_t rows, int W, int Wb, int col0,
                        int ncols, cudaStream_t st);
 size_t gather_plan_step_bytes();  // bytes per step record (+ its own-row rank)
-// emit = 0: per-bin step and list counts into cnt[b] / cnt[P + b]; emit = 1: the plan.
+// The plan of one mode in one launch.  base[b] (b <= P) counts the step units of the bins
+// before b (an item of len entries has max(1, ceil(len / 32))), base[P + 1 + b] their
+// entries; bin b's records go to [rmax * base[b], rmax * base[b + 1]) of steps / rank and
+// its lists to [2 base[P + 1 + b], 2 base[P + 2 + b]) of list, rmax =
+// plan_records_per_step(cap); range[2b], range[2b + 1] receive the bin's first and end
+// record.  Overrunning a region (which the bounds exclude) sets kStatPlan.
 void launch_gather_plan(const tf_item *items, const int64_t *bin_ptr, int P, const int32_t *ixR,
                         const int32_t *ixV, const int32_t *rank_n, int RR, int RV, int cap,
-                        int first, uint32_t *cnt, const uint32_t *step_ptr,
-                        const uint32_t *list_ptr, void *steps, int32_t *rank, int32_t *list,
-                        uint32_t *word, int emit, cudaStream_t st);
+                        int first, const uint32_t *base, uint32_t *range, void *steps,
+                        int32_t *rank, int32_t *list, uint32_t *word, DeviceStatus *stat,
+                        cudaStream_t st);
 void launch_lean_pass(const PassArgs<float> &a, int CM, const LeanPlan &pl,
                       const GatherPlanDev &gp, cudaStream_t st);
 
