@@ -841,6 +841,7 @@ def main():
     p = synth.skewed_3way(seed=args.seed + rank, nnz=args.nnz, device="cuda")
     nnz, N = p.nnz, p.N
     stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()  # the generator's kernels are not part of the build
     t0 = time.perf_counter()
     f = tf.Factorization(p.coords, p.x, p.dims, K, seed=args.seed + rank, dtype=tf.F32,
                          stream=stream.cuda_stream, device_input=True)

@@ -106,6 +106,49 @@ PinnedCache &pinned_cache() {
     return c;
 }
 
+// Page-locked staging of host-to-device copies queued on a stream.  cudaMemcpyAsync from
+// pageable memory returns only once the stream has reached the copy, which would hold
+// the host behind all device work queued before it; from page-locked memory it returns at
+// once.  The blocks go back to the cache after the stream has passed the last copy out of
+// them (also when the caller fails part way).
+struct PinnedStage {
+    std::vector<std::pair<void *, size_t>> blocks;
+    cudaEvent_t done = nullptr;
+    char *arena = nullptr;  // one block taken up front, handed out in 16-byte steps
+    size_t arena_bytes = 0, used = 0;
+    // Takes the block before any device work is queued: a first page-locked allocation
+    // is not stream-ordered and would otherwise wait on the work queued before it.
+    void reserve(size_t bytes) {
+        arena = static_cast<char *>(pinned_cache().get(bytes));
+        blocks.emplace_back(arena, bytes);
+        arena_bytes = bytes;
+    }
+    void copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+        if (bytes == 0) return;
+        void *p = nullptr;
+        const size_t at = (used + 15) / 16 * 16;
+        if (arena && at + bytes <= arena_bytes) {
+            p = arena + at;
+            used = at + bytes;
+        } else {
+            p = pinned_cache().get(bytes);
+            blocks.emplace_back(p, bytes);
+        }
+        memcpy(p, src, bytes);
+        if (!done) TFS_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        TFS_CUDA(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, st));
+        TFS_CUDA(cudaEventRecord(done, st));
+    }
+    PinnedStage() = default;
+    PinnedStage(const PinnedStage &) = delete;
+    PinnedStage &operator=(const PinnedStage &) = delete;
+    ~PinnedStage() {
+        if (done) cudaEventSynchronize(done);
+        for (auto &b : blocks) pinned_cache().put(b.first, b.second);
+        if (done) cudaEventDestroy(done);
+    }
+};
+
 cudaMemPool_t library_pool() {
     static std::mutex mu;
     static std::map<int, cudaMemPool_t> pools;
@@ -350,6 +393,10 @@ struct Impl : CtxBase {
         std::vector<SplitRow> split, single;
         std::vector<int32_t> groups;  // slot groups of rows with many chunks (wide subsets)
         int64_t n_slots = 0;
+        // gather-plan regions: step units (max(1, ceil(len / 32)) per item) and entries
+        // of the bins before each bin, [P + 1] each
+        std::vector<uint32_t> plan_base;
+        int64_t plan_units = 0;
     };
 
     // Host vectors whose device copies are queued on st during the build: they live
@@ -358,6 +405,7 @@ struct Impl : CtxBase {
         std::vector<PlanHost> plans;
         std::vector<std::vector<int64_t>> offs;
         std::vector<std::vector<int32_t>> ids, ranks;
+        PinnedStage stage;  // declared last: destroyed first, once its copies have run
     };
 
     // ------------------------------------------------------------ construction
@@ -393,13 +441,33 @@ struct Impl : CtxBase {
         x.alloc(nnz, st);
         const bool packed = packed_layout_applies(dims.data(), N, nnz, flags);
         BuildHost bh;
+        {
+            // staged host-to-device bytes of the build at most: per mode its row offsets and
+            // degree tables, and its schedule (items at most rows + bins, bin offsets, row
+            // lists, slot groups, plan regions)
+            size_t b = 0;
+            for (int n = 0; n < N; ++n) {
+                const size_t I = (size_t)dims[n], it = I + (size_t)P + 1;
+                b += 16 * I + 8 + sizeof(tf_item) * it + 8 * ((size_t)P + 1) + sizeof(SplitRow) * I +
+                     8 * it + 8 * ((size_t)P + 1) + 12 * 16;
+            }
+            bh.stage.reserve(b);
+            // and the landing block of the packed build's row counts, cached now for the
+            // same reason
+            if (packed) {
+                int64_t sum_I = 0;
+                for (int n = 0; n < N; ++n) sum_I += dims[n];
+                const size_t cb = (size_t)sum_I * sizeof(uint32_t);
+                pinned_cache().put(pinned_cache().get(cb), cb);
+            }
+        }
         if (packed) {
             build_packed(coords, values, on_dev, bh);
         } else {
             if (nnz > 0) TFS_CUDA(cudaMemcpyAsync(x.p, values, nnz * sizeof(T), kind, st));
             build_general(coords, on_dev, bh);
         }
-        for (int n = 0; n < N; ++n) plan_upload(n, bh.plans[n]);
+        for (int n = 0; n < N; ++n) plan_upload(n, bh.plans[n], bh.stage);
 
         // Algorithm 1 initialisation: A^(1) = 0, the other modes random, so R = X.
         const double std = pow((double)K, -1.0 / (2.0 * N));
@@ -422,6 +490,25 @@ struct Impl : CtxBase {
             rebuild_residuals();
         }
         TFS_CUDA(cudaStreamSynchronize(st));  // host copies of the schedules and tables read
+        if (packed) {
+            const DeviceStatus s = read_status();
+            if (s.bits & kStatRange)
+                throw ApiError{TF_ERANGE, "a coordinate is negative or not below its mode length"};
+            if (s.bits & kStatDup)
+                throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
+        }
+    }
+
+    // The other-mode index arrays are written entry by entry (positions below nnz); only
+    // their padding after nnz is zeroed here (all of it where no other mode exists).
+    void zero_oidx_padding(ModeLayout &L) {
+        if (N < 2) {
+            TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0, (size_t)L.ostride * sizeof(int32_t), st));
+            return;
+        }
+        for (int t = 0; t < N - 1; ++t)
+            TFS_CUDA(cudaMemsetAsync(L.oidx.p + (size_t)t * L.ostride + nnz, 0,
+                                     (size_t)(L.ostride - nnz) * sizeof(int32_t), st));
     }
 
     // Per-mode sorted layout by key sorts of gathered coordinates: mode 0's order by N
@@ -512,8 +599,7 @@ struct Impl : CtxBase {
                 // (bulk copies read fixed windows past a step's last entry)
                 L.ostride = (nnz + 64 + 63) / 64 * 64;
                 L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride, st);
-                TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0,
-                                         (size_t)std::max(N - 1, 1) * L.ostride * sizeof(int32_t), st));
+                zero_oidx_padding(L);
                 int t = 0;
                 for (int l = 0; l < N; ++l) {
                     if (l == n) continue;
@@ -581,7 +667,7 @@ struct Impl : CtxBase {
             cudaEvent_t allocated = side.make();
             TFS_CUDA(cudaEventRecord(allocated, st));  // x and rowmajor exist from here on
             TFS_CUDA(cudaStreamWaitEvent(side.s, allocated, 0));
-            constexpr int64_t kChunks = 8;
+            constexpr int64_t kChunks = 16;
             const int64_t tile = pack_count_tile();
             const int64_t chunk = std::max<int64_t>(tile, ceil_div(ceil_div(nnz, kChunks), tile) * tile);
             for (int64_t e0 = 0; e0 < nnz; e0 += chunk) {
@@ -660,17 +746,15 @@ struct Impl : CtxBase {
             }
             degree_order(n, count, bh.ids[n], bh.ranks[n]);
         });
+        // page-locked staging: the copies queue behind mode 0's sort without holding the host
         for (int n = 0; n < N; ++n) {
             ModeLayout &L = mode[n];
             L.off.alloc(L.I + 1, st);
             L.id_of.alloc(L.I, st);
             L.rank_of.alloc(L.I, st);
-            TFS_CUDA(cudaMemcpyAsync(L.off.p, bh.offs[n].data(), (L.I + 1) * sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, st));
-            TFS_CUDA(cudaMemcpyAsync(L.id_of.p, bh.ids[n].data(), L.I * sizeof(int32_t),
-                                     cudaMemcpyHostToDevice, st));
-            TFS_CUDA(cudaMemcpyAsync(L.rank_of.p, bh.ranks[n].data(), L.I * sizeof(int32_t),
-                                     cudaMemcpyHostToDevice, st));
+            bh.stage.copy(L.off.p, bh.offs[n].data(), (L.I + 1) * sizeof(int64_t), st);
+            bh.stage.copy(L.id_of.p, bh.ids[n].data(), L.I * sizeof(int32_t), st);
+            bh.stage.copy(L.rank_of.p, bh.ranks[n].data(), L.I * sizeof(int32_t), st);
         }
         // the schedules on host threads while the device continues
         bh.plans.assign((size_t)N, {});
@@ -696,8 +780,7 @@ struct Impl : CtxBase {
             ModeLayout &L = mode[n];
             L.ostride = (nnz + 64 + 63) / 64 * 64;
             L.oidx.alloc((size_t)std::max(N - 1, 1) * L.ostride, st);
-            TFS_CUDA(cudaMemsetAsync(L.oidx.p, 0,
-                                     (size_t)std::max(N - 1, 1) * L.ostride * sizeof(int32_t), st));
+            zero_oidx_padding(L);
             int t = 0;
             for (int l = 0; l < N; ++l)
                 if (l != n) L.omode[t++] = l;
@@ -737,11 +820,7 @@ struct Impl : CtxBase {
         for (auto &t : planners) t.join();
         for (auto &e : plan_err)
             if (e) std::rethrow_exception(e);
-        const DeviceStatus s = read_status();
-        if (s.bits & kStatRange)
-            throw ApiError{TF_ERANGE, "a coordinate is negative or not below its mode length"};
-        if (s.bits & kStatDup)
-            throw ApiError{TF_EDUP, "two observed entries share a coordinate"};
+        // the range and duplicate flags are read once create has synchronised
     }
 
     // Rows of mode n in decreasing order of entry count, equal counts by row id: ids[r]
@@ -805,11 +884,30 @@ struct Impl : CtxBase {
                     h.groups.push_back(sr.first_slot + g);
                     h.groups.push_back(std::min(kSlotGroup, sr.n_slots - g));
                 }
+        {
+            const int Pn = (int)h.bin_ptr.size() - 1;
+            h.plan_base.assign((size_t)2 * (Pn + 1), 0u);
+            uint64_t su = 0, se = 0;
+            for (int b = 0; b < Pn; ++b) {
+                h.plan_base[b] = (uint32_t)su;
+                h.plan_base[Pn + 1 + b] = (uint32_t)se;
+                for (int64_t it = h.bin_ptr[b]; it < h.bin_ptr[b + 1]; ++it) {
+                    const int64_t len = h.items[it].len;
+                    su += (uint64_t)std::max<int64_t>(1, (len + 31) / 32);
+                    se += (uint64_t)len;
+                }
+            }
+            h.plan_base[Pn] = (uint32_t)su;
+            h.plan_base[2 * Pn + 1] = (uint32_t)se;
+            if (su > 0xFFFFFFFFull || se > 0x7FFFFFFFull)
+                throw ApiError{TF_EINVAL, "too many entries for the gather plan's 32-bit offsets"};
+            h.plan_units = (int64_t)su;
+        }
         return h;
     }
 
-    // Device copies of a schedule (queued on st; h must live until st reaches them).
-    void plan_upload(int n, const PlanHost &h) {
+    // Device copies of a schedule, queued on st through page-locked staging.
+    void plan_upload(int n, const PlanHost &h, PinnedStage &stage) {
         ModeLayout &L = mode[n];
         ++layout_gen;
         L.P = P;
@@ -823,45 +921,14 @@ struct Impl : CtxBase {
         L.single.alloc(h.single.size(), st);
         L.n_groups = (int)(h.groups.size() / 2);
         L.groups.alloc(std::max<size_t>(h.groups.size(), 2), st);
-        if (!h.groups.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.groups.p, h.groups.data(), h.groups.size() * sizeof(int32_t),
-                                     cudaMemcpyHostToDevice, st));
-        if (!h.single.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.single.p, h.single.data(), h.single.size() * sizeof(SplitRow),
-                                     cudaMemcpyHostToDevice, st));
-        if (!h.items.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.items.p, h.items.data(), h.items.size() * sizeof(tf_item),
-                                     cudaMemcpyHostToDevice, st));
-        TFS_CUDA(cudaMemcpyAsync(L.bin_ptr.p, h.bin_ptr.data(), h.bin_ptr.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, st));
-        {
-            // gather-plan regions: step units (max(1, ceil(len / 32)) per item) and entries
-            // of the bins before each bin
-            const int Pn = (int)h.bin_ptr.size() - 1;
-            std::vector<uint32_t> base((size_t)2 * (Pn + 1), 0u);
-            uint64_t su = 0, se = 0;
-            for (int b = 0; b < Pn; ++b) {
-                base[b] = (uint32_t)su;
-                base[Pn + 1 + b] = (uint32_t)se;
-                for (int64_t it = h.bin_ptr[b]; it < h.bin_ptr[b + 1]; ++it) {
-                    const int64_t len = h.items[it].len;
-                    su += (uint64_t)std::max<int64_t>(1, (len + 31) / 32);
-                    se += (uint64_t)len;
-                }
-            }
-            base[Pn] = (uint32_t)su;
-            base[2 * Pn + 1] = (uint32_t)se;
-            if (su > 0xFFFFFFFFull || se > 0x7FFFFFFFull)
-                throw ApiError{TF_EINVAL, "too many entries for the gather plan's 32-bit offsets"};
-            L.plan_units = (int64_t)su;
-            L.plan_base.alloc(base.size(), st);
-            // pageable source: the call returns once the bytes are staged
-            TFS_CUDA(cudaMemcpyAsync(L.plan_base.p, base.data(), base.size() * sizeof(uint32_t),
-                                     cudaMemcpyHostToDevice, st));
-        }
-        if (!h.split.empty())
-            TFS_CUDA(cudaMemcpyAsync(L.split.p, h.split.data(), h.split.size() * sizeof(SplitRow),
-                                     cudaMemcpyHostToDevice, st));
+        L.plan_base.alloc(h.plan_base.size(), st);
+        L.plan_units = h.plan_units;
+        stage.copy(L.groups.p, h.groups.data(), h.groups.size() * sizeof(int32_t), st);
+        stage.copy(L.single.p, h.single.data(), h.single.size() * sizeof(SplitRow), st);
+        stage.copy(L.items.p, h.items.data(), h.items.size() * sizeof(tf_item), st);
+        stage.copy(L.bin_ptr.p, h.bin_ptr.data(), h.bin_ptr.size() * sizeof(int64_t), st);
+        stage.copy(L.split.p, h.split.data(), h.split.size() * sizeof(SplitRow), st);
+        stage.copy(L.plan_base.p, h.plan_base.data(), h.plan_base.size() * sizeof(uint32_t), st);
     }
 
     // Schedules of every mode from their row offsets on the host: one thread per mode.
@@ -897,8 +964,9 @@ struct Impl : CtxBase {
     void plan_all() {
         const auto offs = download_offsets();
         const auto hs = plan_all_host(offs);
-        for (int n = 0; n < N; ++n) plan_upload(n, hs[n]);
-        TFS_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+        PinnedStage stage;
+        for (int n = 0; n < N; ++n) plan_upload(n, hs[n], stage);
+        TFS_CUDA(cudaStreamSynchronize(st));
     }
 
     DeviceStatus read_status() {
