@@ -477,7 +477,9 @@ def batched_config(args, tensors, hbm):
     """The batch of many small tensors (mode lengths 50..5,000 and 1e3..1e6 entries,
     log-uniform, capped at half the cells; rank-16 truth; K = 16, C = 4) as one
     block-diagonal tensor, each sweep one CUDA-graph launch; ms per sweep against the
-    sweep's algorithmic HBM bytes."""
+    sweep's algorithmic HBM bytes, on the default schedule; beside it the autotuner's
+    timings of subset sizes and bin counts (tf_autotune: one timed sweep per candidate,
+    the state restored after each) and its choice."""
     import torch
     import paper_1410_5209_gb300 as tf
     import synth
@@ -494,6 +496,12 @@ def batched_config(args, tensors, hbm):
     create_s = time.perf_counter() - t0
     del p
     f.set_graphs(True)
+    Cs, Ps = [2, 4, 8], [0, 152 * 32]
+    bc, bp, tms = f.autotune(Cs, Ps, lam=lam)
+    tune = {"C": Cs, "bins": [b or "default" for b in Ps], "ms_per_sweep": tms.round(2).tolist(),
+            "best_C": bc, "best_bins": bp or "default", "best_ms_per_sweep": float(tms.min()),
+            "best_nnz_rank_per_s": None}
+    f.set_schedule(tf.SCHED_LPT, 0)  # the timed sweeps below keep the default schedule
     for _ in range(3):
         f.sweep(C, lam, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -511,6 +519,7 @@ def batched_config(args, tensors, hbm):
     N = 3
     sweep_bytes = nnz * (N * (4 * (N - 1) + 4) + 4) * math.ceil(K / C)
     achieved = sweep_bytes / (ms / 1e3) / 1e9
+    tune["best_nnz_rank_per_s"] = nnz * K / (tune["best_ms_per_sweep"] / 1e3)
     return {"tensors": tensors, "nnz": nnz, "K": K, "C": C, "ms_per_sweep": ms,
             "nnz_rank_per_s": nnz * K / (ms / 1e3), "train_rmse": rmse,
             "kernels_per_sweep": cnt["last_sweep_launches"],
@@ -518,7 +527,7 @@ def batched_config(args, tensors, hbm):
             "roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": sweep_bytes,
                          "floor_ms": sweep_bytes / (hbm * 1e9) * 1e3, "achieved": achieved,
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
-            "generate_s": gen_s, "create_s": create_s}
+            "autotune": tune, "generate_s": gen_s, "create_s": create_s}
 
 
 def fiveway_config(args, nnz, hbm):
