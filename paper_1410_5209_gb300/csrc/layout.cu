@@ -118,25 +118,36 @@ constexpr int kSortWarps = kSortThreads / kWarp;
 constexpr int kMaxDigitBits = 10;
 
 // Per-tile digit counts, hist[d * ntiles + tile] (digit-major, so one exclusive scan
-// gives every (digit, tile) its first output position).
+// gives every (digit, tile) its first output position).  A block counts kHistTiles
+// consecutive tiles, so each digit's counts of those tiles go out as one run of
+// consecutive words (whole 32-byte sectors instead of one partial sector per count).
+constexpr int kHistTiles = 8;
+
 template <int DB>
 __global__ void __launch_bounds__(kSortThreads) k_hist64(const uint64_t *__restrict__ kin,
                                                          int64_t n, int shift, int width,
                                                          uint32_t *__restrict__ hist,
                                                          int64_t ntiles) {
-    __shared__ uint32_t cnt[1 << DB];
+    __shared__ uint32_t cnt[kHistTiles << DB];  // [tile][digit]
     const int nb = 1 << width;
-    for (int d = threadIdx.x; d < nb; d += kSortThreads) cnt[d] = 0;
+    for (int i = threadIdx.x; i < (kHistTiles << DB); i += kSortThreads) cnt[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int64_t t0 = (int64_t)blockIdx.x * kHistTiles;
+    const int nt = (int)(ntiles - t0 < kHistTiles ? ntiles - t0 : kHistTiles);
+    for (int t = 0; t < nt; ++t) {
+        const int64_t base = (t0 + t) * kTile;
+        uint32_t *c = cnt + (t << DB);
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&cnt[(kin[idx] >> shift) & (uint64_t)(nb - 1)], 1u);
+        for (int r = 0; r < kSortItems; ++r) {
+            const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+            if (idx < n) atomicAdd(&c[(kin[idx] >> shift) & (uint64_t)(nb - 1)], 1u);
+        }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += kSortThreads)
-        hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
+    for (int i = threadIdx.x; i < nb * kHistTiles; i += kSortThreads) {
+        const int d = i / kHistTiles, t = i - d * kHistTiles;
+        if (t < nt) hist[(int64_t)d * ntiles + t0 + t] = cnt[(t << DB) + d];
+    }
 }
 
 // Second payload carried with the keys: none, 4-byte or 8-byte words.
@@ -337,7 +348,8 @@ void sort_pass(const uint64_t *kin, const int32_t *vin, const void *xin, uint64_
     using XT = typename XWord<XB>::type;
     const int64_t ntiles = ceil_div<int64_t>(n, kTile);
     const int64_t hn = ntiles << width;
-    k_hist64<DB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(kin, n, shift, width, ws.hist, ntiles);
+    k_hist64<DB><<<(unsigned)ceil_div<int64_t>(ntiles, kHistTiles), kSortThreads, 0, st>>>(
+        kin, n, shift, width, ws.hist, ntiles);
     TFS_CUDA(cudaGetLastError());
     scan_exclusive_u32(ws.hist, ws.hist, hn, ws.scan_tmp, st);
     const int smem = ScatterLayout<DB, XB>::kBytes;
