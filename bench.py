@@ -785,7 +785,7 @@ def main():
     ap.add_argument("--batched-tensors", type=int, default=4096)
     ap.add_argument("--serve-large-requests", type=int, default=1500)
     ap.add_argument("--serve-large-rate", type=float, default=5000.0)
-    ap.add_argument("--serve-large-sm-limits", default="-1,0,144,112,96,80",
+    ap.add_argument("--serve-large-sm-limits", default="-1,0,144,112,96,80,64",
                     help="SM limits of the concurrently sweeping context (-1: no sweep)")
     ap.add_argument("--fiveway-nnz", type=int, default=500_000_000)
     ap.add_argument("--e2e-steps", type=int, default=5)
