@@ -1593,9 +1593,69 @@ struct Impl : CtxBase {
         a.res = res[0].p;
         a.block_out = scratch + 2;
         double *regp = scratch + 2 + blocks;
+        // float three-way contexts whose last sweep ran mode 0's lean pass in its default
+        // form: the loss from that pass's plan and caches (the plain pass with the sums of
+        // r^2 in place of the Gram); otherwise the pipelined residual kernel
+        LeanPlan lplan{};
+        GatherPlanDev lgp{};
+        bool lean_loss = false;
+        if constexpr (sizeof(T) == 4) {
+            if (N == 3 && Cq > 0 && precision == 0 && (path == 0 || path == 3) &&
+                lean_pass_supported(CM_last, N)) {
+                const std::vector<int64_t> *dc[2] = {&mode[L.omode[0]].deg_cum,
+                                                     &mode[L.omode[1]].deg_cum};
+                const int64_t dims_o[2] = {dims[L.omode[0]], dims[L.omode[1]]};
+                // the sweep's plan (packed Gram, same cache, pool and warps): the same gather plan
+                lplan = lean_pass_plan(CM_last, false, 0, dims_o, dc, nnz, pass_sms(), L.P,
+                                       lean_cache_rows, lean_ring_cap, lean_warps, 0, 0);
+                // the per-item sums go to the partials buffer (a sweep has sized it for
+                // every slot, at two floats or more per slot)
+                lean_loss = (path != 0 || lplan.coverage >= 0.25) && partials.p != nullptr &&
+                            partials.n >= (size_t)2 * (size_t)std::max<int64_t>(L.n_slots, 1);
+                if (lean_loss) {
+                    const int run = lean_run_mode(0);
+                    lgp = gather_plan(0, lplan.p.R[run], lplan.p.R[1 - run], lplan.p.cap[0]);
+                    lplan.gk = 2;
+                }
+            }
+        }
+        double *item_sums = lean_loss ? reinterpret_cast<double *>(partials.p) : nullptr;
         timed(TF_KIND_LOSS, [&] {
-            launch_res<T>(a, CM_last, st);
-            launch_sum_blocks(scratch + 2, blocks, scratch + 0, st);
+            if constexpr (sizeof(T) == 4) {
+                if (lean_loss) {
+                    PassArgs<float> pa{};
+                    pa.items = L.items.p;
+                    pa.bin_ptr = L.bin_ptr.p;
+                    pa.P = L.P;
+                    pa.N = N;
+                    pa.n = 0;
+                    pa.C = CM_last;
+                    pa.Cq = Cq;
+                    pa.first = 0;
+                    for (int u = 0; u < N - 1; ++u) {
+                        pa.oidx[u] = L.oidx.p + (size_t)u * L.ostride;
+                        pa.Zo[u] = reinterpret_cast<const float *>(Z[L.omode[u]].p);
+                        pa.Zob[u] = Zb[L.omode[u]].p;
+                    }
+                    pa.Zn = reinterpret_cast<float *>(Z[0].p);
+                    pa.rank_n = L.rank_of.p;
+                    pa.res = reinterpret_cast<float *>(res[0].p);
+                    pa.K = K;
+                    pa.stat = stat.p;
+                    pa.ticket = ticket.p;
+                    pa.ticket_base = ticket_base;
+                    pa.loss_out = item_sums;
+                    launch_lean_pass(pa, CM_last, lplan, lgp, st);
+                    ticket_base += (unsigned long long)L.P +
+                                   (unsigned long long)lplan.grid * lplan.warps;
+                    // the items' sums in slot order
+                    launch_sum_blocks(item_sums, (int)L.n_slots, scratch + 0, st);
+                }
+            }
+            if (!lean_loss) {
+                launch_res<T>(a, CM_last, st);
+                launch_sum_blocks(scratch + 2, blocks, scratch + 0, st);
+            }
             for (int n = 0; n < N; ++n)
                 launch_reg<T>(A[n].p, dims[n], K,
                               (flags & TF_WEIGHTED_LAMBDA) ? mode[n].off.p : nullptr,

@@ -39,7 +39,7 @@ namespace {
 // set the register budget (12 warps at CM = 10 and 12); the tensor-core Gram holds 8 sums
 // per lane.
 __host__ __device__ constexpr int lean_max_warps(int CM, int GK) {
-    return GK != 0 ? 16 : (CM <= 4 ? 20 : (CM <= 8 ? 16 : 12));
+    return (GK == 1 || GK == 3) ? 16 : (CM <= 4 ? 20 : (CM <= 8 ? 16 : 12));
 }
 
 typedef unsigned long long u64;
@@ -149,7 +149,10 @@ struct LG {
 constexpr int kLeanSlots = 3;        // pool slots: cold rows are staged two steps ahead
 
 // ---------------------------------------------------------------------------- the pass
-// GK: how the Gram matrix and right-hand side are accumulated.  0: per lane, packed
+// GK: how the Gram matrix and right-hand side are accumulated.  2: not at all: the loss
+// pass (plain geometry, mode 0): per entry r = r_hat - <own row, h> over the slices'
+// current columns, r^2 summed in FP64 per item into a.loss_out[the item's slot].  0: per
+// lane, packed
 // two-wide FP32 FMAs (a lane sums its own entries; the warp's sums are combined at the
 // end of an item).  1 / 3: on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
 // accumulation): the warp writes the step's H' = [h | r_hat] (columns 0 .. CM-1 and 15)
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
     for (int q = 0; q < 4; ++q) dg[0][q] = dg[1][q] = 0.f;
     const unsigned stage_hi = ring_s + 4u * (unsigned)lp.list_off;
     const unsigned stage_lo = stage_hi + 4u * 16u * kLeanStageStride;
-    if (GK != 0) {  // staged H' rows CM .. 14 stay zero
+    if (GK == 1 || GK == 3) {  // staged H' rows CM .. 14 stay zero
         for (int q = lane; q < 16 * kLeanStageStride * (GK == 3 ? 2 : 1); q += 32)
             sts32(stage_hi + 4u * (unsigned)q, 0u);
         __syncwarp();
@@ -236,6 +239,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
     u64 wc[H], wp[H], wo[H];
 #pragma unroll
     for (int k = 0; k < H; ++k) wc[k] = wp[k] = wo[k] = 0ull;
+    double lacc = 0.0;  // loss pass: this lane's sum of r^2
 
     unsigned long long tk_next = 0;
     if (lane == 0) tk_next = atomicAdd(a.ticket, 1ull) - a.ticket_base;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
             rrank = 0;
             if (base + lane < s_end) {
                 rec = steps[base + lane];
-                if (FIRST) rrank = srank[base + lane];
+                if (FIRST || GK == 2) rrank = srank[base + lane];
             }
         };
         window(s_begin);
@@ -328,6 +332,12 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                 if (lane < 2 * CM)
                     cp4(ring_s + 4u * (unsigned)(lp.own_off + (int)((inf >> 8) & 3u) * 2 * CM + lane),
                         a.Zn + (int64_t)rk * W + CM + lane);
+            }
+            if (GK == 2 && (inf & 64u)) {  // the own row's current columns
+                const int rk = __shfl_sync(0xFFFFFFFFu, rrank, s - wb);
+                if (lane < CM)
+                    cp4(ring_s + 4u * (unsigned)(lp.own_off + (int)((inf >> 8) & 3u) * 2 * CM + lane),
+                        a.Zn + (int64_t)rk * W + lane);
             }
         };
 
@@ -446,6 +456,19 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                     v = v - (hsum(pp0) + hsum(pp1)) + (hsum(po0) + hsum(po1));
                     a.res[j0 + lane] = v;
                 }
+                if constexpr (GK == 2) {
+                    // R of this entry: the copy's r_hat less the products of the columns
+                    // in the slices (beyond C they are zero)
+                    const unsigned o = ring_s + 4u * (unsigned)(lp.own_off + (int)((inf >> 8) & 3u) * 2 * CM);
+                    u64 pa = 0ull, pb = 0ull;
+#pragma unroll
+                    for (int q = 0; q < H; q += 2) {
+                        pa = fma2(lds1(o + 8 * q), h[q], pa);
+                        if (q + 1 < H) pb = fma2(lds1(o + 8 * (q + 1)), h[q + 1], pb);
+                    }
+                    const float r = v - (hsum(pa) + hsum(pb));
+                    lacc += (double)r * (double)r;
+                }
                 if constexpr (GK == 0) {
                     const u64 vv = pk(v, v);
 #pragma unroll
@@ -463,7 +486,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                         acc[2 * G::NBLK + I] = fma2(h[I], vv, acc[2 * G::NBLK + I]);
                 }
             }
-            if constexpr (GK != 0) {
+            if constexpr (GK == 1 || GK == 3) {
                 // H' of the step (idle lanes: zeros), transposed: row f holds feature f of
                 // the 32 entries; then per 8 entries one A-fragment load and two MMAs
                 // (three products each for GK 3)
@@ -502,7 +525,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                 }
                 __syncwarp();  // the staging buffer is rewritten by the next step
             }
-            if (GK != 0 && (inf & 128u)) {
+            if ((GK == 1 || GK == 3) && (inf & 128u)) {
                 // end of item: each sum is held by one lane (the C-fragment layout)
                 const int pslot = __shfl_sync(0xFFFFFFFFu, rec.slot, s - wb);
                 float *p = a.partials + (int64_t)pslot * (G::NT + CM);
@@ -520,6 +543,15 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                         }
                         dg[nb][q] = 0.f;
                     }
+            }
+            if (GK == 2 && (inf & 128u)) {
+                // end of item: its sum of r^2 (butterfly: every lane holds the same value)
+                // to the item's slot, so the total does not depend on which warp took it
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xFFFFFFFFu, lacc, o);
+                const int pslot = __shfl_sync(0xFFFFFFFFu, rec.slot, s - wb);
+                if (lane == 0) a.loss_out[pslot] = lacc;
+                lacc = 0.0;
             }
             if (GK == 0 && (inf & 128u)) {
                 // ------------------------------------------------------ end of item
@@ -612,7 +644,7 @@ LeanPlan lean_pass_plan(int CM, bool first, int n, const int64_t *dims_o,
     lp.cap[0] = lp.cap[1] = pool_rows;
     pl.gk = gk;
     pl.vb = vb;
-    const int stage = gk == 0 ? 0 : 16 * kLeanStageStride * (gk == 3 ? 2 : 1);
+    const int stage = (gk == 1 || gk == 3) ? 16 * kLeanStageStride * (gk == 3 ? 2 : 1) : 0;
     lp.slot_floats = pool_rows * csp;
     lp.own_off = kLeanSlots * lp.slot_floats;
     lp.list_off = (lp.own_off + 4 * 2 * CM + 3) / 4 * 4;  // the tensor-core staging follows
@@ -686,6 +718,11 @@ static void launch_lean_t(const PassArgs<float> &a, const LeanPlan &pl, const Ga
 template <int CM, int GK, int VB>
 static void launch_lean_cm(const PassArgs<float> &a, const LeanPlan &pl, const GatherPlanDev &gp,
                            cudaStream_t st) {
+    if constexpr (GK == 2) {  // the loss pass: mode 0, plain geometry
+        if (a.first || a.n != 0) throw ApiError{TF_EINVAL, "the lean loss pass runs mode 0's plain pass"};
+        launch_lean_t<CM, false, 0, 0, 2, 0>(a, pl, gp, st);
+        return;
+    }
     if (!a.first) {
         if (a.n == 1)
             launch_lean_t<CM, false, 0, 1, GK, VB>(a, pl, gp, st);
@@ -713,6 +750,7 @@ static void launch_lean_gk(const PassArgs<float> &a, const LeanPlan &pl, const G
     }
     switch (pl.gk) {
         case 1: launch_lean_cm<CM, 1, 0>(a, pl, gp, st); return;
+        case 2: launch_lean_cm<CM, 2, 0>(a, pl, gp, st); return;
         case 3: launch_lean_cm<CM, 3, 0>(a, pl, gp, st); return;
         default: launch_lean_cm<CM, 0, 0>(a, pl, gp, st); return;
     }

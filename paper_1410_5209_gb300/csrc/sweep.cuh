@@ -57,6 +57,7 @@ struct PassArgs {
     // d_j / (B_jj + lambda) of the Cholesky is below 1 / cond_limit (0: never)
     int refine;
     float cond_limit;
+    double *loss_out;  // lean loss pass: per-item (slot) sums of r^2 (other passes: unused)
 };
 
 template <class T>
