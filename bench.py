@@ -38,12 +38,12 @@ WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=
 # reports traffic as null once the sources differ or the entry count is not 1e8.
 NCU_TRAFFIC = 1.749e9
 NCU_TRAFFIC_NNZ = 100_000_000
-NCU_SOURCE_HASH = "59cfd85a604b0fc2"
+NCU_SOURCE_HASH = "34a252b2c00cd0cc"
 
 
 # Utilisation of the L1 data pipe (shared-memory and L1 wavefronts) of the mode pass in the
 # same capture, averaged over the three modes' launches; null once the sources differ.
-NCU_L1_PIPE_PCT = 70.6
+NCU_L1_PIPE_PCT = 70.7
 
 
 def pass_units(nnz, N, C, avg_launch_ms):
