@@ -565,6 +565,33 @@ def test_sm_limit_does_not_change_results(dt):
         f.set_sm_limit(-1)
 
 
+@pytest.mark.parametrize("C", [4, 10])
+def test_lean_loss_pass_matches_residual_kernel_and_oracle(C):
+    """tf_loss after a lean sweep of a float three-way context runs as the lean plain pass
+    (sums of r^2 per item, then in slot order): the same state read through the pipelined
+    residual kernel (kernel path 1) gives the same loss up to FP32 rounding of each r (the
+    two form the products in different orders: 1e-5 relative), and both match the FP64
+    oracle's loss of the same sweeps within the FP32 bar."""
+    p = synth.small(55 + C, (2500, 1800, 90), 220_000, 4, 20, modes=["zipf", "zipf", "uniform"])
+    f, t, A = make(p, tf.F32)
+    r = oracle.residual(t, A)
+    for s in range(2):
+        order = p.column_order(s, C)
+        f.sweep(C, 0.2, 1, order)
+        oracle.sals_sweep(t, A, r, C, 0.2, 1, order)
+    assert f.counters()["pass_path"] & 8
+    lean = f.loss(0.2)
+    f.set_kernel_path(tf.Factorization.PATH_SIMT)
+    pipe = f.loss(0.2)
+    f.set_kernel_path(0)
+    assert f.loss(0.2) == lean   # deterministic
+    assert abs(lean[0] - pipe[0]) <= 1e-5 * abs(pipe[0])
+    assert abs(lean[1] - pipe[1]) <= 1e-5 * abs(pipe[1])
+    Lo, rmseo = oracle.loss(t, r, A, 0.2)
+    assert abs(lean[1] - rmseo) <= 1e-3 * rmseo
+    assert abs(lean[0] - Lo) <= 2e-3 * abs(Lo)
+
+
 def test_deterministic_rerun_fp32():
     p = synth.small(34, (300, 300, 30), 50_000, 3, 10, modes=["zipf", "uniform", "uniform"])
     res = []
