@@ -1050,6 +1050,14 @@ struct Impl : CtxBase {
     // time a split needs it, then kept (one per mode) until the row schedule or the cache
     // sizes change.  The refreshing and the plain inner iterations share it: their cache
     // sizes are both planned for the refreshing pass's wider rows.
+    // The plan of mode n for these cache sizes if one is kept (nothing is built).
+    const GatherPlan *find_gather_plan(int n, int RR, int RV, int cap) const {
+        for (auto &g : gplans)
+            if (g->n == n && g->RR == RR && g->RV == RV && g->cap == cap && g->layout_gen == layout_gen)
+                return g.get();
+        return nullptr;
+    }
+
     GatherPlanDev gather_plan(int n, int RR, int RV, int cap) {
         const int first = 1;
         const ModeLayout &L = mode[n];
@@ -1609,9 +1617,13 @@ struct Impl : CtxBase {
                 lplan = lean_pass_plan(CM_last, false, 0, dims_o, dc, nnz, pass_sms(), L.P,
                                        lean_cache_rows, lean_ring_cap, lean_warps, 0, 0);
                 // the per-item sums go to the partials buffer (a sweep has sized it for
-                // every slot, at two floats or more per slot)
+                // every slot, at two floats or more per slot); the sweep's gather plan must
+                // be kept (the loss builds and allocates nothing)
+                const int run0 = lean_run_mode(0);
                 lean_loss = (path != 0 || lplan.coverage >= 0.25) && partials.p != nullptr &&
-                            partials.n >= (size_t)2 * (size_t)std::max<int64_t>(L.n_slots, 1);
+                            partials.n >= (size_t)2 * (size_t)std::max<int64_t>(L.n_slots, 1) &&
+                            find_gather_plan(0, lplan.p.R[run0], lplan.p.R[1 - run0],
+                                             lplan.p.cap[0]) != nullptr;
                 if (lean_loss) {
                     const int run = lean_run_mode(0);
                     lgp = gather_plan(0, lplan.p.R[run], lplan.p.R[1 - run], lplan.p.cap[0]);

@@ -91,11 +91,13 @@ __global__ void __launch_bounds__(256) k_gather_plan(const GPlanArgs g) {
                 const uint32_t from = lo >= 32 ? 0u : ~((1u << lo) - 1u);
                 const uint32_t hV = __ballot_sync(0xFFFFFFFFu, coldV && (!pcV || pV != iV)) & from;
                 const uint32_t hR = __ballot_sync(0xFFFFFFFFu, coldR && (!pcR || pR != iR)) & from;
-                const int upto = __popc(hV & le) + __popc(hR & le);
-                const int hi = cmax > 0
-                                   ? lo + __popc(__ballot_sync(0xFFFFFFFFu,
-                                                               valid && lane >= lo && upto <= g.cap))
-                                   : 0;
+                // usually every remaining cold row fits: one record to the step's end (the
+                // same lanes the general count below would take)
+                int hi = cmax;
+                if (__popc(hV) + __popc(hR) > g.cap) {
+                    const int upto = __popc(hV & le) + __popc(hR & le);
+                    hi = lo + __popc(__ballot_sync(0xFFFFFFFFu, valid && lane >= lo && upto <= g.cap));
+                }
                 const uint32_t keep = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & from;
                 const int nVr = __popc(hV & keep), nRr = __popc(hR & keep);
                 over = over || ns >= s_cap || nl + (uint32_t)(nVr + nRr) > l_cap;
