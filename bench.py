@@ -36,14 +36,14 @@ WORKLOAD = dict(workload="skewed_3way_1e8", dims=[100_000, 100_000, 1_000], nnz=
 # profiles/k_lean_pass_skewed_3way_1e8.md (2e7-entry case, scaled by entries to a
 # 1e8-entry launch), and the hash of the kernel sources it was taken with; the bench
 # reports traffic as null once the sources differ or the entry count is not 1e8.
-NCU_TRAFFIC = 1.749e9
+NCU_TRAFFIC = 1.737e9
 NCU_TRAFFIC_NNZ = 100_000_000
-NCU_SOURCE_HASH = "34a252b2c00cd0cc"
+NCU_SOURCE_HASH = "03862e7fb4cb30ec"
 
 
 # Utilisation of the L1 data pipe (shared-memory and L1 wavefronts) of the mode pass in the
 # same capture, averaged over the three modes' launches; null once the sources differ.
-NCU_L1_PIPE_PCT = 70.7
+NCU_L1_PIPE_PCT = 70.9
 
 
 def pass_units(nnz, N, C, avg_launch_ms):
