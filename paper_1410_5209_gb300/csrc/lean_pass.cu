@@ -18,7 +18,7 @@
 //     that the lane already holds the products of that row (the same run index as the
 //     lane's previous entry).
 //   * The pass (k_lean_pass) walks a bin's steps: it loads the entries' words and residuals
-//     and the steps' cold-row lists three steps ahead, stages the listed rows two steps
+//     and the steps' cold-row lists three steps ahead, stages the listed rows one step
 //     ahead with 16-byte cp.async (a fixed group of lanes per row), and computes: per lane,
 //     products of the run-mode row with the own row's previous / old columns that stay in
 //     registers while the run index holds, the Hadamard product h, the R-hat refresh, and
@@ -146,7 +146,7 @@ struct LG {
     static constexpr int NT = CM * (CM + 1) / 2;
 };
 
-constexpr int kLeanSlots = 3;        // pool slots: cold rows are staged two steps ahead
+constexpr int kLeanSlots = 2;        // pool slots: cold rows are staged one step ahead
 
 // ---------------------------------------------------------------------------- the pass
 // GK: how the Gram matrix and right-hand side are accumulated.  2: not at all: the loss
@@ -341,29 +341,30 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
             }
         };
 
-        // Pipeline (one cp.async group per step): words and residuals three steps ahead,
-        // list entries four ahead, rows two ahead.  At the top of step s the group of step
-        // s - 2 is complete: the rows of s, the words of s + 1 and the list of s + 2.
+        // Pipeline (two cp.async groups per step, the rows of the next step first, then the
+        // streams): words and residuals three steps ahead, list entries four ahead, rows
+        // one ahead.  At the top of step s every group but the newest is complete: the
+        // rows of s (committed at step s - 1), its words (s - 3) and the list of s + 1.
         load_words(s_begin);
         load_list(s_begin);
         load_list(s_begin + 1);
         load_list(s_begin + 2);
+        load_list(s_begin + 3);
         cp_commit();
         cp_wait<0>();
         __syncwarp();
         stage(s_begin, 0);
+        cp_commit();
         load_words(s_begin + 1);
         load_words(s_begin + 2);
-        cp_commit();
-        stage(s_begin + 1, 1);
-        load_list(s_begin + 3);
         cp_commit();
         int slot = 0;
         for (int s = s_begin; s < s_end; ++s) {
             if (s + 4 - wb >= 32) window(s);
             cp_wait<1>();
             __syncwarp();
-            stage(s + 2, slot + 2 >= kLeanSlots ? slot + 2 - kLeanSlots : slot + 2);
+            stage(s + 1, slot ^ 1);
+            cp_commit();
             load_words(s + 3);
             load_list(s + 4);
             cp_commit();
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(lean_max_warps(CM, GK) * kWarp, 1)
                 for (int k = 0; k < NACC; ++k) acc[k] = 0ull;
             }
             __syncwarp();
-            slot = slot + 1 >= kLeanSlots ? 0 : slot + 1;
+            slot ^= 1;
         }
         cp_wait<0>();
         __syncwarp();
