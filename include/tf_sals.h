@@ -325,9 +325,9 @@ tf_status tf_set_sm_limit(tf_ctx *ctx, int sms);
 /* Shared-memory layout of the lean pass (kernel path 0 or 3): at most max_rows rows of
  * each other mode's slice are held in shared memory per launch (< 0: as many as fit, the
  * rows with the most entries first; 0: none); the distinct rows outside that cache that a
- * step of 32 entries needs are staged two steps ahead in a per-warp pool of pool_rows
- * rows (2..32; a step's lanes are split over several rounds where its rows would not
- * fit); warps per block 1..16 (0: the most that fit the registers and shared memory, at
+ * step of 32 entries needs are staged one step ahead in one of two per-warp pool slots of
+ * pool_rows rows each (2..32; a step's lanes are split over several rounds where its rows
+ * would not fit); warps per block 1..16 (0: the most that fit the registers and shared memory, at
  * most 12 with the packed-FMA Gram, 16 with the tensor-core Gram).  The lean pass plans, once per row schedule and setting, where
  * each entry's rows will be; no setting changes any result (bit-identical).  TF_EINVAL
  * for values outside these ranges.  No counterpart in the paper. */
