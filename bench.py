@@ -247,8 +247,8 @@ def reference_arm(args, rank, world):
 def study(args, rank, world):
     """Section 5.5-style studies on the same workload, one JSON line per configuration:
     sweeps at each C (time per sweep, training RMSE and the RMSE on 1% held-out entries
-    after each, from the same initial factors; C = K is ALS), then the row-assignment
-    policies at the workload's C."""
+    after each, from the same initial factors; C = K is ALS), then the inner-iteration
+    counts T_in at the workload's C, then the row-assignment policies at that C."""
     import numpy as np
     import torch
     import paper_1410_5209_gb300 as tf
@@ -274,7 +274,7 @@ def study(args, rank, world):
         pred = f.predict(test_c).double()
         return float(torch.sqrt(torch.mean((test_x - pred) ** 2)))
 
-    def run(C, sweeps):
+    def run(C, sweeps, T_in=1):
         for n in range(3):
             f.set_factors(n, A0[n])
         times, rmses, tests = [], [], []
@@ -282,7 +282,7 @@ def study(args, rank, world):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             ev0.record(stream)
-            f.sweep(C, lam, 1, p.column_order(s, C))
+            f.sweep(C, lam, T_in, p.column_order(s, C))
             ev1.record(stream)
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
@@ -313,6 +313,15 @@ def study(args, rank, world):
         f.set_precision(0)
         f.set_solve(0, 0.0)
     C = WORKLOAD["C"]
+    # inner iterations (Algorithm 1's T_in): the same outer sweeps from the same start, each
+    # sweep T_in passes over the modes per column subset; convergence against elapsed time
+    for T_in in [int(t) for t in args.study_tin.split(",") if t]:
+        run(C, 1, T_in)
+        times, rmses, tests = run(C, args.study_sweeps, T_in)
+        print(json.dumps({"study": "T_in", "T_in": T_in, "C": C, "K": K,
+                          "ms_per_sweep": float(np.median(times)),
+                          "elapsed_ms": [float(t) for t in np.cumsum(times)],
+                          "train_rmse": rmses, "test_rmse": tests}), flush=True)
     policies = [q for q in args.study_policies.split(",") if q]
     for name, pol in (("lpt", tf.SCHED_LPT), ("greedy_alg3", tf.SCHED_GREEDY),
                       ("seq", tf.SCHED_SEQ), ("ran", tf.SCHED_RAN)):
@@ -811,6 +820,8 @@ def main():
     ap.add_argument("--study-c", default="1,2,4,10,20,50,100")
     ap.add_argument("--study-sweeps", type=int, default=3)
     ap.add_argument("--study-policies", default="lpt,greedy,seq,ran")
+    ap.add_argument("--study-tin", default="1,2,3,5",
+                    help="inner-iteration counts of the T_in study (empty: skip it)")
     ap.add_argument("--fiveway", type=int, default=0,
                     help="entries of the 5-way workload to time instead (5e8 at full size)")
     ap.add_argument("--fiveway-c", default="10,50,1")
