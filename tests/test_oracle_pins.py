@@ -220,13 +220,17 @@ def test_group_matches_library_lexsort():
     pin_group(oracle.load())
 
 
-def test_validate_rejects_range_and_duplicates():
+def pin_validate(lib):
     t = oracle.Tensor(np.array([[0, 0], [1, 2]], np.int32), [1.0, 2.0], [2, 3])
-    assert oracle.validate(t) == oracle.OK
+    assert oracle.validate(t, lib) == oracle.OK
     t = oracle.Tensor(np.array([[0, 0], [1, 3]], np.int32), [1.0, 2.0], [2, 3])
-    assert oracle.validate(t) == oracle.ERANGE
+    assert oracle.validate(t, lib) == oracle.ERANGE
     t = oracle.Tensor(np.array([[1, 2], [0, 0], [1, 2]], np.int32), [1.0, 2.0, 3.0], [2, 3])
-    assert oracle.validate(t) == oracle.EDUP
+    assert oracle.validate(t, lib) == oracle.EDUP
+
+
+def test_validate_rejects_range_and_duplicates():
+    pin_validate(oracle.load())
 
 
 def test_residual_matches_dense_reconstruction():
@@ -240,25 +244,35 @@ def test_init_invariant_R_equals_X():
     assert np.array_equal(oracle.residual(t, A), t.x)
 
 
-def test_loss_matches_definition():
+def pin_loss(lib):
+    """Eq. (1) and the training RMSE, from the numpy model (not the oracle's residual)."""
     p, t, A = tiny_problem(10)
     rng = np.random.default_rng(3)
     A = [rng.standard_normal(a.shape) for a in A]
-    r = oracle.residual(t, A)
-    L, rmse = oracle.loss(t, r, A, 0.25)
+    r = t.x - model_np(t.coords, A)
+    L, rmse = oracle.loss(t, r, A, 0.25, lib=lib)
     assert np.isclose(L, loss_np(t, A, 0.25), rtol=1e-13)
-    assert np.isclose(rmse, np.sqrt(np.mean((t.x - model_np(t.coords, A)) ** 2)), rtol=1e-13)
+    assert np.isclose(rmse, np.sqrt(np.mean(r ** 2)), rtol=1e-13)
 
 
-def test_weighted_loss_definition():
+def pin_weighted_loss(lib):
+    """The weighted regulariser (Section 5.1.3): row i of mode n counts |Omega_i^(n)| times."""
     p, t, A = tiny_problem(10)
     rng = np.random.default_rng(3)
     A = [rng.standard_normal(a.shape) for a in A]
-    r = oracle.residual(t, A)
-    L, _ = oracle.loss(t, r, A, 0.25, weighted=True)
+    r = t.x - model_np(t.coords, A)
+    L, _ = oracle.loss(t, r, A, 0.25, weighted=True, lib=lib)
     reg = sum((np.bincount(t.coords[:, n], minlength=int(t.dims[n])) * (A[n] ** 2).sum(1)).sum()
               for n in range(t.N))
     assert np.isclose(L, r @ r + 0.25 * reg, rtol=1e-13)
+
+
+def test_loss_matches_definition():
+    pin_loss(oracle.load())
+
+
+def test_weighted_loss_definition():
+    pin_weighted_loss(oracle.load())
 
 
 def test_row_update_is_ridge_least_squares():
@@ -348,17 +362,22 @@ def test_convergence_on_noiseless_low_rank():
     assert rmse < 1e-2 * rmse0
 
 
-def test_foldin_is_ridge_least_squares():
+def pin_foldin(lib):
+    """Eq. (2) for a new row against frozen factors: the ridge least-squares row."""
     p, t, A = tiny_problem(14, dims=(5, 30, 20), nnz=300, K=6)
     rng = np.random.default_rng(5)
     A = [rng.standard_normal(a.shape) for a in A]
     m = 40
     other = np.stack([rng.integers(0, 30, m), rng.integers(0, 20, m)], 1).astype(np.int32)
     x = rng.standard_normal(m)
-    row, st = oracle.foldin(A, 0, other, x, 0.3)
+    row, st = oracle.foldin(A, 0, other, x, 0.3, lib)
     Phi = A[1][other[:, 0]] * A[2][other[:, 1]]
     assert st == 0
     assert np.allclose(row, ridge_lstsq(Phi, x, 0.3), rtol=1e-10, atol=1e-12)
+
+
+def test_foldin_is_ridge_least_squares():
+    pin_foldin(oracle.load())
 
 
 def pin_alg3(lib):
@@ -398,10 +417,26 @@ MUTANTS = {
     "wrong column in h": ("* K + S[q]];\n            h[q] = p;", "* K + S[0]];\n            h[q] = p;"),
     "tie-break on rows reversed": ("rows_n[m] < rows_n[best]", "rows_n[m] > rows_n[best]"),
     "residual sign": ("r[e] = x[e] - s;", "r[e] = s - x[e];"),
+    "weighted lambda ignored in the row update": (
+        "if (flags & ORC_WEIGHTED) lam *= (double)(off[i + 1] - off[i]);",
+        "if (flags & ORC_WEIGHTED) lam *= 1.0;"),
+    "regulariser dropped from the loss": ("*loss = sr + lambda * reg;", "*loss = sr;"),
+    "row weights ignored in the weighted loss": (
+        "double w = (flags & ORC_WEIGHTED) ? (double)row_nnz[n][i] : 1.0;", "double w = 1.0;"),
+    "RMSE not divided by the entry count": ("sqrt(sr / (double)nnz)", "sqrt(sr)"),
+    "inner iterations run once": ("for (int t = 0; t < T_in; ++t)", "for (int t = 0; t < 1; ++t)"),
+    "lambda dropped from the fold-in": ("for (int k = 0; k < K; ++k) B[k * K + k] += lambda;",
+                                        "for (int k = 0; k < K; ++k) B[k * K + k] += 0.0 * lambda;"),
+    "fold-in rhs not weighted by the values": ("c[k1] += x[j] * h[k1];", "c[k1] += h[k1];"),
 }
 
-PINS = [pin_group, pin_residual, pin_row_update_lstsq, pin_als, pin_cdtf, pin_golden_cdtf,
-        pin_sals_general, pin_alg3]
+def pin_row_update_weighted(lib):
+    pin_row_update_lstsq(lib, weighted=True)
+
+
+PINS = [pin_group, pin_validate, pin_residual, pin_loss, pin_weighted_loss, pin_row_update_lstsq,
+        pin_row_update_weighted, pin_als, pin_cdtf, pin_golden_cdtf, pin_sals_general, pin_foldin,
+        pin_alg3]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
