@@ -428,6 +428,22 @@ MUTANTS = {
     "lambda dropped from the fold-in": ("for (int k = 0; k < K; ++k) B[k * K + k] += lambda;",
                                         "for (int k = 0; k < K; ++k) B[k * K + k] += 0.0 * lambda;"),
     "fold-in rhs not weighted by the values": ("c[k1] += x[j] * h[k1];", "c[k1] += h[k1];"),
+    "cyclic order of the remaining modes reversed": ("int m = (g_mode + t) % g_N;",
+                                                      "int m = (g_mode + g_N - t) % g_N;"),
+    "Cholesky column update dropped": (
+        "for (int k = 0; k < j; ++k) s -= M[i * m + k] * M[j * m + k];",
+        "for (int k = 0; k < 0; ++k) s -= M[i * m + k] * M[j * m + k];"),
+    "transposed factor in forward substitution": ("s -= M[i * m + k] * a[k];",
+                                                  "s -= M[k * m + i] * a[k];"),
+    "pivot not square-rooted": ("double ljj = sqrt(d);", "double ljj = d;"),
+    "range check off by one": ("coords[e * N + n] >= dims[n]) return ORC_ERANGE;",
+                               "coords[e * N + n] > dims[n]) return ORC_ERANGE;"),
+    "duplicates accepted": ("if (same) st = ORC_EDUP;", "if (same) st = ORC_OK;"),
+    "row cap of Algorithm 3 ignored": ("if (rows_n[m] >= cap) continue;",
+                                       "if (rows_n[m] > In) continue;"),
+    "Algorithm 3 rows in increasing length": (
+        "return g_rownnz[a] > g_rownnz[b] ? -1 : 1;", "return g_rownnz[a] > g_rownnz[b] ? 1 : -1;"),
+    "residuals not squared in the loss": ("sr += r[e] * r[e];", "sr += r[e];"),
 }
 
 def pin_row_update_weighted(lib):
