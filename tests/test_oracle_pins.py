@@ -333,18 +333,22 @@ def test_row_relabel_invariance():
     assert np.allclose(r1, r2, rtol=1e-12, atol=1e-14)
 
 
-def test_singular_row_left_unchanged():
+def pin_singular(lib):
     """Reading for lambda = 0: an empty row has B + lambda I = 0, a zero pivot; the row
-    keeps its value and is counted."""
+    keeps its value and is counted (with lambda > 0 the empty row's solution is 0)."""
     coords = np.array([[0, 0, 0], [0, 1, 0], [2, 1, 0]], np.int32)  # row 1 of mode 1 empty
     t = oracle.Tensor(coords, [1.0, 2.0, 3.0], [3, 2, 1])
     A = [np.full((3, 1), 0.5), np.ones((2, 1)), np.ones((1, 1))]
-    r = oracle.residual(t, A)
-    bad = oracle.sals_sweep(t, A, r, 1, 0.0)
+    r = oracle.residual(t, A, lib)
+    bad = oracle.sals_sweep(t, A, r, 1, 0.0, lib=lib)
     assert bad == 1 and A[0][1, 0] == 0.5
     A = [np.full((3, 1), 0.5), np.ones((2, 1)), np.ones((1, 1))]
-    r = oracle.residual(t, A)
-    assert oracle.sals_sweep(t, A, r, 1, 0.1) == 0 and A[0][1, 0] == 0.0
+    r = oracle.residual(t, A, lib)
+    assert oracle.sals_sweep(t, A, r, 1, 0.1, lib=lib) == 0 and A[0][1, 0] == 0.0
+
+
+def test_singular_row_left_unchanged():
+    pin_singular(oracle.load())
 
 
 def test_convergence_on_noiseless_low_rank():
@@ -444,6 +448,10 @@ MUTANTS = {
     "Algorithm 3 rows in increasing length": (
         "return g_rownnz[a] > g_rownnz[b] ? -1 : 1;", "return g_rownnz[a] > g_rownnz[b] ? 1 : -1;"),
     "residuals not squared in the loss": ("sr += r[e] * r[e];", "sr += r[e];"),
+    "zero pivot accepted": ("if (!(d > 0.0)) return 1;", "if (d < 0.0) return 1;"),
+    "R-hat and Eq. (5) carry only the subset's first column": (
+        "for (int q = 0; q < C; ++q) {\n        double p = 1.0;\n        for (int n = 0; n < N; ++n) p *= A[n][(int64_t)ce[n]",
+        "for (int q = 0; q < 1; ++q) {\n        double p = 1.0;\n        for (int n = 0; n < N; ++n) p *= A[n][(int64_t)ce[n]"),
 }
 
 def pin_row_update_weighted(lib):
@@ -452,7 +460,7 @@ def pin_row_update_weighted(lib):
 
 PINS = [pin_group, pin_validate, pin_residual, pin_loss, pin_weighted_loss, pin_row_update_lstsq,
         pin_row_update_weighted, pin_als, pin_cdtf, pin_golden_cdtf, pin_sals_general, pin_foldin,
-        pin_alg3]
+        pin_singular, pin_alg3]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
